@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Benchmark: k-th order statistics of one 2^27 float32 array on GB300.
+
+Workload (the library's headline case): n = 2^27 float32, an equal-weight mixture of
+N(0,1), lognormal(0,2) and Student-t(1) with 5% exact duplicates of one value and 10
++-inf entries (seed 4); one step selects the five ranks k in {1, n/100, [(n+1)/2],
+99n/100, n}.  Inputs are resident in HBM when the timed region starts and are larger
+than L2 (512 MiB vs 129 MB), so no flush is needed between steps.
+
+value       whole-job Gelem/s = (selections x n) / time, device-timed with CUDA events
+e2e         the same through the public API with the array in pinned HOST memory:
+            host-to-device copy + selections + device-to-host read of the results
+roofline    the persistent select kernel: algorithmic bytes (passes x n x 4 + the
+            compacted bracket written once) / its CUDA-event duration, against the
+            measured HBM copy bandwidth
+cpu_baseline  the CPU oracle (numpy introselect on totalOrder keys, one thread) on the
+            same array and ranks
+
+``--impl reference`` times that oracle as the reference arm.  Under torchrun (N > 1)
+every rank runs an independent replica of the workload (the single-array path has no
+data to exchange on one GPU per rank); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_LOG2 = 27
+FAMILY = "mixture"
+SEED = 4
+
+
+def ranks_for(n):
+    return [1, n // 100, (n + 1) // 2, (99 * n) // 100, n]
+
+
+def measured_peaks():
+    for p in (os.path.join(ROOT, "MEASURED_PEAKS.json"),):
+        if os.path.exists(p):
+            with open(p) as f:
+                d = json.load(f)
+            return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_time(x, ks):
+    """The CPU oracle as it stands (oracle.select.select_kth, single-threaded numpy)."""
+    from oracle import select as osel
+    t0 = time.perf_counter()
+    for k in ks:
+        osel.select_kth(x, k)
+    return time.perf_counter() - t0
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle on the host cores, on a bounded sample of the workload."""
+    import numpy as np
+    import synth
+    n = 1 << N_LOG2
+    x = synth.heavy_mixture(FAMILY, n, seed=SEED)
+    ks = ranks_for(n)
+    # each step: the median rank on the full array (the five ranks cost ~5x as much)
+    for _ in range(args.warmup):
+        cpu_oracle_time(x, ks[2:3])
+    times = [cpu_oracle_time(x, ks[2:3]) for _ in range(args.steps)]
+    t = sum(times)
+    value = args.steps * n / t / 1e9
+    line = {
+        "impl": "reference", "metric": "k-th select Gelem/s (n=2^27 float32)", "value": value,
+        "unit": "Gelem/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"single-array k-th select, n=2^27 float32 {FAMILY} (+5% dups, 10 inf)",
+                   "ranks": "median rank per step", "l2": "input larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "Gelem/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} median selections on the full 2^27 array"},
+        "e2e": {"value": value, "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1104_2732_gb300 as gbs
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    n = 1 << N_LOG2
+    ks = ranks_for(n)
+    x_host = synth.heavy_mixture(FAMILY, n, seed=SEED + rank)
+    x = torch.from_numpy(x_host).cuda()
+    ctx = gbs.Context(local_rank)
+    ctx.reserve(n, 4)
+    out = torch.empty(len(ks), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for i, k in enumerate(ks):
+            ctx.select_kth(x, k, out=out[i:i + 1])
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    # per-call records (passes, per-pass timestamps) from one untimed step
+    records = []
+    for i, k in enumerate(ks):
+        ctx.select_kth(x, k, out=out[i:i + 1])
+        records.append(ctx.last_stats())
+
+    # ---------------- device-timed region ----------------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps * len(ks))]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        start.record(stream)
+        j = 0
+        for _ in range(args.steps):
+            for i, k in enumerate(ks):
+                ev[j][0].record(stream)
+                ctx.select_kth(x, k, out=out[i:i + 1])
+                ev[j][1].record(stream)
+                j += 1
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = start.elapsed_time(stop)
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+
+    total_elems = world * args.steps * len(ks) * n
+    value = total_elems / (ms_max * 1e-3) / 1e9
+
+    # ---------------- roofline of the select kernel ----------------
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bytes_per_call = [(r["passes"] * n + r["finish_pop"]) * 4 for r in records]
+    alg_bytes = args.steps * sum(bytes_per_call)
+    achieved = alg_bytes / (sum(launch_ms) * 1e-3) / 1e9
+    # per-pass bandwidth from the kernel's own timestamps (pass 0 and Kelley passes)
+    pass_gbs = []
+    for r in records:
+        t = r["t_ns"]
+        for i in range(min(r["passes"], len(t) - 1)):
+            dt = (t[i + 1] - t[i]) * 1e-9
+            if dt > 0:
+                pass_gbs.append(n * 4 / dt / 1e9)
+
+    # ---------------- end to end through the public API, host buffers ----------------
+    pinned = torch.from_numpy(x_host).pin_memory()
+    res_host = torch.empty(len(ks), dtype=torch.float32).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        x.copy_(pinned, non_blocking=True)
+        step()
+        res_host.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_value = world * len(ks) * n / (e2e_ms * 1e-3) / 1e9
+
+    # ---------------- comparator: full on-device sort of the same array ----------------
+    torch.cuda.synchronize()
+    for _ in range(2):
+        torch.sort(x)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(3):
+        torch.sort(x)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    sort_ms = s0.elapsed_time(s1) / 3
+
+    # ---------------- CPU oracle baseline (rank 0 only) ----------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        sample = ks[1:4]
+        t = cpu_oracle_time(x_host, sample)
+        cpu = {"value": len(sample) * n / t / 1e9, "unit": "Gelem/s", "cores": 1, "kind": "oracle",
+               "sample": "ranks n/100, (n+1)/2, 99n/100 on the full 2^27 array, one pass each",
+               "seconds": t}
+
+    if rank == 0:
+        sel_ms = [sum(launch_ms[i::len(ks)]) / args.steps for i in range(len(ks))]
+        line = {
+            "metric": "k-th select Gelem/s (n=2^27 float32)",
+            "value": value,
+            "unit": "Gelem/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": max(3, args.warmup),
+            "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"single-array k-th select, n=2^27 float32 {FAMILY} "
+                                   "(+5% duplicates, 10 +-inf), 5 ranks per step",
+                       "n": n, "ranks": ks, "parallelism": f"replicas x{world}",
+                       "l2": "input larger than L2 (no flush needed)"},
+            "gpu_launches": args.steps * len(ks),
+            "e2e": {"value": e2e_value, "unit": "Gelem/s", "h2d_bytes_per_step": n * 4,
+                    "d2h_bytes_per_step": len(ks) * 4},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "peak_kind": f"{peak_kind} hbm_gbs", "kernel": "select_kernel<float>"},
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+            "detail": {
+                "ms_per_selection": dict(zip([str(k) for k in ks], sel_ms)),
+                "passes": [r["passes"] for r in records],
+                "how": [r["how"] for r in records],
+                "finish_pop": [r["finish_pop"] for r in records],
+                "pass_gbs_median": statistics.median(pass_gbs) if pass_gbs else None,
+                "pass_gbs": [round(v, 1) for v in pass_gbs],
+                "torch_sort_ms": sort_ms,
+                "torch_sort_gelems": n / (sort_ms * 1e-3) / 1e9,
+                "median_select_ms": sel_ms[2],
+                "speedup_vs_torch_sort_median": sort_ms / sel_ms[2],
+            },
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+/*
+ * gbselect — exact order statistics of large real vectors on one GB300 (sm_103a).
+ *
+ * Method: G. Beliakov, "Parallel calculation of the median and order statistics on
+ * GPUs with application to robust regression", arXiv:1104.2732.  The k-th order
+ * statistic x_(k) is the minimiser of the convex piecewise-linear cost of
+ * Eq. (med_objOS); Kelley's cutting plane (Algorithm 1, Sec. 3) minimises it, one
+ * fused pass over x per iterate computing #(x<t), #(x<=t) and the cost; the final
+ * bracket is compacted and the answer selected inside it (Sec. 3, hybrid finish).
+ *
+ * Conventions for every entry point:
+ *  - Array pointers are DEVICE pointers owned by the caller; inputs are never
+ *    written.  Outputs are device pointers, written asynchronously on `stream`.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.
+ *  - k is 1-based (Sec. 1).  The median is x_(k) with k = floor((n+1)/2) (Sec. 1).
+ *  - Results are elements of x, bit for bit: ties, -0/+0 and +-inf are ordered by
+ *    IEEE-754 totalOrder (-inf < ... < -0 < +0 < ... < +inf).
+ *  - Argument errors are detected on the host before any launch and return
+ *    GBS_EINVAL (nothing is launched).  Data-dependent errors (NaN in the input,
+ *    an internal wait that gave up) are recorded on the device; gbs_last_stats()
+ *    synchronises the stream of the last call and returns them.  On GBS_ENAN the
+ *    output holds a quiet NaN.
+ *  - A context owns a device workspace.  Calls on one context must not overlap in
+ *    time (issue them on one stream, or use one context per stream).  A call that
+ *    needs more workspace than reserved allocates it (synchronously); call
+ *    gbs_reserve() first to keep later calls allocation-free.
+ *  - No exception crosses this interface.
+ */
+#ifndef GBSELECT_H
+#define GBSELECT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GBS_OK = 0,
+    GBS_EINVAL = 1,   /* bad argument (n < 1, k outside [1,n], NULL pointer, ...) */
+    GBS_ENAN = 2,     /* the input holds a NaN: it has no rank */
+    GBS_ENOMEM = 3,   /* workspace allocation failed */
+    GBS_ECUDA = 4,    /* a CUDA runtime call failed */
+    GBS_ETIMEOUT = 5, /* a bounded device-side wait gave up; the result is not valid */
+    GBS_EINTERNAL = 6 /* an internal consistency check failed; the result is not valid */
+} gbs_status;
+
+typedef struct gbs_ctx gbs_ctx;
+
+/* How a selection ended (gbs_run_stats.how). */
+enum {
+    GBS_HOW_NONE = 0,
+    GBS_HOW_NEGINF = 1, /* k <= #(x = -inf) */
+    GBS_HOW_POSINF = 2, /* k > n - #(x = +inf) */
+    GBS_HOW_MIN = 3,    /* x_(k) is the finite minimum (Sec. 3, step 0 extremes) */
+    GBS_HOW_MAX = 4,    /* x_(k) is the finite maximum */
+    GBS_HOW_HIT = 5,    /* an iterate t had 0 in dF(t) (Algorithm 1, step 1.3) */
+    GBS_HOW_FINISH = 6  /* compaction of the bracket and radix select (Sec. 3, hybrid) */
+};
+
+/* Tuning knobs.  Zero fields take the defaults given beside them. */
+typedef struct {
+    int64_t cap;         /* the pass that sees a bracket of <= cap elements compacts it and
+                            the cutting plane stops (Sec. 3: "the algorithm stops when the
+                            cost of its iteration outweighs the benefit"); 0 = max(n/16, 4096) */
+    int32_t maxit;       /* cutting-plane iterations before compaction is forced; 0 = 64 */
+    int32_t blocks_per_sm; /* CTAs per SM of the persistent kernel; 0 = as many as fit (<= 2) */
+    int32_t use_learned; /* 1 = start from the bracket proposed by the loaded model (if any) */
+    int32_t reserved[7];
+} gbs_config;
+
+/* Per-call record of the last selection on a context (host copy). */
+typedef struct {
+    int32_t status;        /* gbs_status of the device work */
+    int32_t how;           /* GBS_HOW_* */
+    int32_t passes;        /* full passes over x, the min/max/count pass included */
+    int32_t kelley_steps;  /* iterates from the tangent intersection (Algorithm 1, step 1.1) */
+    int32_t bisect_steps;  /* safeguard iterates (bracket midpoint in totalOrder keys) */
+    int32_t finish_rounds; /* 8-bit radix rounds of the finish */
+    int32_t grid;          /* CTAs of the persistent launch */
+    int32_t learned;       /* 1 if a proposed bracket was used, 2 if it failed its count check */
+    int64_t n, k;
+    int64_t finish_pop;    /* elements compacted for the finish */
+    int64_t pops[64];      /* bracket population after each iterate */
+    double iterates[64];   /* the evaluated points t */
+    uint64_t t_ns[72];     /* device timestamps (globaltimer, ns) at each grid-wide step */
+    int32_t n_t;           /* valid entries of t_ns */
+    int32_t pad;
+} gbs_run_stats;
+
+/* Pass 0 of Algorithm 1 (Sec. 3, step 0): extremes and sums over x. */
+typedef struct {
+    int64_t n;
+    int64_t n_nan, n_neginf, n_posinf, n_negzero, n_finite;
+    double min, max;        /* finite minimum / maximum (0 if no finite element); a zero
+                               extreme is reported as +0, see n_negzero */
+    int64_t c_le_min;       /* #(x <= min) under IEEE comparison (infinities included) */
+    int64_t c_lt_max;       /* #(x <  max) */
+    double sum;             /* sum of the finite elements (float32 partials, float64 total) */
+} gbs_array_stats;
+
+/* One fused cost + count pass (Algorithm 1, step 1.2; the figure's Objective()). */
+typedef struct {
+    int64_t c_lt_t;   /* #(x <  t) */
+    int64_t c_le_t;   /* #(x <= t) */
+    int64_t c_le_a;   /* #(x <= a) */
+    int64_t pad;
+    double S;         /* sum over a < x_i < t of (t - x_i) */
+    double dphi;      /* Phi(t) - Phi(a) = (c_le_a - k + 1/2)(t - a) + S, Phi = F/n of Eq. (med_objOS) */
+} gbs_cost_eval;
+
+/* Context lifetime.  `device` is the CUDA ordinal the context works on. */
+gbs_status gbs_create(gbs_ctx** ctx, int device);
+void gbs_destroy(gbs_ctx* ctx);
+
+/* Grows the workspace so that selections of up to n elements of elem_bytes (4 or 8)
+ * run without allocating.  Synchronous. */
+gbs_status gbs_reserve(gbs_ctx* ctx, int64_t n, int32_t elem_bytes);
+
+gbs_status gbs_set_config(gbs_ctx* ctx, const gbs_config* cfg);
+gbs_status gbs_get_config(gbs_ctx* ctx, gbs_config* cfg);
+
+/* x_(k) of x[0..n) (Sec. 1; Algorithm 1 and the hybrid finish of Sec. 3).
+ * x: n elements, device, contiguous, any alignment.  out: 1 element, device. */
+gbs_status gbs_select_kth_f32(gbs_ctx* ctx, const float* x, int64_t n, int64_t k, float* out,
+                              void* stream);
+gbs_status gbs_select_kth_f64(gbs_ctx* ctx, const double* x, int64_t n, int64_t k, double* out,
+                              void* stream);
+
+/* Med(x) = x_(floor((n+1)/2)) (Sec. 1, Eq. (med_obj)). */
+gbs_status gbs_median_f32(gbs_ctx* ctx, const float* x, int64_t n, float* out, void* stream);
+gbs_status gbs_median_f64(gbs_ctx* ctx, const double* x, int64_t n, double* out, void* stream);
+
+/* Pass 0 alone (Sec. 3, step 0).  out: device pointer to one gbs_array_stats. */
+gbs_status gbs_array_stats_f32(gbs_ctx* ctx, const float* x, int64_t n, gbs_array_stats* out,
+                               void* stream);
+gbs_status gbs_array_stats_f64(gbs_ctx* ctx, const double* x, int64_t n, gbs_array_stats* out,
+                               void* stream);
+
+/* One fused pass at the points a < t for rank k (Algorithm 1, step 1.2; Sec. 4 figure,
+ * Objective()).  a and t are converted to the element type.  out: device pointer to one
+ * gbs_cost_eval.  EINVAL unless a < t and 1 <= k <= n. */
+gbs_status gbs_cost_pass_f32(gbs_ctx* ctx, const float* x, int64_t n, int64_t k, double a,
+                             double t, gbs_cost_eval* out, void* stream);
+gbs_status gbs_cost_pass_f64(gbs_ctx* ctx, const double* x, int64_t n, int64_t k, double a,
+                             double t, gbs_cost_eval* out, void* stream);
+
+/* Synchronises the stream of the last call on ctx and copies its record to *out. */
+gbs_status gbs_last_stats(gbs_ctx* ctx, gbs_run_stats* out);
+
+/* Static, human-readable name of a status code. */
+const char* gbs_status_string(gbs_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBSELECT_H */

@@ -1,0 +1,239 @@
+"""Python binding of libgbselect (exact order statistics on GB300).
+
+Argument marshalling only: every step of the selection runs in the library's CUDA
+kernels.  The raw C entry points are exposed under their C names (``gbs_select_kth_f32``
+and so on, see include/gbselect.h); :class:`Context` wraps them for torch tensors.
+Importing fails loudly if the library has not been built (``python -m
+paper_1104_2732_gb300.build``); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgbselect.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1104_2732_gb300.build`")
+_lib = C.CDLL(LIB_PATH)
+
+# ------------------------------------------------------------------ status codes
+GBS_OK, GBS_EINVAL, GBS_ENAN, GBS_ENOMEM, GBS_ECUDA, GBS_ETIMEOUT, GBS_EINTERNAL = range(7)
+HOW = {0: "none", 1: "neginf", 2: "posinf", 3: "min", 4: "max", 5: "hit", 6: "finish"}
+
+
+class GbsError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = int(status)
+        msg = _lib.gbs_status_string(self.status).decode()
+        super().__init__(f"{what}: {msg} (status {self.status})" if what else msg)
+
+
+# ------------------------------------------------------------------ structures
+class gbs_config(C.Structure):
+    _fields_ = [("cap", C.c_int64), ("maxit", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("use_learned", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class gbs_run_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("how", C.c_int32), ("passes", C.c_int32),
+                ("kelley_steps", C.c_int32), ("bisect_steps", C.c_int32), ("finish_rounds", C.c_int32),
+                ("grid", C.c_int32), ("learned", C.c_int32), ("n", C.c_int64), ("k", C.c_int64),
+                ("finish_pop", C.c_int64), ("pops", C.c_int64 * 64), ("iterates", C.c_double * 64),
+                ("t_ns", C.c_uint64 * 72), ("n_t", C.c_int32), ("pad", C.c_int32)]
+
+
+class gbs_array_stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_nan", C.c_int64), ("n_neginf", C.c_int64), ("n_posinf", C.c_int64),
+                ("n_negzero", C.c_int64), ("n_finite", C.c_int64), ("min", C.c_double), ("max", C.c_double),
+                ("c_le_min", C.c_int64), ("c_lt_max", C.c_int64), ("sum", C.c_double)]
+
+
+class gbs_cost_eval(C.Structure):
+    _fields_ = [("c_lt_t", C.c_int64), ("c_le_t", C.c_int64), ("c_le_a", C.c_int64), ("pad", C.c_int64),
+                ("S", C.c_double), ("dphi", C.c_double)]
+
+
+_P = C.c_void_p
+_I64 = C.c_int64
+_SIGS = {
+    "gbs_create": (C.c_int, [C.POINTER(_P), C.c_int]),
+    "gbs_destroy": (None, [_P]),
+    "gbs_reserve": (C.c_int, [_P, _I64, C.c_int32]),
+    "gbs_set_config": (C.c_int, [_P, C.POINTER(gbs_config)]),
+    "gbs_get_config": (C.c_int, [_P, C.POINTER(gbs_config)]),
+    "gbs_select_kth_f32": (C.c_int, [_P, _P, _I64, _I64, _P, _P]),
+    "gbs_select_kth_f64": (C.c_int, [_P, _P, _I64, _I64, _P, _P]),
+    "gbs_median_f32": (C.c_int, [_P, _P, _I64, _P, _P]),
+    "gbs_median_f64": (C.c_int, [_P, _P, _I64, _P, _P]),
+    "gbs_array_stats_f32": (C.c_int, [_P, _P, _I64, _P, _P]),
+    "gbs_array_stats_f64": (C.c_int, [_P, _P, _I64, _P, _P]),
+    "gbs_cost_pass_f32": (C.c_int, [_P, _P, _I64, _I64, C.c_double, C.c_double, _P, _P]),
+    "gbs_cost_pass_f64": (C.c_int, [_P, _P, _I64, _I64, C.c_double, C.c_double, _P, _P]),
+    "gbs_last_stats": (C.c_int, [_P, C.POINTER(gbs_run_stats)]),
+    "gbs_status_string": (C.c_char_p, [C.c_int]),
+}
+
+
+def _bind(table):
+    for name, (res, args) in table.items():
+        fn = getattr(_lib, name)
+        fn.restype = res
+        fn.argtypes = args
+        globals()[name] = fn
+
+
+_bind(_SIGS)
+EXPORTED = tuple(_SIGS)
+
+
+def _check(status, what):
+    if status != GBS_OK:
+        raise GbsError(status, what)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(int(stream.cuda_stream))
+
+
+def _suffix(x):
+    import torch
+    if x.dtype == torch.float32:
+        return "f32"
+    if x.dtype == torch.float64:
+        return "f64"
+    raise TypeError(f"float32 or float64 expected, got {x.dtype}")
+
+
+def _as_input(x):
+    import torch
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError("a CUDA tensor is required")
+    if not x.is_contiguous():
+        raise ValueError("a contiguous tensor is required")
+    return x
+
+
+class Context:
+    """Owns a gbs_ctx (workspace, configuration) on one CUDA device."""
+
+    def __init__(self, device=None):
+        import torch
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        h = _P()
+        _check(gbs_create(C.byref(h), self.device), "gbs_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            gbs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -------------------------------------------------------------- configuration
+    def set_config(self, **kw):
+        cfg = gbs_config()
+        _check(gbs_get_config(self._h, C.byref(cfg)), "gbs_get_config")
+        for key, val in kw.items():
+            setattr(cfg, key, int(val))
+        _check(gbs_set_config(self._h, C.byref(cfg)), "gbs_set_config")
+
+    def get_config(self):
+        cfg = gbs_config()
+        _check(gbs_get_config(self._h, C.byref(cfg)), "gbs_get_config")
+        return {"cap": cfg.cap, "maxit": cfg.maxit, "blocks_per_sm": cfg.blocks_per_sm,
+                "use_learned": cfg.use_learned}
+
+    def reserve(self, n, elem_bytes=4):
+        _check(gbs_reserve(self._h, int(n), int(elem_bytes)), "gbs_reserve")
+
+    # -------------------------------------------------------------- selection
+    def select_kth(self, x, k, out=None, stream=None):
+        """x_(k) of a contiguous CUDA tensor (1-based k); returns a 1-element device tensor."""
+        import torch
+        x = _as_input(x)
+        if out is None:
+            out = torch.empty(1, dtype=x.dtype, device=x.device)
+        fn = globals()["gbs_select_kth_" + _suffix(x)]
+        _check(fn(self._h, C.c_void_p(x.data_ptr()), x.numel(), int(k), C.c_void_p(out.data_ptr()),
+                  _stream_ptr(stream)), "gbs_select_kth")
+        return out
+
+    def median(self, x, out=None, stream=None):
+        import torch
+        x = _as_input(x)
+        if out is None:
+            out = torch.empty(1, dtype=x.dtype, device=x.device)
+        fn = globals()["gbs_median_" + _suffix(x)]
+        _check(fn(self._h, C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(out.data_ptr()),
+                  _stream_ptr(stream)), "gbs_median")
+        return out
+
+    def array_stats(self, x, stream=None):
+        import torch
+        x = _as_input(x)
+        buf = torch.empty(C.sizeof(gbs_array_stats), dtype=torch.uint8, device=x.device)
+        fn = globals()["gbs_array_stats_" + _suffix(x)]
+        _check(fn(self._h, C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(buf.data_ptr()),
+                  _stream_ptr(stream)), "gbs_array_stats")
+        rec = gbs_array_stats.from_buffer_copy(bytes(buf.cpu().numpy()))
+        return {f: getattr(rec, f) for f, _ in gbs_array_stats._fields_}
+
+    def cost_pass(self, x, k, a, t, stream=None):
+        import torch
+        x = _as_input(x)
+        buf = torch.empty(C.sizeof(gbs_cost_eval), dtype=torch.uint8, device=x.device)
+        fn = globals()["gbs_cost_pass_" + _suffix(x)]
+        _check(fn(self._h, C.c_void_p(x.data_ptr()), x.numel(), int(k), float(a), float(t),
+                  C.c_void_p(buf.data_ptr()), _stream_ptr(stream)), "gbs_cost_pass")
+        rec = gbs_cost_eval.from_buffer_copy(bytes(buf.cpu().numpy()))
+        return {f: getattr(rec, f) for f, _ in gbs_cost_eval._fields_ if f != "pad"}
+
+    def last_stats(self, raise_on_error=True):
+        """Synchronises the last call's stream and returns its record as a dict."""
+        rs = gbs_run_stats()
+        _check(gbs_last_stats(self._h, C.byref(rs)), "gbs_last_stats")
+        if raise_on_error and rs.status != GBS_OK:
+            raise GbsError(rs.status, "device")
+        d = {f: getattr(rs, f) for f in ("status", "how", "passes", "kelley_steps", "bisect_steps",
+                                           "finish_rounds", "grid", "learned", "n", "k", "finish_pop", "n_t")}
+        npass = max(0, rs.passes - 1)
+        d["how"] = HOW.get(rs.how, str(rs.how))
+        d["pops"] = list(rs.pops[:min(npass, 64)])
+        d["iterates"] = list(rs.iterates[:min(npass, 64)])
+        d["t_ns"] = list(rs.t_ns[:rs.n_t])
+        return d
+
+
+_default = {}
+
+
+def default_context(device=None):
+    import torch
+    dev = torch.cuda.current_device() if device is None else int(device)
+    if dev not in _default:
+        _default[dev] = Context(dev)
+    return _default[dev]
+
+
+def select_kth(x, k, out=None, stream=None):
+    return default_context(x.device.index).select_kth(x, k, out, stream)
+
+
+def median(x, out=None, stream=None):
+    return default_context(x.device.index).median(x, out, stream)

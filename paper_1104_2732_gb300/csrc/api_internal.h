@@ -1,0 +1,38 @@
+// Internal layout of a context (not part of the C-ABI).
+#pragma once
+
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "gbselect.h"
+
+namespace gbs {
+struct Ctrl;
+struct PassPartial;
+struct StatsPartial;
+}  // namespace gbs
+
+struct gbs_ctx {
+  int device = 0;
+  int num_sms = 0;
+  gbs_config cfg{};
+  // one device allocation, carved into the pieces below
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  gbs::Ctrl* ctrl = nullptr;
+  gbs::PassPartial* part = nullptr;
+  gbs::StatsPartial* spart = nullptr;
+  unsigned long long* ghist = nullptr;
+  gbs_run_stats* rs = nullptr;
+  void* aux = nullptr;          // fixed-size area for the other subsystems
+  size_t aux_bytes = 1 << 20;
+  void* z = nullptr;            // compaction regions (grows with n)
+  size_t z_bytes = 0;
+  cudaStream_t last_stream = nullptr;
+  int last_grid = 0;
+};
+
+// Grows the workspace so that its z area holds at least z_bytes.  Synchronous.
+gbs_status gbs_internal_ensure(gbs_ctx* c, size_t z_bytes);
+// Frees the resources other subsystems attached to the context.
+void gbs_internal_release(gbs_ctx* c);

@@ -1,0 +1,4 @@
+// Per-context resources of the subsystems beyond the single-array select.
+#include "api_internal.h"
+
+void gbs_internal_release(gbs_ctx*) {}

@@ -77,11 +77,14 @@ def heavy_mixture(family, n, seed, dtype=np.float32, dup_frac=0.05, n_inf=10):
     elif family == "lognormal":
         x = rng.lognormal(0.0, 2.0, n)
     elif family == "cauchy":
-        x = rng.standard_t(1.0, n)
+        x = rng.standard_cauchy(n)          # Student-t with nu = 1
     elif family == "mixture":
-        which = rng.integers(0, 3, n)
-        x = np.where(which == 0, rng.standard_normal(n),
-                     np.where(which == 1, rng.lognormal(0.0, 2.0, n), rng.standard_t(1.0, n)))
+        which = rng.integers(0, 3, n, dtype=np.int8)
+        x = np.empty(n)
+        for c, draw in enumerate((rng.standard_normal, lambda m: rng.lognormal(0.0, 2.0, m),
+                                  rng.standard_cauchy)):
+            sel = which == c
+            x[sel] = draw(int(np.count_nonzero(sel)))
     else:
         raise ValueError(family)
     x = x.astype(dtype)

@@ -1,0 +1,67 @@
+"""The C-ABI library builds, loads and exports every entry point include/*.h declares.
+CPU only: no call here touches a GPU."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:gbs_status|void|const char\s*\*)\s+(gbs_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1104_2732_gb300 import build as b
+    return b.build()
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    assert {"gbs_create", "gbs_select_kth_f32", "gbs_median_f64", "gbs_status_string"} <= names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = _declared() - exported
+    assert not missing, missing
+
+
+def test_binding_covers_header(libpath):
+    import paper_1104_2732_gb300 as gbs
+    missing = _declared() - set(gbs.EXPORTED)
+    assert not missing, missing
+    for name in _declared():
+        assert callable(getattr(gbs, name))
+
+
+def test_host_side_checks_need_no_gpu(libpath):
+    import paper_1104_2732_gb300 as gbs
+    assert gbs.gbs_status_string(0) == b"ok"
+    assert gbs.gbs_status_string(2) == b"input contains NaN"
+    # NULL context / bad arguments are rejected before any CUDA call
+    assert gbs.gbs_select_kth_f32(None, None, 10, 1, None, None) == gbs.GBS_EINVAL
+    assert gbs.gbs_median_f64(None, None, 0, None, None) == gbs.GBS_EINVAL
+    assert gbs.gbs_cost_pass_f32(None, None, 5, 1, 0.0, 1.0, None, None) == gbs.GBS_EINVAL
+    assert gbs.gbs_create(None, 0) == gbs.GBS_EINVAL
+
+
+def test_struct_sizes_match_header(libpath):
+    """The ctypes mirrors of the header's structs have the C layout's sizes."""
+    import paper_1104_2732_gb300 as gbs
+    assert ctypes.sizeof(gbs.gbs_config) == 8 + 4 * 10
+    assert ctypes.sizeof(gbs.gbs_cost_eval) == 48
+    assert ctypes.sizeof(gbs.gbs_array_stats) == 88
+    assert ctypes.sizeof(gbs.gbs_run_stats) == 4 * 8 + 3 * 8 + 64 * 8 * 2 + 72 * 8 + 8
