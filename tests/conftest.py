@@ -19,5 +19,7 @@ def lib():
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_1104_2732_gb300 as gbs
     return gbs

@@ -23,8 +23,8 @@ def _declared():
 
 @pytest.fixture(scope="module")
 def libpath():
-    from paper_1104_2732_gb300 import build as b
-    return b.build()
+    import __graft_entry__
+    return __graft_entry__._build_module().build()
 
 
 def test_header_declares_entry_points():
