@@ -72,6 +72,7 @@ _SIGS = {
     "gbs_cost_pass_f32": (C.c_int, [_P, _P, _I64, _I64, C.c_double, C.c_double, _P, _P]),
     "gbs_cost_pass_f64": (C.c_int, [_P, _P, _I64, _I64, C.c_double, C.c_double, _P, _P]),
     "gbs_last_stats": (C.c_int, [_P, C.POINTER(gbs_run_stats)]),
+    "gbs_select_kth_f32_noalloc": (C.c_int, [_P, _I64, _I64, _P, _P]),
     "gbs_status_string": (C.c_char_p, [C.c_int]),
 }
 

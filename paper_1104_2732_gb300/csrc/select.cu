@@ -831,6 +831,24 @@ gbs_status run_select(gbs_ctx* c, const double* x, long long n, long long k, dou
                       double t, gbs_array_stats* sout, gbs_cost_eval* eout, cudaStream_t stream) {
   return launch_select<double>(c, x, n, k, out, mode, a, t, sout, eout, stream);
 }
+// Pieces of the float32 launch for callers that bring their own scratch.
+long long select_region_cap_f32(long long n, int grid) { return region_cap_for<float>(n, grid); }
+float select_stats_sigma_f32(long long n, int grid) { return stats_sigma<float>(n, grid); }
+int select_occupancy_f32() {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, select_kernel<float>, kThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return occ;
+}
+cudaError_t select_launch_f32(const SelArgs<float>& A, int grid, cudaStream_t stream) {
+  SelArgs<float> a = A;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel((const void*)select_kernel<float>, dim3(grid), dim3(kThreads), args, 0,
+                                     stream);
+}
+
 gbs_status reserve_select(gbs_ctx* c, long long n, int elem_bytes) {
   DeviceGuard g(c->device);
   if (!g.ok) return GBS_ECUDA;

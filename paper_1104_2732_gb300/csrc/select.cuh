@@ -55,4 +55,11 @@ gbs_status run_select(gbs_ctx* c, const double* x, long long n, long long k, dou
 // Grows the workspace for selections of up to n elements of elem_bytes.
 gbs_status reserve_select(gbs_ctx* c, long long n, int elem_bytes);
 
+// Pieces of the float32 launch for callers that bring their own scratch: the compaction
+// region stride, the pass-0 sum scale, CTAs per SM that fit, and the cooperative launch.
+long long select_region_cap_f32(long long n, int grid);
+float select_stats_sigma_f32(long long n, int grid);
+int select_occupancy_f32();
+cudaError_t select_launch_f32(const SelArgs<float>& A, int grid, cudaStream_t stream);
+
 }  // namespace gbs
