@@ -232,13 +232,19 @@ def main():
     alg_bytes = args.steps * sum(bytes_per_call)
     achieved = alg_bytes / (sum(launch_ms) * 1e-3) / 1e9
     # per-pass bandwidth from the kernel's own timestamps (pass 0 and Kelley passes)
-    pass_gbs = []
+    pass_gbs, stream_gbs, overhead_us = [], [], []
     for r in records:
         t = r["t_ns"]
         for i in range(min(r["passes"], len(t) - 1)):
             dt = (t[i + 1] - t[i]) * 1e-9
             if dt > 0:
                 pass_gbs.append(n * 4 / dt / 1e9)
+            # cutting-plane pass i-1 (pass 0 has no separate stamp): streaming part alone
+            if i >= 1 and i - 1 < len(r["t_stream_ns"]) and r["t_stream_ns"][i - 1]:
+                ds = (r["t_stream_ns"][i - 1] - t[i]) * 1e-9
+                if ds > 0:
+                    stream_gbs.append(n * 4 / ds / 1e9)
+                    overhead_us.append(round((dt - ds) * 1e6, 1))
 
     # ---------------- end to end through the public API, host buffers ----------------
     pinned = torch.from_numpy(x_host).pin_memory()
@@ -311,6 +317,8 @@ def main():
                 "finish_pop": [r["finish_pop"] for r in records],
                 "pass_gbs_median": statistics.median(pass_gbs) if pass_gbs else None,
                 "pass_gbs": [round(v, 1) for v in pass_gbs],
+                "stream_gbs": [round(v, 1) for v in stream_gbs],
+                "pass_overhead_us": overhead_us,
                 "torch_sort_ms": sort_ms,
                 "torch_sort_gelems": n / (sort_ms * 1e-3) / 1e9,
                 "median_select_ms": sel_ms[2],

@@ -85,6 +85,7 @@ typedef struct {
     int64_t pops[64];      /* bracket population after each iterate */
     double iterates[64];   /* the evaluated points t */
     uint64_t t_ns[72];     /* device timestamps (globaltimer, ns) at each grid-wide step */
+    uint64_t t_stream_ns[64]; /* CTA 0: end of the streaming part of each cutting-plane pass */
     int32_t n_t;           /* valid entries of t_ns */
     int32_t pad;
 } gbs_run_stats;
@@ -152,7 +153,7 @@ gbs_status gbs_cost_pass_f64(gbs_ctx* ctx, const double* x, int64_t n, int64_t k
  * is captured into a graph, hosts whose device memory belongs to their own arena, loops
  * where an allocation's implicit device synchronisation is not acceptable).
  * Same kernel and same result as gbs_select_kth_f32.  Its scratch is one static device
- * array of about 8.5 MiB that every GPU loading the library holds until process exit.
+ * array of about 4.1 MiB that every GPU loading the library holds until process exit.
  * Limits: 1 <= k <= n <= 1048576 (2^20), else GBS_EINVAL before any launch.
  * Runs on the current device.  The first call on a device resolves the array's address
  * there (cudaGetSymbolAddress); make that first call before any stream capture.

@@ -41,7 +41,8 @@ class gbs_run_stats(C.Structure):
                 ("kelley_steps", C.c_int32), ("bisect_steps", C.c_int32), ("finish_rounds", C.c_int32),
                 ("grid", C.c_int32), ("learned", C.c_int32), ("n", C.c_int64), ("k", C.c_int64),
                 ("finish_pop", C.c_int64), ("pops", C.c_int64 * 64), ("iterates", C.c_double * 64),
-                ("t_ns", C.c_uint64 * 72), ("n_t", C.c_int32), ("pad", C.c_int32)]
+                ("t_ns", C.c_uint64 * 72), ("t_stream_ns", C.c_uint64 * 64), ("n_t", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 class gbs_array_stats(C.Structure):
@@ -218,6 +219,7 @@ class Context:
         d["pops"] = list(rs.pops[:min(npass, 64)])
         d["iterates"] = list(rs.iterates[:min(npass, 64)])
         d["t_ns"] = list(rs.t_ns[:rs.n_t])
+        d["t_stream_ns"] = list(rs.t_stream_ns[:min(npass, 64)])
         return d
 
 

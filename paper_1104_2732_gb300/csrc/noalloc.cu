@@ -6,7 +6,7 @@
 // stream is being captured into a CUDA graph, hosts whose device memory is owned by an
 // arena or pool of their own, and latency-critical loops where cudaMalloc / cudaFree
 // would synchronise the device.  This entry point serves them.  Its scratch is the
-// static array below (about 8.5 MiB), which every GPU that loads the library holds
+// static array below (about 4.1 MiB), which every GPU that loads the library holds
 // until the process exits.
 #include <cstddef>
 #include <mutex>
@@ -21,8 +21,9 @@ namespace {
 
 constexpr long long kNoAllocMaxN = 1ll << 20;   // largest n this entry point accepts
 constexpr int kNoAllocMaxGrid = 512;            // CTAs of its persistent launch, at most
-// Compaction area: grid x region_cap floats <= 4 (n/4 + 1) + 2056 grid <= this bound.
-constexpr long long kNoAllocZ = 2048ll * (513 + kNoAllocMaxGrid) + 8ll * kNoAllocMaxGrid;
+// Compaction area: whole chunks of the largest input plus the scalar head and tail,
+// chunk_count(n/4 + 1) * kChunkVecs * 4 + 8 floats.
+constexpr long long kNoAllocZ = ((kNoAllocMaxN / 4 + 1 + kChunkVecs - 1) / kChunkVecs) * kChunkVecs * 4 + 8;
 
 constexpr size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 constexpr size_t kOffCtrl = 0;
@@ -89,8 +90,8 @@ extern "C" gbs_status gbs_select_kth_f32_noalloc(const float* x, int64_t n, int6
   DeviceSetup s;
   gbs_status st = setup_current_device(dev, &s);
   if (st != GBS_OK) return st;
-  const long long rcap = select_region_cap_f32(n, s.grid);
-  if (rcap * s.grid > kNoAllocZ) return GBS_EINVAL;   // cannot happen for n <= kNoAllocMaxN
+  const long long zel = select_z_elems_f32(n, s.grid);
+  if (zel > kNoAllocZ) return GBS_EINVAL;   // cannot happen for n <= kNoAllocMaxN
 
   cudaStream_t strm = static_cast<cudaStream_t>(stream);
   SelArgs<float> A;
@@ -105,7 +106,7 @@ extern "C" gbs_status gbs_select_kth_f32_noalloc(const float* x, int64_t n, int6
   A.ghist = reinterpret_cast<unsigned long long*>(s.base + kOffHist);
   A.rs = reinterpret_cast<gbs_run_stats*>(s.base + kOffRs);
   A.z = reinterpret_cast<float*>(s.base + kOffZ);
-  A.region_cap = rcap;
+  A.z_elems = zel;
   A.stats_out = nullptr;
   A.eval_out = nullptr;
   // The array keeps the previous call's contents: the barrier and status words must

@@ -14,6 +14,7 @@
 #include <cstdint>
 
 #include "common.cuh"
+#include "layout.cuh"
 #include "select.cuh"
 #include "api_internal.h"
 
@@ -104,121 +105,38 @@ struct Geometry {
   }
 };
 
-// Calls f(element) for every element of x handled by this thread.  Direction
-// alternates with `reverse` so that consecutive passes start where the previous one
-// ended (the most recently read lines are still in L2).
-template <typename T, typename Fn>
-__device__ __forceinline__ void stream_x(const T* __restrict__ x, const Geometry<T>& g, bool reverse, Fn& f) {
-  using V = typename Ops<T>::V;
-  const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
-  const long long stride = (long long)gridDim.x * kThreads;
-  if (gtid < g.head) f(x[gtid]);
-  if (gtid < g.n - g.tail0) f(x[g.tail0 + gtid]);
-  const V* xv = reinterpret_cast<const V*>(x + g.head);
-  const long long nv = g.nv;
-  long long v = gtid;
-  for (; v + (kUnroll - 1) * stride < nv; v += kUnroll * stride) {
-    V r[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      long long i = v + u * stride;
-      r[u] = load_stream(xv + (reverse ? nv - 1 - i : i));
-    }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) Ops<T>::each(r[u], f);
-  }
-  for (; v < nv; v += stride) {
-    V r = load_stream(xv + (reverse ? nv - 1 - v : v));
-    Ops<T>::each(r, f);
-  }
-}
-
-// Streaming loop of a compacting pass: f(element) as above, plus every element with
-// keep(element) true is appended to this CTA's region `zr` (counter `*s_cnt` in shared
-// memory).  Warp-uniform loop so that the per-warp scan is legal.
-template <typename T, typename Fn, typename Keep>
-__device__ __forceinline__ void stream_x_compact(const T* __restrict__ x, const Geometry<T>& g,
-                                                 bool reverse, Fn& f, Keep& keep, T* __restrict__ zr,
-                                                 unsigned int* s_cnt) {
-  using V = typename Ops<T>::V;
-  constexpr int kVec = Ops<T>::kVec;
-  const int lane = threadIdx.x & 31;
-  const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
-  const long long stride = (long long)gridDim.x * kThreads;
-  // scalar head and tail (at most 2*kVec elements, first threads of CTA 0)
-  if (gtid < g.head) {
-    T e = x[gtid];
-    f(e);
-    if (keep(e)) zr[atomicAdd(s_cnt, 1u)] = e;
-  }
-  if (gtid < g.n - g.tail0) {
-    T e = x[g.tail0 + gtid];
-    f(e);
-    if (keep(e)) zr[atomicAdd(s_cnt, 1u)] = e;
-  }
-  const V* xv = reinterpret_cast<const V*>(x + g.head);
-  const long long nv = g.nv;
-  const long long wbase0 = gtid - lane;           // warp-uniform
-  for (long long wb = wbase0; wb < nv; wb += kUnroll * stride) {
-    V r[kUnroll];
-    bool ok[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      long long i = wb + lane + u * stride;
-      ok[u] = i < nv;
-      if (ok[u]) r[u] = load_stream(xv + (reverse ? nv - 1 - i : i));
-    }
-    unsigned int mask = 0, cnt = 0;
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      if (ok[u]) {
-        Ops<T>::each(r[u], f);
-#pragma unroll
-        for (int j = 0; j < kVec; ++j) {
-          bool kk = keep(Ops<T>::get(r[u], j));
-          mask |= (kk ? 1u : 0u) << (u * kVec + j);
-          cnt += kk;
-        }
-      }
-    }
-    // warp exclusive scan of cnt
-    unsigned int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned int base = 0;
-    if (total) {
-      if (lane == 31) base = atomicAdd(s_cnt, total);
-      base = __shfl_sync(0xffffffffu, base, 31);
-      unsigned int pos = base + incl - cnt;
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-#pragma unroll
-        for (int j = 0; j < kVec; ++j) {
-          if (mask & (1u << (u * kVec + j))) zr[pos++] = Ops<T>::get(r[u], j);
-        }
-      }
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------------
-// Pass-0 accumulators.
+// Per-element cores.
 // ---------------------------------------------------------------------------------
-template <typename T>
-struct StatsAcc {
-  using C = typename Ops<T>::C;
-  unsigned int nnan = 0, nneg = 0, npos = 0, nnz = 0, nfin = 0;
-  C mn, mx;
-  unsigned int cmn = 0, cmx = 0;
-  float sum = 0.f;     // sum of (x - x0) * sigma over finite x
-  float x0s = 0.f;     // x0 * sigma
-  float x0 = 0.f;      // float image of the shift
-  float sigma = 1.f;
-};
+// One element of a cutting-plane pass (Algorithm 1, step 1.2; the figure's Objective()):
+// lt += [x < t], le += [x <= t], S += [a < x < t] * (t - x) * sigma.
+__device__ __forceinline__ void core(float x, float a, float t, float nsig, float tsig, unsigned& lt,
+                                     unsigned& le, float& S) {
+  asm("{\n\t"
+      ".reg .pred p, q, r;\n\t"
+      ".reg .f32 d;\n\t"
+      "setp.lt.f32 p, %3, %5;\n\t"
+      "setp.le.f32 q, %3, %5;\n\t"
+      "setp.gt.and.f32 r, %3, %4, p;\n\t"
+      "fma.rn.f32 d, %3, %6, %7;\n\t"
+      "@p add.u32 %0, %0, 1;\n\t"
+      "@q add.u32 %1, %1, 1;\n\t"
+      "@r add.f32 %2, %2, d;\n\t"
+      "}"
+      : "+r"(lt), "+r"(le), "+f"(S)
+      : "f"(x), "f"(a), "f"(t), "f"(nsig), "f"(tsig));
+}
+// float64: comparisons on signed integer keys, the cost on the truncated float32 image.
+__device__ __forceinline__ void core(double xv, long long sa, long long st, float nsig, float tsig,
+                                     unsigned& lt, unsigned& le, float& S) {
+  const uint64_t u = (uint64_t)__double_as_longlong(xv);
+  const long long sx = (long long)skey_bits(u);
+  lt += (sx < st);
+  le += (sx <= st);
+  const bool in = (sx > sa) & (sx < st);
+  const float d = fmaf(f64_to_f32_trunc(u), nsig, tsig);
+  S += in ? d : 0.f;
+}
 
 template <typename T> __device__ __forceinline__ typename Ops<T>::C cmp_pos_inf();
 template <> __device__ __forceinline__ float cmp_pos_inf<float>() { return INFINITY; }
@@ -227,6 +145,139 @@ template <> __device__ __forceinline__ long long cmp_pos_inf<double>() { return 
 // value of a comparison key
 __device__ __forceinline__ float cmp_value(float c, float) { return c; }
 __device__ __forceinline__ double cmp_value(long long c, double) { return skey_value(c); }
+
+template <typename T> struct CmpOf;
+template <> struct CmpOf<float> {
+  static __device__ __forceinline__ float of(float v) { return v; }
+};
+template <> struct CmpOf<double> {
+  static __device__ __forceinline__ long long of(double v) { return (long long)skey(v); }
+};
+
+// Scalar head and tail of x handled by this thread (the first threads of CTA 0).
+template <typename T, typename Fn>
+__device__ __forceinline__ void stream_edges(const T* __restrict__ x, const Geometry<T>& g, Fn& f) {
+  const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (gtid < g.head) f(x[gtid]);
+  if (gtid < g.n - g.tail0) f(x[g.tail0 + gtid]);
+}
+
+// Streaming over this CTA's chunks of the 16-byte-vector body: chunk c = bid + j*grid
+// (reverse order when `rev`), thread t loads vectors t + u*kThreads (u < kVPT) of each,
+// with 128-bit streaming loads, all kVPT of them in flight before any is used.
+constexpr int kVPT = (int)(kChunkVecs / kThreads);
+
+template <typename T, typename Fn>
+__device__ __forceinline__ void stream_chunks(const T* __restrict__ x, const Geometry<T>& g, bool rev, Fn& f) {
+  using V = typename Ops<T>::V;
+  const V* xv = reinterpret_cast<const V*>(x + g.head);
+  const long long G = gridDim.x, bid = blockIdx.x;
+  const long long nch = chunk_count(g.nv);
+  const long long my = bid < nch ? (nch - 1 - bid) / G + 1 : 0;
+  for (long long j = 0; j < my; ++j) {
+    const long long c = bid + (rev ? my - 1 - j : j) * G;
+    const V* p = xv + c * kChunkVecs + threadIdx.x;
+    const long long lim = g.nv - c * kChunkVecs - threadIdx.x;   // vectors left from p on
+    if (lim > (long long)(kVPT - 1) * kThreads) {
+      V r[kVPT];
+#pragma unroll
+      for (int u = 0; u < kVPT; ++u) r[u] = load_stream(p + u * kThreads);
+#pragma unroll
+      for (int u = 0; u < kVPT; ++u) Ops<T>::each(r[u], f);
+    } else {
+      for (int u = 0; u < kVPT; ++u)
+        if ((long long)u * kThreads < lim) {
+          const V r = load_stream(p + u * kThreads);
+          Ops<T>::each(r, f);
+        }
+    }
+  }
+}
+
+// As stream_chunks, and every element with keep(element) is appended to `zr` (counter
+// *cnt in shared memory): one warp-wide prefix sum per chunk.
+template <typename T, typename Fn, typename Keep>
+__device__ __forceinline__ void stream_chunks_compact(const T* __restrict__ x, const Geometry<T>& g, bool rev,
+                                                      Fn& f, Keep& keep, T* __restrict__ zr,
+                                                      unsigned int* cnt) {
+  using V = typename Ops<T>::V;
+  constexpr int kVec = Ops<T>::kVec;
+  const int lane = threadIdx.x & 31;
+  const V* xv = reinterpret_cast<const V*>(x + g.head);
+  const long long G = gridDim.x, bid = blockIdx.x;
+  const long long nch = chunk_count(g.nv);
+  const long long my = bid < nch ? (nch - 1 - bid) / G + 1 : 0;
+  for (long long j = 0; j < my; ++j) {
+    const long long c = bid + (rev ? my - 1 - j : j) * G;
+    const V* p = xv + c * kChunkVecs + threadIdx.x;
+    const long long lim = g.nv - c * kChunkVecs - threadIdx.x;
+    V r[kVPT];
+#pragma unroll
+    for (int u = 0; u < kVPT; ++u)
+      if ((long long)u * kThreads < lim) r[u] = load_stream(p + u * kThreads);
+    unsigned int mask = 0, k = 0;
+#pragma unroll
+    for (int u = 0; u < kVPT; ++u) {
+      if ((long long)u * kThreads < lim) {
+        Ops<T>::each(r[u], f);
+#pragma unroll
+        for (int e = 0; e < kVec; ++e) {
+          const bool kk = keep(Ops<T>::get(r[u], e));
+          mask |= (kk ? 1u : 0u) << (u * kVec + e);
+          k += kk;
+        }
+      }
+    }
+    unsigned int incl = k;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total) {
+      unsigned int b0 = 0;
+      if (lane == 31) b0 = atomicAdd(cnt, total);
+      b0 = __shfl_sync(0xffffffffu, b0, 31);
+      unsigned int pos = b0 + incl - k;
+#pragma unroll
+      for (int u = 0; u < kVPT; ++u)
+#pragma unroll
+        for (int e = 0; e < kVec; ++e)
+          if (mask & (1u << (u * kVec + e))) zr[pos++] = Ops<T>::get(r[u], e);
+    }
+  }
+}
+
+// Sums up to 6 per-thread values over the CTA in one exchange (fixed order, so every
+// CTA that sums the same data gets the same bits).  Result valid in every thread.
+struct Sum6 {
+  unsigned long long u[5];
+  double d;
+};
+__device__ __forceinline__ Sum6 block_sum6(Sum6 v, Sum6* scratch /* [kWarps + 1] */) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) v.u[i] += __shfl_xor_sync(0xffffffffu, v.u[i], o);
+    v.d += __shfl_xor_sync(0xffffffffu, v.d, o);
+  }
+  __syncthreads();
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Sum6 r = scratch[0];
+    for (int i = 1; i < kWarps; ++i) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) r.u[q] += scratch[i].u[q];
+      r.d += scratch[i].d;
+    }
+    scratch[kWarps] = r;
+  }
+  __syncthreads();
+  return scratch[kWarps];
+}
 
 // ---------------------------------------------------------------------------------
 // The kernel.
@@ -237,7 +288,11 @@ struct BracketState {
   long long cle_a, clt_b, cle_b;
   double dF;
   float sigma;
-  int it, use_bisect, stalled, compact, phase;   // phase: 0 run, 1 done, 2 finish, 3 error
+  int it, use_bisect, stalled, compact;
+  int first;        // 1: the multiplicities of the extremes are still estimates
+  int phase;        // 0 run, 1 done, 2 finish, 3 NaN, 4 internal error
+  int how;          // GBS_HOW_* of a resolved result
+  long long clt_res;// #(x < result) for the sign of a zero result
   T result;
 };
 
@@ -260,18 +315,122 @@ __device__ __forceinline__ float cost_scale(double width, long long per_thread) 
   return ldexpf(1.f, e);
 }
 
+template <typename T> __device__ __forceinline__ bool is_neg_zero_bits(T v);
+template <> __device__ __forceinline__ bool is_neg_zero_bits<float>(float v) {
+  return __float_as_uint(v) == 0x80000000u;
+}
+template <> __device__ __forceinline__ bool is_neg_zero_bits<double>(double v) {
+  return (uint64_t)__double_as_longlong(v) == 0x8000000000000000ull;
+}
+
+// Grid totals of the pass partials in `slot` (identical in every CTA: fixed order).
+struct Totals {
+  unsigned long long c_lt, c_le, c_aux, c_aux2, c_reg;
+  double S;
+};
+__device__ __forceinline__ Totals grid_totals(const PassPartial* part, unsigned int G, Sum6* scratch) {
+  Sum6 v;
+  v.u[0] = v.u[1] = v.u[2] = v.u[3] = v.u[4] = 0;
+  v.d = 0.0;
+  for (unsigned int i = threadIdx.x; i < G; i += kThreads) {
+    const PassPartial* p = &part[i];
+    v.u[0] += __ldcg(&p->c_lt); v.u[1] += __ldcg(&p->c_le); v.u[2] += __ldcg(&p->c_aux);
+    v.u[3] += __ldcg(&p->c_aux2); v.u[4] += __ldcg(&p->c_reg); v.d += __ldcg(&p->S);
+  }
+  const Sum6 r = block_sum6(v, scratch);
+  Totals t;
+  t.c_lt = r.u[0]; t.c_le = r.u[1]; t.c_aux = r.u[2]; t.c_aux2 = r.u[3]; t.c_reg = r.u[4]; t.S = r.d;
+  return t;
+}
+
+// Per-thread accumulators of one cutting-plane pass.
+struct PassAcc {
+  unsigned int lt, le, xa, xb;
+  float S;
+};
+
+// One streaming pass over x at the iterate t (Algorithm 1, step 1.2).  FIRST also counts
+// #(x <= a) and #(x < b); COMPACT also appends the elements of (a, b] to region `zr`.
+// Kept out of line so that its registers are allocated apart from the kernel's control.
+template <typename T, bool FIRST, bool COMPACT>
+__device__ __noinline__ bool cut_pass(const T* __restrict__ x, const Geometry<T>& geo, bool rev,
+                                      typename Ops<T>::C ca, typename Ops<T>::C ct, typename Ops<T>::C cb,
+                                      float nsig, float tsig, T* __restrict__ zr, unsigned int* s_cnt,
+                                      PassAcc& acc) {
+  using C = typename Ops<T>::C;
+  using V = typename Ops<T>::V;
+  unsigned int lt = 0, le = 0, xa = 0, xb = 0;
+  float S = 0.f;
+  auto f = [&](T v) {
+    core(v, ca, ct, nsig, tsig, lt, le, S);
+    if (FIRST) {
+      const C cv = CmpOf<T>::of(v);
+      xa += (cv <= ca);
+      xb += (cv < cb);
+    }
+  };
+  if (COMPACT) {
+    auto keep = [&](T v) { const C cv = CmpOf<T>::of(v); return (cv > ca) & (cv <= cb); };
+    if ((long long)blockIdx.x * kThreads + threadIdx.x < geo.head + (geo.n - geo.tail0)) {
+      auto fk = [&](T v) {
+        f(v);
+        if (keep(v)) zr[atomicAdd(s_cnt, 1u)] = v;
+      };
+      stream_edges(x, geo, fk);
+    }
+    stream_chunks_compact(x, geo, rev, f, keep, zr, s_cnt);
+  } else {
+    stream_edges(x, geo, f);
+    stream_chunks(x, geo, rev, f);
+  }
+  acc.lt = lt; acc.le = le; acc.xa = xa; acc.xb = xb; acc.S = S;
+  return true;
+}
+
+// Per-thread accumulators of pass 0.
 template <typename T>
-__device__ __forceinline__ T zero_signed(T v, long long k, long long clt_v, long long nnegzero) {
-  if (v == T(0)) return (k - clt_v) <= nnegzero ? T(-0.0) : T(0.0);
-  return v;
+struct StatsAcc {
+  typename Ops<T>::C mn, mx;
+  unsigned int nnan, nneg, npos, seen;
+  float sum;   // sum over finite x of (x - x0) * sigma
+};
+
+// Pass 0 (Sec. 3, step 0): finite extremes and sum; NaN and infinities take a rare branch.
+template <typename T>
+__device__ __noinline__ bool stats_pass(const T* __restrict__ x, const Geometry<T>& geo, float sig,
+                                        float x0s, StatsAcc<T>& out) {
+  using C = typename Ops<T>::C;
+  using V = typename Ops<T>::V;
+  C mn = cmp_pos_inf<T>(), mx = -cmp_pos_inf<T>();
+  unsigned int nnan = 0, nneg = 0, npos = 0, seen = 0;
+  float sum = 0.f;
+  auto f = [&](T v) {
+    ++seen;
+    if (Ops<T>::is_finite(v)) {
+      const C cv = CmpOf<T>::of(v);
+      mn = cv < mn ? cv : mn;
+      mx = cv > mx ? cv : mx;
+      sum += fmaf(Ops<T>::img(v), sig, -x0s);
+    } else {
+      nnan += Ops<T>::is_nan(v);
+      nneg += Ops<T>::is_neginf(v);
+      npos += Ops<T>::is_posinf(v);
+    }
+  };
+  stream_edges(x, geo, f);
+  stream_chunks(x, geo, false, f);
+  out.mn = mn; out.mx = mx; out.nnan = nnan; out.nneg = nneg; out.npos = npos; out.seen = seen; out.sum = sum;
+  return true;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
   using C = typename Ops<T>::C;
   using U = typename KeyOf<T>::U;
+  using V = typename Ops<T>::V;
   constexpr int W = KeyOf<T>::kBitsW;
   const int tid = threadIdx.x;
+  const int lane = tid & 31;
   const int bid = blockIdx.x;
   const unsigned int G = gridDim.x;
   const long long n = A.n, k = A.k;
@@ -281,19 +440,23 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
   __shared__ BracketState<T> s_br;
   __shared__ unsigned int s_zcnt;
   __shared__ unsigned int s_hist[kBins];
-  __shared__ unsigned long long s_off[kMaxGrid + 1];
-  __shared__ unsigned long long s_tot[8];
   __shared__ unsigned long long s_tns[72];
   __shared__ int s_ntns;
   __shared__ long long s_pops[kMaxIt];
+  __shared__ unsigned long long s_tstream[kMaxIt];
   __shared__ double s_iter[kMaxIt];
   __shared__ int s_nk, s_nb;
   __shared__ U s_prefix;
   __shared__ int s_known;
   __shared__ unsigned long long s_rank;
+  __shared__ StatsPartial s_st;
+  __shared__ Sum6 s_sum6[kWarps + 1];
+
+  __shared__ unsigned long long s_off[kMaxGrid + 1];   // region offsets of the finish
 
   const Geometry<T> geo(A.x, n);
-  const long long per_thread = (geo.nv + (long long)G * kThreads - 1) / ((long long)G * kThreads) * Ops<T>::kVec + 2 * Ops<T>::kVec;
+  const long long nch = chunk_count(geo.nv);
+  const long long per_thread = per_thread_bound(nch, G, Ops<T>::kVec);
 
   if (tid == 0) { s_ntns = 0; s_nk = 0; s_nb = 0; }
   if (bid == 0) {   // zero the radix histograms (visible after the first barrier)
@@ -304,170 +467,170 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
   };
   stamp();
 
+  // Counting pass over x for three predicates: [x <= lo], [x < hi], [x is -0].  Used for
+  // the multiplicities of the extremes (array statistics) and the sign of a zero result.
+  auto aux_pass = [&](T lo, T hi, unsigned long long* o_le, unsigned long long* o_lt,
+                      unsigned long long* o_nz) -> bool {
+    const C cl = CmpOf<T>::of(lo), ch = CmpOf<T>::of(hi);
+    unsigned int a0 = 0, a1 = 0, a2 = 0;
+    auto f = [&](T v) {
+      const C cv = CmpOf<T>::of(v);
+      a0 += (cv <= cl);
+      a1 += (cv < ch);
+      a2 += is_neg_zero_bits<T>(v);
+    };
+    stream_edges(A.x, geo, f);
+    stream_chunks(A.x, geo, false, f);
+    PassPartial pp;
+    pp.c_lt = block_sum<unsigned long long>(a0, s_u64);
+    pp.c_le = block_sum<unsigned long long>(a1, s_u64);
+    pp.c_aux = block_sum<unsigned long long>(a2, s_u64);
+    pp.c_aux2 = 0; pp.c_reg = 0; pp.S = 0.0;
+    if (tid == 0) A.part[bid] = pp;
+    if (!grid_sync(A.ctrl, G)) return false;
+    stamp();
+    Totals t = grid_totals(A.part, G, s_sum6);
+    *o_le = t.c_lt; *o_lt = t.c_le; *o_nz = t.c_aux;
+    return true;
+  };
+
   if (A.mode == kModeEval) {
     // ---------------- one fused pass at (a, t) ----------------
     const T a = Ops<T>::from_double(A.a_eval), t = Ops<T>::from_double(A.t_eval);
-    const C ca = Ops<T>::cmp(a), ct = Ops<T>::cmp(t);
+    const C ca = CmpOf<T>::of(a), ct = CmpOf<T>::of(t);
     const float sig = cost_scale((double)Ops<T>::img(t) - (double)Ops<T>::img(a), per_thread);
     const float tsig = Ops<T>::img(t) * sig;
     unsigned int lt = 0, le = 0, lea = 0;
     float S = 0.f;
-    auto fn = [&](T xv) {
-      C cx = Ops<T>::cmp(xv);
-      lt += (cx < ct);
-      le += (cx <= ct);
-      lea += (cx <= ca);
-      bool in = (cx > ca) & (cx < ct);
-      float d = fmaf(Ops<T>::img(xv), -sig, tsig);
-      S += in ? d : 0.f;
+    auto f = [&](T v) {
+      core(v, ca, ct, -sig, tsig, lt, le, S);
+      lea += (CmpOf<T>::of(v) <= ca);
     };
-    stream_x(A.x, geo, false, fn);
-    unsigned long long blt = block_sum<unsigned long long>(lt, s_u64);
-    unsigned long long ble = block_sum<unsigned long long>(le, s_u64);
-    unsigned long long blea = block_sum<unsigned long long>(lea, s_u64);
-    double bS = block_sum<double>((double)S, s_f64);
-    if (tid == 0) {
-      PassPartial p;
-      p.c_lt = blt; p.c_le = ble; p.c_aux = blea; p.S = bS;
-      A.part[bid] = p;
-    }
+    stream_edges(A.x, geo, f);
+    stream_chunks(A.x, geo, false, f);
+    PassPartial pp;
+    pp.c_lt = block_sum<unsigned long long>(lt, s_u64);
+    pp.c_le = block_sum<unsigned long long>(le, s_u64);
+    pp.c_aux = block_sum<unsigned long long>(lea, s_u64);
+    pp.c_aux2 = 0; pp.c_reg = 0;
+    pp.S = block_sum<double>((double)S, s_f64);
+    if (tid == 0) A.part[bid] = pp;
     if (!grid_sync(A.ctrl, G)) return;
-    if (bid == 0) {
-      unsigned long long l0 = 0, l1 = 0, l2 = 0;
-      double dS = 0.0;
-      for (unsigned int i = tid; i < G; i += kThreads) {
-        l0 += __ldcg(&A.part[i].c_lt); l1 += __ldcg(&A.part[i].c_le); l2 += __ldcg(&A.part[i].c_aux);
-        dS += __ldcg(&A.part[i].S);
-      }
-      l0 = block_sum<unsigned long long>(l0, s_u64);
-      l1 = block_sum<unsigned long long>(l1, s_u64);
-      l2 = block_sum<unsigned long long>(l2, s_u64);
-      dS = block_sum<double>(dS, s_f64);
-      if (tid == 0) {
-        gbs_cost_eval e;
-        e.c_lt_t = (long long)l0; e.c_le_t = (long long)l1; e.c_le_a = (long long)l2; e.pad = 0;
-        e.S = dS / (double)sig;
-        e.dphi = ((double)e.c_le_a - (double)k + 0.5) * ((double)t - (double)a) + e.S;
-        *A.eval_out = e;
-      }
+    Totals tt = grid_totals(A.part, G, s_sum6);
+    if (bid == 0 && tid == 0) {
+      gbs_cost_eval e;
+      e.c_lt_t = (long long)tt.c_lt; e.c_le_t = (long long)tt.c_le; e.c_le_a = (long long)tt.c_aux; e.pad = 0;
+      e.S = tt.S / (double)sig;
+      e.dphi = ((double)e.c_le_a - (double)k + 0.5) * ((double)t - (double)a) + e.S;
+      *A.eval_out = e;
     }
     return;
   }
 
-  // ---------------- pass 0: extremes, counts, sum (Sec. 3, step 0) ----------------
+  // ---------------- pass 0: finite extremes, sum, non-finite counts (Sec. 3, step 0) ----------------
   {
-    StatsAcc<T> acc;
-    acc.mn = cmp_pos_inf<T>();
-    acc.mx = -cmp_pos_inf<T>();
-    acc.sigma = A.sigma_stats;
+    const float sig = A.sigma_stats;
+    float x0 = 0.f;   // per-thread shift of the float32 sum
     {
       const long long gtid = (long long)bid * kThreads + tid;
-      long long i0 = gtid < geo.head ? gtid : geo.head + gtid * Ops<T>::kVec;
+      const long long i0 = gtid < geo.head ? gtid : geo.head + gtid * Ops<T>::kVec;
       if (i0 < n) {
-        T e = A.x[i0];
-        if (Ops<T>::is_finite(e)) acc.x0 = Ops<T>::img(e);
+        const T e = A.x[i0];
+        if (Ops<T>::is_finite(e)) x0 = Ops<T>::img(e);
       }
-      acc.x0s = acc.x0 * acc.sigma;
     }
-    auto fn = [&](T xv) {
-      acc.nnan += Ops<T>::is_nan(xv);
-      acc.nneg += Ops<T>::is_neginf(xv);
-      acc.npos += Ops<T>::is_posinf(xv);
-      acc.nnz += Ops<T>::is_negzero(xv);
-      const bool fin = Ops<T>::is_finite(xv);
-      acc.nfin += fin;
-      C cx = Ops<T>::cmp(xv);
-      C cm = fin ? cx : acc.mn;
-      acc.cmn = (cm < acc.mn) ? 0u : acc.cmn;
-      acc.mn = (cm < acc.mn) ? cm : acc.mn;
-      acc.cmn += (fin && cm == acc.mn);
-      C cM = fin ? cx : acc.mx;
-      acc.cmx = (cM > acc.mx) ? 0u : acc.cmx;
-      acc.mx = (cM > acc.mx) ? cM : acc.mx;
-      acc.cmx += (fin && cM == acc.mx);
-      float d = fmaf(Ops<T>::img(xv), acc.sigma, -acc.x0s);
-      acc.sum += fin ? d : 0.f;
-    };
-    stream_x(A.x, geo, false, fn);
-    // block reduction of (min, count) and (max, count): smem pairs per warp
+    const float x0s = x0 * sig;
+    StatsAcc<T> sa;
+    if (!stats_pass<T>(A.x, geo, sig, x0s, sa)) return;
+    C mn = sa.mn, mx = sa.mx;
+    const unsigned int nnan = sa.nnan, nneg = sa.nneg, npos = sa.npos, seen = sa.seen;
+    const float sum = sa.sum;
     __shared__ C s_m[kWarps], s_M[kWarps];
-    __shared__ unsigned long long s_cm[kWarps], s_cM[kWarps];
-    C mn = acc.mn, mx = acc.mx;
-    unsigned long long cmn = acc.cmn, cmx = acc.cmx;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      C omn = __shfl_xor_sync(0xffffffffu, mn, o);
-      unsigned long long ocm = __shfl_xor_sync(0xffffffffu, cmn, o);
-      C omx = __shfl_xor_sync(0xffffffffu, mx, o);
-      unsigned long long ocM = __shfl_xor_sync(0xffffffffu, cmx, o);
-      cmn = omn < mn ? ocm : (omn == mn ? cmn + ocm : cmn);
+      const C omn = __shfl_xor_sync(0xffffffffu, mn, o);
+      const C omx = __shfl_xor_sync(0xffffffffu, mx, o);
       mn = omn < mn ? omn : mn;
-      cmx = omx > mx ? ocM : (omx == mx ? cmx + ocM : cmx);
       mx = omx > mx ? omx : mx;
     }
-    if ((tid & 31) == 0) { s_m[tid >> 5] = mn; s_M[tid >> 5] = mx; s_cm[tid >> 5] = cmn; s_cM[tid >> 5] = cmx; }
-    unsigned long long b_nan = block_sum<unsigned long long>(acc.nnan, s_u64);
-    unsigned long long b_neg = block_sum<unsigned long long>(acc.nneg, s_u64);
-    unsigned long long b_pos = block_sum<unsigned long long>(acc.npos, s_u64);
-    unsigned long long b_nz = block_sum<unsigned long long>(acc.nnz, s_u64);
-    unsigned long long b_fin = block_sum<unsigned long long>(acc.nfin, s_u64);
-    double own = (double)acc.sum / (double)acc.sigma + (double)acc.nfin * (double)acc.x0;
-    double b_sum = block_sum<double>(own, s_f64);
+    if (lane == 0) { s_m[tid >> 5] = mn; s_M[tid >> 5] = mx; }
+    const unsigned int nfin = seen - nnan - nneg - npos;
+    const unsigned long long b_nan = block_sum<unsigned long long>(nnan, s_u64);
+    const unsigned long long b_neg = block_sum<unsigned long long>(nneg, s_u64);
+    const unsigned long long b_pos = block_sum<unsigned long long>(npos, s_u64);
+    const unsigned long long b_fin = block_sum<unsigned long long>(nfin, s_u64);
+    const double own = (double)sum / (double)sig + (double)nfin * (double)x0;
+    const double b_sum = block_sum<double>(own, s_f64);
     if (tid == 0) {
       C bm = s_m[0], bM = s_M[0];
-      unsigned long long bcm = s_cm[0], bcM = s_cM[0];
       for (int w = 1; w < kWarps; ++w) {
-        bcm = s_m[w] < bm ? s_cm[w] : (s_m[w] == bm ? bcm + s_cm[w] : bcm);
         bm = s_m[w] < bm ? s_m[w] : bm;
-        bcM = s_M[w] > bM ? s_cM[w] : (s_M[w] == bM ? bcM + s_cM[w] : bcM);
         bM = s_M[w] > bM ? s_M[w] : bM;
       }
       StatsPartial sp;
-      sp.n_nan = b_nan; sp.n_neginf = b_neg; sp.n_posinf = b_pos; sp.n_negzero = b_nz; sp.n_finite = b_fin;
+      sp.n_nan = b_nan; sp.n_neginf = b_neg; sp.n_posinf = b_pos; sp.n_negzero = 0; sp.n_finite = b_fin;
       sp.mn = (double)cmp_value(bm, T()); sp.mx = (double)cmp_value(bM, T());
-      sp.c_mn = bcm; sp.c_mx = bcM; sp.sum = b_sum;
+      sp.c_mn = 0; sp.c_mx = 0; sp.sum = b_sum;
       A.spart[bid] = sp;
     }
   }
   if (!grid_sync(A.ctrl, G)) return;
   stamp();
 
-  // every CTA: reduce the G pass-0 partials in the same order
-  __shared__ StatsPartial s_st;
-  if (tid == 0) {
-    StatsPartial t;
-    t.n_nan = t.n_neginf = t.n_posinf = t.n_negzero = t.n_finite = 0;
-    t.c_mn = t.c_mx = 0;
-    t.mn = INFINITY; t.mx = -INFINITY; t.sum = 0.0;
-    for (unsigned int i = 0; i < G; ++i) {
+  // every CTA: reduce the G pass-0 partials in the same order (thread i takes partials
+  // i, i + kThreads, ...; then a fixed warp / block tree)
+  {
+    Sum6 v;
+    v.u[0] = v.u[1] = v.u[2] = v.u[3] = v.u[4] = 0;
+    v.d = 0.0;
+    double m = INFINITY, M = -INFINITY;
+    for (unsigned int i = tid; i < G; i += kThreads) {
       const StatsPartial* p = &A.spart[i];
-      t.n_nan += __ldcg(&p->n_nan); t.n_neginf += __ldcg(&p->n_neginf);
-      t.n_posinf += __ldcg(&p->n_posinf); t.n_negzero += __ldcg(&p->n_negzero);
-      t.n_finite += __ldcg(&p->n_finite);
-      double m = __ldcg(&p->mn), M = __ldcg(&p->mx);
-      unsigned long long cm = __ldcg(&p->c_mn), cM = __ldcg(&p->c_mx);
-      t.c_mn = m < t.mn ? cm : (m == t.mn ? t.c_mn + cm : t.c_mn);
-      t.mn = m < t.mn ? m : t.mn;
-      t.c_mx = M > t.mx ? cM : (M == t.mx ? t.c_mx + cM : t.c_mx);
-      t.mx = M > t.mx ? M : t.mx;
-      t.sum += __ldcg(&p->sum);
+      v.u[0] += __ldcg(&p->n_nan); v.u[1] += __ldcg(&p->n_neginf);
+      v.u[2] += __ldcg(&p->n_posinf); v.u[3] += __ldcg(&p->n_finite);
+      const double pm = __ldcg(&p->mn), pM = __ldcg(&p->mx);
+      m = pm < m ? pm : m;
+      M = pM > M ? pM : M;
+      v.d += __ldcg(&p->sum);
     }
-    s_st = t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double om = __shfl_xor_sync(0xffffffffu, m, o), oM = __shfl_xor_sync(0xffffffffu, M, o);
+      m = om < m ? om : m;
+      M = oM > M ? oM : M;
+    }
+    __shared__ double s_mm[kWarps], s_MM[kWarps];
+    if (lane == 0) { s_mm[tid >> 5] = m; s_MM[tid >> 5] = M; }
+    const Sum6 r = block_sum6(v, s_sum6);   // its barriers also publish s_mm / s_MM
+    if (tid == 0) {
+      StatsPartial t;
+      t.n_nan = r.u[0]; t.n_neginf = r.u[1]; t.n_posinf = r.u[2]; t.n_finite = r.u[3];
+      t.n_negzero = 0; t.c_mn = t.c_mx = 0; t.sum = r.d;
+      t.mn = s_mm[0]; t.mx = s_MM[0];
+      for (int w = 1; w < kWarps; ++w) {
+        t.mn = s_mm[w] < t.mn ? s_mm[w] : t.mn;
+        t.mx = s_MM[w] > t.mx ? s_MM[w] : t.mx;
+      }
+      s_st = t;
+    }
   }
   __syncthreads();
-  const StatsPartial st = s_st;
+  const StatsPartial& st = s_st;     // read from shared memory where needed
+  const long long nneg = (long long)st.n_neginf, npos = (long long)st.n_posinf;
 
   if (A.mode == kModeStats) {
+    // multiplicities of the extremes and the -0 count need one more pass
+    const bool any = st.n_finite > 0;
+    unsigned long long cle = 0, clt = 0, nz = 0;
+    if (!aux_pass((T)(any ? st.mn : 0.0), (T)(any ? st.mx : 0.0), &cle, &clt, &nz)) return;
     if (bid == 0 && tid == 0) {
       gbs_array_stats o;
       o.n = n;
-      o.n_nan = (long long)st.n_nan; o.n_neginf = (long long)st.n_neginf;
-      o.n_posinf = (long long)st.n_posinf; o.n_negzero = (long long)st.n_negzero;
-      o.n_finite = (long long)st.n_finite;
-      const bool any = st.n_finite > 0;
+      o.n_nan = (long long)st.n_nan; o.n_neginf = nneg; o.n_posinf = npos;
+      o.n_negzero = (long long)nz; o.n_finite = (long long)st.n_finite;
       o.min = any ? st.mn : 0.0; o.max = any ? st.mx : 0.0;
-      o.c_le_min = any ? (long long)(st.n_neginf + st.c_mn) : 0;
-      o.c_lt_max = any ? (long long)(n - st.n_posinf - st.c_mx - st.n_nan) : 0;
+      o.c_le_min = any ? (long long)cle : 0;
+      o.c_lt_max = any ? (long long)clt - (long long)st.n_nan : 0;
       o.sum = st.sum;
       *A.stats_out = o;
     }
@@ -477,31 +640,30 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
   // ---------------- trivial resolution and the starting bracket ----------------
   if (tid == 0) {
     BracketState<T> br;
-    br.it = 0; br.use_bisect = 0; br.stalled = 0; br.compact = 0; br.phase = 0;
+    br.it = 0; br.use_bisect = 0; br.stalled = 0; br.compact = 0; br.phase = 0; br.first = 0;
+    br.how = GBS_HOW_NONE; br.clt_res = -1;
     br.result = T(0); br.sigma = 1.f;
-    const long long nneg = (long long)st.n_neginf, npos = (long long)st.n_posinf;
-    const long long nnz = (long long)st.n_negzero;
+    br.a = T(0); br.b = T(0); br.t = T(0); br.cle_a = 0; br.clt_b = 0; br.cle_b = 0; br.dF = 0.0;
     if (st.n_nan > 0) {
       br.phase = 3;
       br.result = T(NAN);
     } else if (k <= nneg) {
-      br.phase = 1; br.result = T(-INFINITY); br.it = GBS_HOW_NEGINF;
+      br.phase = 1; br.result = T(-INFINITY); br.how = GBS_HOW_NEGINF;
     } else if (k > n - npos) {
-      br.phase = 1; br.result = T(INFINITY); br.it = GBS_HOW_POSINF;
+      br.phase = 1; br.result = T(INFINITY); br.how = GBS_HOW_POSINF;
     } else {
       const T m = (T)st.mn, M = (T)st.mx;
-      const long long cle_m = nneg + (long long)st.c_mn;
-      const long long clt_M = n - npos - (long long)st.c_mx;
-      if (cle_m >= k) {
-        br.phase = 1; br.result = zero_signed<T>(m, k, nneg, nnz); br.it = GBS_HOW_MIN;
-      } else if (clt_M < k) {
-        br.phase = 1; br.result = zero_signed<T>(M, k, clt_M, nnz); br.it = GBS_HOW_MAX;
+      if (!(m < M)) {             // every finite element has the same value
+        br.phase = 1; br.result = m; br.how = GBS_HOW_MIN; br.clt_res = nneg;
       } else {
+        // Multiplicities of the extremes are not known yet: start from the paper's
+        // closed forms for unique extremes (Sec. 3, step 0); the first pass counts
+        // #(x <= m) and #(x < M) and corrects the state.
         br.a = m; br.b = M;
-        br.cle_a = cle_m; br.clt_b = clt_M; br.cle_b = n - npos;
-        const double gL = (double)(cle_m - k) + 0.5;
-        const double inner = st.sum - (double)st.c_mn * (double)m - (double)st.c_mx * (double)M;
-        br.dF = gL * ((double)M - (double)m) + (double)(clt_M - cle_m) * (double)M - inner;
+        br.cle_a = nneg + 1; br.clt_b = n - npos - 1; br.cle_b = n - npos; br.first = 1;
+        const double gL = (double)(br.cle_a - k) + 0.5;
+        const double inner = st.sum - (double)m - (double)M;
+        br.dF = gL * ((double)M - (double)m) + (double)(br.clt_b - br.cle_a) * (double)M - inner;
       }
     }
     s_br = br;
@@ -519,8 +681,8 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
       const double gR = (double)(br.clt_b - k) + 0.5;
       T t;
       if (br.use_bisect) {
-        U ka = ukey(br.a), kb = ukey(br.b);
-        U mid = ka + (kb - ka) / 2;
+        const U ka = ukey(br.a), kb = ukey(br.b);
+        const U mid = ka + (kb - ka) / 2;
         t = inside<T>(ukey_value(mid, T()), br.a, br.b);
         if (bid == 0) s_nb++;
       } else {
@@ -534,78 +696,84 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
       s_br = br;
     }
     __syncthreads();
-    const BracketState<T> br = s_br;
-    const C ca = Ops<T>::cmp(br.a), ct = Ops<T>::cmp(br.t), cb = Ops<T>::cmp(br.b);
-    const float sig = br.sigma;
-    const float tsig = Ops<T>::img(br.t) * sig;
-    unsigned int lt = 0, le = 0;
-    float S = 0.f;
-    auto fn = [&](T xv) {     // step 1.2: the fused cost + count evaluation
-      C cx = Ops<T>::cmp(xv);
-      lt += (cx < ct);
-      le += (cx <= ct);
-      bool in = (cx > ca) & (cx < ct);
-      float d = fmaf(Ops<T>::img(xv), -sig, tsig);
-      S += in ? d : 0.f;
-    };
+    const C ca = CmpOf<T>::of(s_br.a), ct = CmpOf<T>::of(s_br.t), cb = CmpOf<T>::of(s_br.b);
+    const float nsig = -s_br.sigma;
+    const float tsig = Ops<T>::img(s_br.t) * s_br.sigma;
+    const int first = s_br.first, compact = s_br.compact;
     const bool rev = (pass & 1) == 0;   // pass 0 ran forward
-    if (br.compact) {
-      if (tid == 0) s_zcnt = 0;
-      __syncthreads();
-      auto keep = [&](T xv) { C cx = Ops<T>::cmp(xv); return (cx > ca) & (cx <= cb); };
-      stream_x_compact(A.x, geo, rev, fn, keep, A.z + (long long)bid * A.region_cap, &s_zcnt);
+    if (tid == 0) s_zcnt = 0;
+    __syncthreads();
+    PassAcc acc;
+    T* zr = A.z + region_start(bid, nch, G, Ops<T>::kVec);
+    bool ok;
+    if (first) {
+      if (compact) ok = cut_pass<T, true, true>(A.x, geo, rev, ca, ct, cb, nsig, tsig, zr, &s_zcnt, acc);
+      else ok = cut_pass<T, true, false>(A.x, geo, rev, ca, ct, cb, nsig, tsig, zr, &s_zcnt, acc);
     } else {
-      stream_x(A.x, geo, rev, fn);
+      if (compact) ok = cut_pass<T, false, true>(A.x, geo, rev, ca, ct, cb, nsig, tsig, zr, &s_zcnt, acc);
+      else ok = cut_pass<T, false, false>(A.x, geo, rev, ca, ct, cb, nsig, tsig, zr, &s_zcnt, acc);
     }
-    unsigned long long blt = block_sum<unsigned long long>(lt, s_u64);
-    unsigned long long ble = block_sum<unsigned long long>(le, s_u64);
-    double bS = block_sum<double>((double)S, s_f64);
+    if (!ok) return;
+    if (bid == 0 && tid == 0 && pass < kMaxIt) s_tstream[pass] = globaltimer();
+    const unsigned int lt = acc.lt, le = acc.le, xa = acc.xa, xb = acc.xb;
+    const float S = acc.S;
+    __syncthreads();   // every append to this CTA's region is done
+    Sum6 v6;
+    v6.u[0] = lt; v6.u[1] = le; v6.u[2] = xa; v6.u[3] = xb;
+    v6.u[4] = (compact && tid == 0) ? s_zcnt : 0u;   // the CTA's count, once
+    v6.d = (double)S;
+    const Sum6 b6 = block_sum6(v6, s_sum6);
+    PassPartial pp;
+    pp.c_lt = b6.u[0]; pp.c_le = b6.u[1]; pp.c_aux = b6.u[2]; pp.c_aux2 = b6.u[3]; pp.c_reg = b6.u[4];
+    pp.S = b6.d;
     const int slot = pass & 1;
-    if (tid == 0) {
-      PassPartial p;
-      p.c_lt = blt; p.c_le = ble; p.c_aux = br.compact ? s_zcnt : 0; p.S = bS;
-      A.part[slot * G + bid] = p;
-    }
+    if (tid == 0) A.part[slot * G + bid] = pp;
     if (!grid_sync(A.ctrl, G)) return;
     stamp();
-    // deterministic grid totals (thread i takes partials i, i+B, ...; then block_sum)
-    unsigned long long l0 = 0, l1 = 0, l2 = 0;
-    double dS = 0.0;
-    for (unsigned int i = tid; i < G; i += kThreads) {
-      const PassPartial* p = &A.part[slot * G + i];
-      l0 += __ldcg(&p->c_lt); l1 += __ldcg(&p->c_le); l2 += __ldcg(&p->c_aux); dS += __ldcg(&p->S);
-    }
-    l0 = block_sum<unsigned long long>(l0, s_u64);
-    l1 = block_sum<unsigned long long>(l1, s_u64);
-    l2 = block_sum<unsigned long long>(l2, s_u64);
-    dS = block_sum<double>(dS, s_f64);
+    const Totals tt = grid_totals(A.part + slot * G, G, s_sum6);
     if (tid == 0) {   // steps 1.3-1.4
+      const BracketState<T> br = s_br;
       BracketState<T> nb = br;
-      const long long clt = (long long)l0, cle = (long long)l1;
-      const long long pop = br.cle_b - br.cle_a;
+      const long long clt = (long long)tt.c_lt, cle = (long long)tt.c_le;
       if (bid == 0 && br.it < kMaxIt) s_iter[br.it] = (double)br.t;
-      if (clt < k && k <= cle) {
-        nb.phase = 1;
-        nb.result = zero_signed<T>(br.t, k, clt, (long long)st.n_negzero);
-        if (bid == 0 && br.it < kMaxIt) s_pops[br.it] = 0;
-        nb.it = br.it + 1;
-      } else {
-        const double gL = (double)(br.cle_a - k) + 0.5;
-        const double dphi = gL * ((double)br.t - (double)br.a) + dS / (double)sig;
-        if (cle < k) {
-          nb.a = br.t; nb.cle_a = cle; nb.dF = br.dF - dphi;
+      nb.it = br.it + 1;
+      bool resolved = false;
+      if (br.first) {
+        const long long cle_m = (long long)tt.c_aux, clt_M = (long long)tt.c_aux2;
+        nb.first = 0;
+        if (cle_m >= k) {
+          nb.phase = 1; nb.result = br.a; nb.how = GBS_HOW_MIN; nb.clt_res = nneg; resolved = true;
+        } else if (clt_M < k) {
+          nb.phase = 1; nb.result = br.b; nb.how = GBS_HOW_MAX; nb.clt_res = clt_M; resolved = true;
         } else {
-          nb.b = br.t; nb.clt_b = clt; nb.cle_b = cle; nb.dF = dphi;
+          nb.cle_a = cle_m; nb.clt_b = clt_M;
+          const double cmn = (double)(cle_m - nneg), cmx = (double)(n - npos - clt_M);
+          const double gL = (double)(cle_m - k) + 0.5;
+          const double inner = st.sum - cmn * (double)br.a - cmx * (double)br.b;
+          nb.dF = gL * ((double)br.b - (double)br.a) + (double)(clt_M - cle_m) * (double)br.b - inner;
         }
-        const long long npop = nb.cle_b - nb.cle_a;
-        if (bid == 0 && br.it < kMaxIt) s_pops[br.it] = npop;
-        nb.use_bisect = (!br.use_bisect) && ((double)npop > 0.75 * (double)pop);
-        nb.stalled = ((double)npop > 0.875 * (double)pop) ? br.stalled + 1 : 0;
-        nb.it = br.it + 1;
-        if (br.compact) {
-          nb.phase = 2;
-          s_tot[0] = l2;   // compacted elements
-          if ((long long)l2 != pop) { nb.phase = 4; }
+        if (resolved && bid == 0 && br.it < kMaxIt) s_pops[br.it] = 0;
+      }
+      if (!resolved) {
+        const long long pop = nb.cle_b - nb.cle_a;
+        if (clt < k && k <= cle) {
+          nb.phase = 1; nb.result = br.t; nb.how = GBS_HOW_HIT; nb.clt_res = clt;
+          if (bid == 0 && br.it < kMaxIt) s_pops[br.it] = 0;
+        } else {
+          const double gL = (double)(nb.cle_a - k) + 0.5;
+          const double dphi = gL * ((double)br.t - (double)br.a) + tt.S / (double)br.sigma;
+          if (cle < k) {
+            nb.a = br.t; nb.cle_a = cle; nb.dF = nb.dF - dphi;
+          } else {
+            nb.b = br.t; nb.clt_b = clt; nb.cle_b = cle; nb.dF = dphi;
+          }
+          const long long npop = nb.cle_b - nb.cle_a;
+          if (bid == 0 && br.it < kMaxIt) s_pops[br.it] = npop;
+          nb.use_bisect = (!br.use_bisect) && ((double)npop > 0.75 * (double)pop);
+          nb.stalled = ((double)npop > 0.875 * (double)pop) ? br.stalled + 1 : 0;
+          if (br.compact) {
+            nb.phase = ((long long)tt.c_reg == pop) ? 2 : 4;
+          }
         }
       }
       s_br = nb;
@@ -620,13 +788,14 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     return;
   }
   int rounds = 0;
+  int extra = 0;
   T result = fin.result;
   long long fpop = 0;
   if (fin.phase == 2) {
     // ---------------- exact finish: radix select inside (a, b] ----------------
     const int slot = (pass - 1) & 1;
     // region offsets (exclusive prefix of the per-CTA compaction counts)
-    for (unsigned int i = tid; i < G; i += kThreads) s_off[i + 1] = __ldcg(&A.part[slot * G + i].c_aux);
+    for (unsigned int i = tid; i < G; i += kThreads) s_off[i + 1] = __ldcg(&A.part[slot * G + i].c_reg);
     if (tid == 0) s_off[0] = 0;
     __syncthreads();
     if (tid == 0) {
@@ -645,20 +814,20 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     fpop = (long long)P;
     const unsigned long long lo_i = P * bid / G, hi_i = P * (bid + 1) / G;
     const T fa = fin.a, fb = fin.b;
+    const int warp = tid >> 5;
     while (s_known < W) {
       const int known = s_known;
       const U prefix = s_prefix;
       const int nbits = (W - known) < kDigitBits ? (W - known) : kDigitBits;
       const int sh = W - known - nbits;
-      const U dmask = (U)((1u << nbits) - 1u);
+      const unsigned int dmask = (1u << nbits) - 1u;
       for (int i = tid; i < kBins; i += kThreads) s_hist[i] = 0;
       __syncthreads();
-      // this CTA's slice of the concatenated regions
       unsigned int r = 0;
       {
         unsigned int lo_r = 0, hi_r = G;   // largest r with s_off[r] <= lo_i
         while (hi_r - lo_r > 1) {
-          unsigned int mid = (lo_r + hi_r) / 2;
+          const unsigned int mid = (lo_r + hi_r) / 2;
           if (s_off[mid] <= lo_i) lo_r = mid; else hi_r = mid;
         }
         r = lo_r;
@@ -666,14 +835,21 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
       for (; r < G && s_off[r] < hi_i; ++r) {
         const unsigned long long s0 = s_off[r] > lo_i ? s_off[r] : lo_i;
         const unsigned long long s1 = s_off[r + 1] < hi_i ? s_off[r + 1] : hi_i;
-        const T* zr = A.z + (long long)r * A.region_cap;
+        const T* zr = A.z + region_start(r, nch, G, Ops<T>::kVec);
         const unsigned long long rbase = s_off[r];
-        for (unsigned long long i = s0 + tid; i < s1; i += kThreads) {
-          const T v = __ldcg(zr + (i - rbase));
-          const U key = ukey(v);
-          const bool inb = (v > fa) && (v <= fb);
-          const bool match = known == 0 || (U)(key >> (W - known)) == prefix;
-          if (inb && match) atomicAdd(&s_hist[(unsigned int)(key >> sh) & (unsigned int)dmask], 1u);
+        // warp-uniform sweep; equal digits within a warp are merged before the atomic
+        for (unsigned long long i0 = s0 + (unsigned long long)warp * 32; i0 < s1; i0 += kThreads) {
+          const unsigned long long i = i0 + lane;
+          unsigned int d = kBins;
+          if (i < s1) {
+            const T v = __ldcg(zr + (i - rbase));
+            const U key = ukey(v);
+            const bool inb = (v > fa) && (v <= fb);
+            const bool match = known == 0 || (U)(key >> (W - known)) == prefix;
+            if (inb && match) d = (unsigned int)(key >> sh) & dmask;
+          }
+          const unsigned int same = __match_any_sync(0xffffffffu, d);
+          if (d < kBins && lane == __ffs(same) - 1) atomicAdd(&s_hist[d], (unsigned int)__popc(same));
         }
       }
       __syncthreads();
@@ -692,7 +868,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
         unsigned long long incl = local;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-          unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+          const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
           if (tid >= o) incl += y;
         }
         const unsigned long long want = s_rank;
@@ -720,6 +896,12 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
       __syncthreads();
     }
     result = ukey_value(s_prefix, T());
+  } else if (fin.phase == 1 && fin.result == T(0) && fin.clt_res >= 0) {
+    // a zero result found by counts: -0 sorts before +0, so count the -0 elements
+    unsigned long long d0 = 0, d1 = 0, nz = 0;
+    if (!aux_pass(T(0), T(0), &d0, &d1, &nz)) return;
+    result = (k - fin.clt_res) <= (long long)nz ? T(-0.0) : T(0.0);
+    extra = 1;
   }
 
   if (bid == 0 && tid == 0) {
@@ -727,10 +909,8 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     *A.out = result;
     gbs_run_stats* rs = A.rs;
     rs->status = ld_relaxed_i32(&A.ctrl->status);
-    rs->how = fin.phase == 3 ? GBS_HOW_NONE
-            : fin.phase == 2 ? GBS_HOW_FINISH
-            : (pass == 0 ? fin.it : GBS_HOW_HIT);
-    rs->passes = 1 + pass;
+    rs->how = fin.phase == 3 ? GBS_HOW_NONE : fin.phase == 2 ? GBS_HOW_FINISH : fin.how;
+    rs->passes = 1 + pass + extra;
     rs->kelley_steps = s_nk;
     rs->bisect_steps = s_nb;
     rs->finish_rounds = rounds;
@@ -742,6 +922,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     for (int i = 0; i < kMaxIt; ++i) {
       rs->pops[i] = i < ni ? s_pops[i] : 0;
       rs->iterates[i] = i < ni ? s_iter[i] : 0.0;
+      rs->t_stream_ns[i] = i < ni ? s_tstream[i] : 0;
     }
     stamp();
     rs->n_t = s_ntns;
@@ -768,19 +949,17 @@ int grid_for(gbs_ctx* c) {
   return std::min(kMaxGrid, c->num_sms * bps);
 }
 
+// Elements of the compaction area for inputs of up to n elements (any alignment).
 template <typename T>
-long long region_cap_for(long long n, int grid) {
-  const long long vec = vec_of<T>();
-  const long long nv_max = n / vec + 1;
-  const long long stride = (long long)grid * kThreads;
-  return ((nv_max + stride - 1) / stride) * kThreads * vec + 2 * vec;
+long long z_elems_for(long long n, int grid) {
+  const int vec = vec_of<T>();
+  return region_start(grid, chunk_count(n / vec + 1), grid, vec);
 }
 
 template <typename T>
 float stats_sigma(long long n, int grid) {
-  const long long vec = vec_of<T>();
-  const long long stride = (long long)grid * kThreads;
-  const long long per_thread = ((n / vec + 1 + stride - 1) / stride) * vec + 2 * vec;
+  const int vec = vec_of<T>();
+  const long long per_thread = per_thread_bound(chunk_count(n / vec + 1), grid, vec);
   int e = 0;
   while ((1ll << e) < per_thread) ++e;
   return std::ldexp(1.0f, -(e + 2));
@@ -793,8 +972,8 @@ gbs_status launch_select(gbs_ctx* c, const T* x, long long n, long long k, T* ou
   DeviceGuard g(c->device);
   if (!g.ok) return GBS_ECUDA;
   const int grid = grid_for<T>(c);
-  const long long rcap = region_cap_for<T>(n, grid);
-  const size_t zb = mode == kModeSelect ? (size_t)rcap * grid * sizeof(T) : 0;
+  const long long zel = z_elems_for<T>(n, grid);
+  const size_t zb = mode == kModeSelect ? (size_t)zel * sizeof(T) : 0;
   gbs_status s = gbs_internal_ensure(c, zb);
   if (s != GBS_OK) return s;
   SelArgs<T> A;
@@ -805,7 +984,7 @@ gbs_status launch_select(gbs_ctx* c, const T* x, long long n, long long k, T* ou
   A.a_eval = a; A.t_eval = t;
   A.sigma_stats = stats_sigma<T>(n, grid);
   A.ctrl = c->ctrl; A.part = c->part; A.spart = c->spart; A.ghist = c->ghist;
-  A.z = reinterpret_cast<T*>(c->z); A.region_cap = rcap;
+  A.z = reinterpret_cast<T*>(c->z); A.z_elems = zel;
   A.rs = c->rs; A.stats_out = sout; A.eval_out = eout;
   if (cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), stream) != cudaSuccess) return GBS_ECUDA;
   if (mode == kModeSelect && cudaMemsetAsync(c->rs, 0, sizeof(gbs_run_stats), stream) != cudaSuccess)
@@ -832,7 +1011,7 @@ gbs_status run_select(gbs_ctx* c, const double* x, long long n, long long k, dou
   return launch_select<double>(c, x, n, k, out, mode, a, t, sout, eout, stream);
 }
 // Pieces of the float32 launch for callers that bring their own scratch.
-long long select_region_cap_f32(long long n, int grid) { return region_cap_for<float>(n, grid); }
+long long select_z_elems_f32(long long n, int grid) { return z_elems_for<float>(n, grid); }
 float select_stats_sigma_f32(long long n, int grid) { return stats_sigma<float>(n, grid); }
 int select_occupancy_f32() {
   int occ = 0;
@@ -845,8 +1024,8 @@ int select_occupancy_f32() {
 cudaError_t select_launch_f32(const SelArgs<float>& A, int grid, cudaStream_t stream) {
   SelArgs<float> a = A;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((const void*)select_kernel<float>, dim3(grid), dim3(kThreads), args, 0,
-                                     stream);
+  return cudaLaunchCooperativeKernel((const void*)select_kernel<float>, dim3(grid), dim3(kThreads), args,
+                                     0, stream);
 }
 
 gbs_status reserve_select(gbs_ctx* c, long long n, int elem_bytes) {
@@ -854,10 +1033,10 @@ gbs_status reserve_select(gbs_ctx* c, long long n, int elem_bytes) {
   if (!g.ok) return GBS_ECUDA;
   if (elem_bytes == 4) {
     const int grid = grid_for<float>(c);
-    return gbs_internal_ensure(c, (size_t)region_cap_for<float>(n, grid) * grid * 4);
+    return gbs_internal_ensure(c, (size_t)z_elems_for<float>(n, grid) * 4);
   }
   const int grid = grid_for<double>(c);
-  return gbs_internal_ensure(c, (size_t)region_cap_for<double>(n, grid) * grid * 8);
+  return gbs_internal_ensure(c, (size_t)z_elems_for<double>(n, grid) * 8);
 }
 
 }  // namespace gbs

@@ -4,16 +4,19 @@
 #include <cstdint>
 
 #include "common.cuh"
+#include "layout.cuh"
 
 namespace gbs {
 
 enum { kModeSelect = 0, kModeStats = 1, kModeEval = 2 };
 
 // One CTA's share of a fused pass (Algorithm 1, step 1.2).
-struct __align__(32) PassPartial {
+struct __align__(16) PassPartial {
   unsigned long long c_lt;   // #(x < t)
   unsigned long long c_le;   // #(x <= t)
-  unsigned long long c_aux;  // #(x <= a) in eval mode; compacted elements in a compacting pass
+  unsigned long long c_aux;  // #(x <= a): eval mode and the first cutting-plane pass
+  unsigned long long c_aux2; // #(x < b): the first cutting-plane pass
+  unsigned long long c_reg;  // elements this CTA compacted
   double S;                  // sum over a < x < t of (t - x), float64 total of float32 partials
 };
 
@@ -40,8 +43,8 @@ struct SelArgs {
   PassPartial* part;               // [2][grid]
   StatsPartial* spart;             // [grid]
   unsigned long long* ghist;       // [kMaxRounds][kBins]
-  T* z;                            // [grid][region_cap]
-  long long region_cap;
+  T* z;                            // compaction area, regions at region_start(g)
+  long long z_elems;               // its size in elements
   gbs_run_stats* rs;               // device record of this call
   gbs_array_stats* stats_out;      // kModeStats
   gbs_cost_eval* eval_out;         // kModeEval
@@ -55,9 +58,9 @@ gbs_status run_select(gbs_ctx* c, const double* x, long long n, long long k, dou
 // Grows the workspace for selections of up to n elements of elem_bytes.
 gbs_status reserve_select(gbs_ctx* c, long long n, int elem_bytes);
 
-// Pieces of the float32 launch for callers that bring their own scratch: the compaction
-// region stride, the pass-0 sum scale, CTAs per SM that fit, and the cooperative launch.
-long long select_region_cap_f32(long long n, int grid);
+// Pieces of the float32 launch for callers that bring their own scratch: the size of the
+// compaction area, the pass-0 sum scale, CTAs per SM that fit, and the cooperative launch.
+long long select_z_elems_f32(long long n, int grid);
 float select_stats_sigma_f32(long long n, int grid);
 int select_occupancy_f32();
 cudaError_t select_launch_f32(const SelArgs<float>& A, int grid, cudaStream_t stream);

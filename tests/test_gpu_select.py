@@ -274,3 +274,17 @@ def test_full_size_single_array_f64(ctx):
     for k in (n // 100, (n + 1) // 2, (99 * n) // 100):
         r = ctx.select_kth(xt, k).cpu().numpy()[0]
         assert bits(r) == bits(osel.select_kth(x, k)), k
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_whole_array_compaction_fills_every_region(ctx, dtype):
+    """cap >= n: the first cutting-plane pass compacts (almost) all of x, so every CTA's
+    compaction region is filled to its bound; sizes straddle chunk boundaries."""
+    try:
+        ctx.set_config(cap=10 ** 12)
+        for n in (4099, 8192 * 3 + 1, 300007, 2 ** 21 + 7):
+            x = synth.paper_distribution("normal", n, seed=60 + n, dtype=dtype)
+            for offset in (0, 1):
+                check(ctx, x, [1, 2, n // 3, (n + 1) // 2, n - 1, n], offset=offset)
+    finally:
+        ctx.set_config(cap=0)
