@@ -162,6 +162,34 @@ gbs_status gbs_cost_pass_f64(gbs_ctx* ctx, const double* x, int64_t n, int64_t k
  * record to read back; a NaN input yields a NaN result. */
 gbs_status gbs_select_kth_f32_noalloc(const float* x, int64_t n, int64_t k, float* out, void* stream);
 
+/* Segmented batched select: out[s] = x_(k[s]) of the segment x[offsets[s], offsets[s+1])
+ * for s = 0..S-1, all in one persistent launch (Sec. 2 notes that many medians of
+ * different vectors are a workload of their own).  offsets: S+1 int64, device,
+ * non-decreasing; k: S int64, device, 1-based, or NULL for the medians
+ * floor((n_s+1)/2); out: S floats, device.  Each CTA takes whole segments, largest
+ * first; a segment that fits in shared memory is radix-selected there, a larger one runs
+ * the cutting plane (Algorithm 1) with CTA-wide reductions and compacts its final
+ * bracket into shared memory.  A segment with n_s = 0 or k outside [1, n_s] gets a NaN
+ * and GBS_EINVAL in the device status (gbs_last_stats).  The call launches two kernels
+ * and no host synchronisation, so it can be captured in a CUDA graph once the
+ * workspace holds 8*S bytes (gbs_reserve or a first call). */
+gbs_status gbs_select_segmented_f32(gbs_ctx* ctx, const float* x, const int64_t* offsets, int32_t S,
+                                    const int64_t* k, float* out, void* stream);
+
+/* Autotuner of the segmented select: times every launch variant (CTA size and the
+ * shared-memory capacity of the in-CTA select) on this batch, keeps the fastest for later
+ * calls on ctx and leaves its results in out.  Synchronous.  chosen (may be NULL)
+ * receives the variant; ms_per_variant (n_variants floats, may be NULL) the times. */
+gbs_status gbs_segmented_autotune_f32(gbs_ctx* ctx, const float* x, const int64_t* offsets, int32_t S,
+                                      const int64_t* k, float* out, void* stream, int32_t* chosen,
+                                      float* ms_per_variant, int32_t n_variants);
+gbs_status gbs_segmented_set_variant(gbs_ctx* ctx, int32_t variant);
+gbs_status gbs_segmented_get_variant(gbs_ctx* ctx, int32_t* variant, int32_t* threads, int32_t* smem_cap,
+                                     int32_t* n_variants);
+/* Passes over each segment of the last segmented call (1 = loaded once into shared
+ * memory).  Synchronises that call's stream.  passes: S int32, host. */
+gbs_status gbs_segmented_passes(gbs_ctx* ctx, int32_t* passes, int32_t S);
+
 /* Synchronises the stream of the last call on ctx and copies its record to *out. */
 gbs_status gbs_last_stats(gbs_ctx* ctx, gbs_run_stats* out);
 

@@ -3,8 +3,8 @@
 Argument marshalling only: every step of the selection runs in the library's CUDA
 kernels.  The raw C entry points are exposed under their C names (``gbs_select_kth_f32``
 and so on, see include/gbselect.h); :class:`Context` wraps them for torch tensors.
-Importing fails loudly if the library has not been built (``python -m
-paper_1104_2732_gb300.build``); there is no CPU fallback.
+Importing fails loudly if the library has not been built (``python
+paper_1104_2732_gb300/build.py``); there is no CPU fallback.
 """
 from __future__ import annotations
 
@@ -15,7 +15,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libgbselect.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1104_2732_gb300.build`")
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_1104_2732_gb300/build.py`")
 _lib = C.CDLL(LIB_PATH)
 
 # ------------------------------------------------------------------ status codes
@@ -74,13 +74,23 @@ _SIGS = {
     "gbs_cost_pass_f64": (C.c_int, [_P, _P, _I64, _I64, C.c_double, C.c_double, _P, _P]),
     "gbs_last_stats": (C.c_int, [_P, C.POINTER(gbs_run_stats)]),
     "gbs_select_kth_f32_noalloc": (C.c_int, [_P, _I64, _I64, _P, _P]),
+    "gbs_select_segmented_f32": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P, _P]),
+    "gbs_segmented_autotune_f32": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P, _P, C.POINTER(C.c_int32),
+                                             C.POINTER(C.c_float), C.c_int32]),
+    "gbs_segmented_set_variant": (C.c_int, [_P, C.c_int32]),
+    "gbs_segmented_get_variant": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                            C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "gbs_segmented_passes": (C.c_int, [_P, C.POINTER(C.c_int32), C.c_int32]),
     "gbs_status_string": (C.c_char_p, [C.c_int]),
 }
 
 
 def _bind(table):
     for name, (res, args) in table.items():
-        fn = getattr(_lib, name)
+        try:
+            fn = getattr(_lib, name)
+        except AttributeError as e:
+            raise ImportError(f"{LIB_PATH} lacks {name}: rebuild it with `python paper_1104_2732_gb300/build.py`") from e
         fn.restype = res
         fn.argtypes = args
         globals()[name] = fn
@@ -205,6 +215,58 @@ class Context:
                   C.c_void_p(buf.data_ptr()), _stream_ptr(stream)), "gbs_cost_pass")
         rec = gbs_cost_eval.from_buffer_copy(bytes(buf.cpu().numpy()))
         return {f: getattr(rec, f) for f, _ in gbs_cost_eval._fields_ if f != "pad"}
+
+    # -------------------------------------------------------------- segmented
+    def _seg_args(self, x, offsets, k, out):
+        import torch
+        x = _as_input(x)
+        if x.dtype != torch.float32:
+            raise TypeError("the segmented select takes float32")
+        offsets = _as_input(offsets)
+        if offsets.dtype != torch.int64:
+            raise TypeError("offsets must be int64")
+        S = offsets.numel() - 1
+        if k is not None:
+            k = _as_input(k)
+            if k.dtype != torch.int64 or k.numel() != S:
+                raise TypeError("k must be int64 with one rank per segment")
+        if out is None:
+            out = torch.empty(S, dtype=torch.float32, device=x.device)
+        kp = C.c_void_p(k.data_ptr()) if k is not None else None
+        return x, offsets, S, kp, out
+
+    def select_segmented(self, x, offsets, k=None, out=None, stream=None):
+        """out[s] = x_(k[s]) of x[offsets[s]:offsets[s+1]] (medians when k is None)."""
+        x, offsets, S, kp, out = self._seg_args(x, offsets, k, out)
+        _check(gbs_select_segmented_f32(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(offsets.data_ptr()), S, kp,
+                                        C.c_void_p(out.data_ptr()), _stream_ptr(stream)), "gbs_select_segmented")
+        return out
+
+    def autotune_segmented(self, x, offsets, k=None, out=None, stream=None):
+        """Times every launch variant on this batch; returns (chosen, ms per variant)."""
+        x, offsets, S, kp, out = self._seg_args(x, offsets, k, out)
+        nv = C.c_int32()
+        _check(gbs_segmented_get_variant(self._h, None, None, None, C.byref(nv)), "gbs_segmented_get_variant")
+        ms = (C.c_float * nv.value)()
+        chosen = C.c_int32()
+        _check(gbs_segmented_autotune_f32(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(offsets.data_ptr()), S, kp,
+                                          C.c_void_p(out.data_ptr()), _stream_ptr(stream), C.byref(chosen), ms,
+                                          nv.value), "gbs_segmented_autotune")
+        return chosen.value, list(ms)
+
+    def segmented_variant(self):
+        v, t, c, nv = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        _check(gbs_segmented_get_variant(self._h, C.byref(v), C.byref(t), C.byref(c), C.byref(nv)),
+               "gbs_segmented_get_variant")
+        return {"variant": v.value, "threads": t.value, "smem_cap": c.value, "n_variants": nv.value}
+
+    def set_segmented_variant(self, v):
+        _check(gbs_segmented_set_variant(self._h, int(v)), "gbs_segmented_set_variant")
+
+    def segmented_passes(self, S):
+        buf = (C.c_int32 * int(S))()
+        _check(gbs_segmented_passes(self._h, buf, int(S)), "gbs_segmented_passes")
+        return list(buf)
 
     def last_stats(self, raise_on_error=True):
         """Synchronises the last call's stream and returns its record as a dict."""

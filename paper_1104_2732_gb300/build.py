@@ -1,6 +1,7 @@
 """Builds libgbselect.so in-tree from csrc/*.cu for sm_103a with nvcc.
 
-Usage: ``python -m paper_1104_2732_gb300.build [--force]``.  Translation units are
+Usage: ``python paper_1104_2732_gb300/build.py [--force]`` (run by path: importing the
+package itself needs the library).  Translation units are
 compiled in parallel into ``_build/`` and linked into the package directory.
 """
 from __future__ import annotations

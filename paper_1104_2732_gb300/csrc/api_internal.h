@@ -30,6 +30,8 @@ struct gbs_ctx {
   size_t z_bytes = 0;
   cudaStream_t last_stream = nullptr;
   int last_grid = 0;
+  int seg_variant = 1;          // launch variant of the segmented select (autotuned)
+  int last_segments = 0;
 };
 
 // Grows the workspace so that its z area holds at least z_bytes.  Synchronous.

@@ -1,0 +1,652 @@
+// Segmented batched selection: out[s] = x_(k_s) of x[off[s], off[s+1]) for thousands of
+// arrays of uneven sizes in one persistent launch.
+//
+// Each CTA takes whole segments from a work queue ordered largest first (a small
+// schedule kernel buckets the segments by size).  A segment that fits in shared memory
+// is loaded once and radix-selected there.  A larger one runs the cutting plane of
+// Algorithm 1 (Sec. 3) with CTA-wide reductions: pass 0 (extremes, sum), then one fused
+// cost + count pass per iterate; the pass that sees a bracket small enough for shared
+// memory compacts it there and the answer is radix-selected inside it (the hybrid of
+// Sec. 3).  No CTA waits on another, so the launch needs no grid-wide barrier and the
+// whole call (schedule + kernel) can be captured in a CUDA graph.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+
+#include "api_internal.h"
+#include "common.cuh"
+#include "elem.cuh"
+#include "segmented.cuh"
+
+namespace gbs {
+
+namespace {
+
+constexpr int kSchedBuckets = 64;
+
+// Buckets segment ids by floor(log2(size)), largest bucket first; also checks offsets.
+__global__ void seg_schedule_kernel(const long long* __restrict__ off, int S, int* __restrict__ order,
+                                    Ctrl* ctrl) {
+  __shared__ unsigned int hist[kSchedBuckets];
+  __shared__ unsigned int base[kSchedBuckets];
+  for (int i = threadIdx.x; i < kSchedBuckets; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    const long long n = off[s + 1] - off[s];
+    if (n < 0) atomicCAS(&ctrl->status, 0, (int)GBS_EINVAL);
+    const int b = n <= 1 ? 0 : 63 - __clzll((unsigned long long)n);
+    atomicAdd(&hist[kSchedBuckets - 1 - b], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int acc = 0;
+    for (int i = 0; i < kSchedBuckets; ++i) {
+      base[i] = acc;
+      acc += hist[i];
+    }
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    const long long n = off[s + 1] - off[s];
+    const int b = n <= 1 ? 0 : 63 - __clzll((unsigned long long)n);
+    order[atomicAdd(&base[kSchedBuckets - 1 - b], 1u)] = s;
+  }
+}
+
+// CTA-wide sum of six values for a CTA of B threads (fixed order).
+template <int B>
+__device__ __forceinline__ Sum6 cta_sum6(Sum6 v, Sum6* scratch /* [B/32 + 1] */) {
+  constexpr int NW = B / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) v.u[i] += __shfl_xor_sync(0xffffffffu, v.u[i], o);
+    v.d += __shfl_xor_sync(0xffffffffu, v.d, o);
+  }
+  __syncthreads();
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Sum6 r = scratch[0];
+    for (int i = 1; i < NW; ++i) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) r.u[q] += scratch[i].u[q];
+      r.d += scratch[i].d;
+    }
+    scratch[NW] = r;
+  }
+  __syncthreads();
+  return scratch[NW];
+}
+
+// Calls f(element) on every element of xs[0, n) handled by this thread of the CTA.
+template <int B, typename Fn>
+__device__ __forceinline__ void cta_stream(const float* __restrict__ xs, const Geometry<float>& g, Fn& f) {
+  const int tid = threadIdx.x;
+  if (tid < g.head) f(xs[tid]);
+  if (tid < g.n - g.tail0) f(xs[g.tail0 + tid]);
+  const float4* xv = reinterpret_cast<const float4*>(xs + g.head);
+  long long v = tid;
+  for (; v + 3 * B < g.nv; v += 4 * B) {
+    float4 r[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) r[u] = __ldcs(xv + v + u * B);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) Ops<float>::each(r[u], f);
+  }
+  for (; v < g.nv; v += B) {
+    const float4 r = __ldcs(xv + v);
+    Ops<float>::each(r, f);
+  }
+}
+
+// As cta_stream, and appends every element with keep(element) to zb (shared memory,
+// counter *cnt).  Warp-uniform loop for the per-warp prefix sum.
+template <int B, typename Fn, typename Keep>
+__device__ __forceinline__ void cta_stream_compact(const float* __restrict__ xs, const Geometry<float>& g, Fn& f,
+                                                   Keep& keep, float* zb, unsigned int* cnt) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid < g.head) {
+    const float e = xs[tid];
+    f(e);
+    if (keep(e)) zb[atomicAdd(cnt, 1u)] = e;
+  }
+  if (tid < g.n - g.tail0) {
+    const float e = xs[g.tail0 + tid];
+    f(e);
+    if (keep(e)) zb[atomicAdd(cnt, 1u)] = e;
+  }
+  const float4* xv = reinterpret_cast<const float4*>(xs + g.head);
+  for (long long wb = tid - lane; wb < g.nv; wb += 4 * B) {
+    float4 r[4];
+    unsigned int mask = 0, c = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long i = wb + lane + (long long)u * B;
+      if (i < g.nv) {
+        r[u] = __ldcs(xv + i);
+        Ops<float>::each(r[u], f);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const bool kk = keep(Ops<float>::get(r[u], e));
+          mask |= (kk ? 1u : 0u) << (u * 4 + e);
+          c += kk;
+        }
+      }
+    }
+    unsigned int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total) {
+      unsigned int b0 = 0;
+      if (lane == 31) b0 = atomicAdd(cnt, total);
+      b0 = __shfl_sync(0xffffffffu, b0, 31);
+      unsigned int pos = b0 + incl - c;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (mask & (1u << (u * 4 + e))) zb[pos++] = Ops<float>::get(r[u], e);
+    }
+  }
+}
+
+// Radix select in shared memory: the rank-th (1-based) smallest, in totalOrder, of the
+// elements of zb[0, m) that lie in (a, b] (all of them when !filter).  Returns the
+// element's key.  8-bit digits from the highest bit where the bracket's keys differ;
+// equal digits within a warp are merged before the shared-memory atomic.
+template <int B>
+__device__ uint32_t smem_radix_select(const float* zb, int m, unsigned long long rank, bool filter, float a,
+                                      float b, unsigned int* hist /* [256] */, uint32_t* s_prefix,
+                                      int* s_known, unsigned long long* s_rank) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    int known = 0;
+    uint32_t prefix = 0;
+    if (filter) {
+      const uint32_t lo = ukey(a) + 1, hi = ukey(b);
+      const uint32_t diff = lo ^ hi;
+      known = diff == 0 ? 32 : __clz(diff);
+      prefix = known == 0 ? 0u : (known == 32 ? hi : (hi >> (32 - known)));
+    }
+    *s_known = known;
+    *s_prefix = prefix;
+    *s_rank = rank;
+  }
+  __syncthreads();
+  while (*s_known < 32) {
+    const int known = *s_known;
+    const uint32_t prefix = *s_prefix;
+    const int nbits = (32 - known) < 8 ? (32 - known) : 8;
+    const int sh = 32 - known - nbits;
+    const unsigned int dmask = (1u << nbits) - 1u;
+    for (int i = tid; i < 256; i += B) hist[i] = 0;
+    __syncthreads();
+    for (int base = warp * 32; base < m; base += B) {
+      const int i = base + lane;
+      unsigned int d = 256;
+      if (i < m) {
+        const float v = zb[i];
+        const uint32_t key = ukey(v);
+        const bool inb = !filter || ((v > a) && (v <= b));
+        const bool match = known == 0 || (key >> (32 - known)) == prefix;
+        if (inb && match) d = (key >> sh) & dmask;
+      }
+      const unsigned int same = __match_any_sync(0xffffffffu, d);
+      if (d < 256 && lane == __ffs(same) - 1) atomicAdd(&hist[d], (unsigned int)__popc(same));
+    }
+    __syncthreads();
+    if (warp == 0) {
+      unsigned int h[8];
+      unsigned int local = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        h[j] = hist[lane * 8 + j];
+        local += h[j];
+      }
+      unsigned long long incl = local;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const unsigned long long want = *s_rank;
+      const unsigned long long excl = incl - local;
+      const bool mine = excl < want && want <= incl;
+      const unsigned int who = __ballot_sync(0xffffffffu, mine);
+      if (mine) {
+        unsigned long long c = excl;
+        int d = 0;
+        for (int j = 0; j < 8; ++j) {
+          if (c + h[j] >= want) { d = lane * 8 + j; break; }
+          c += h[j];
+        }
+        *s_rank = want - c;
+        *s_prefix = (prefix << nbits) | (uint32_t)d;
+        *s_known = known + nbits;
+      }
+      if (who == 0 && lane == 0) {
+        *s_known = 32;
+        *s_prefix = 0;
+        *s_rank = 0;   // flags an inconsistency to the caller
+      }
+    }
+    __syncthreads();
+  }
+  return *s_prefix;
+}
+
+struct SegShared {
+  Sum6 sum6[33];
+  float mn[32], mx[32];
+  unsigned int hist[256];
+  unsigned int zcnt;
+  uint32_t prefix;
+  int known;
+  unsigned long long rank;
+  int seg;
+  // bracket state (thread 0 writes, all read)
+  float a, b, t, m, M, sig, result;
+  long long cle_a, clt_b, cle_b, nneg, npos, nnz, n_nan, clt_res;
+  double dF, sum;
+  int it, use_bisect, stalled, compact, first, phase, how, passes;
+};
+
+template <int B, int CAP>
+__global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
+  extern __shared__ __align__(16) float zb[];   // CAP floats
+  __shared__ SegShared sh;
+  const int tid = threadIdx.x, lane = tid & 31;
+  constexpr int NW = B / 32;
+  for (;;) {
+    if (tid == 0) {
+      const unsigned long long q = atomicAdd(&A.ctrl->w_count, 1ull);
+      sh.seg = q < (unsigned long long)A.S ? A.order[q] : -1;
+    }
+    __syncthreads();
+    const int s = sh.seg;
+    if (s < 0) break;
+    const long long o0 = A.off[s];
+    const long long n = A.off[s + 1] - o0;
+    const long long k = A.kk ? A.kk[s] : (n + 1) / 2;
+    if (n < 1 || k < 1 || k > n) {
+      if (tid == 0) {
+        A.out[s] = NAN;
+        atomicCAS(&A.ctrl->status, 0, (int)GBS_EINVAL);
+        if (A.seg_passes) A.seg_passes[s] = 0;
+      }
+      __syncthreads();
+      continue;
+    }
+    const float* xs = A.x + o0;
+    const Geometry<float> g(xs, n);
+
+    if (n <= CAP) {
+      // ---- small segment: load once, radix select in shared memory ----
+      unsigned int nan_here = 0;
+      for (long long i = tid; i < n; i += B) {
+        const float v = xs[i];
+        nan_here += (v != v);
+        zb[i] = v;
+      }
+      Sum6 v6;
+      v6.u[0] = nan_here; v6.u[1] = v6.u[2] = v6.u[3] = v6.u[4] = 0; v6.d = 0.0;
+      const Sum6 r6 = cta_sum6<B>(v6, sh.sum6);
+      if (r6.u[0] > 0) {
+        if (tid == 0) {
+          A.out[s] = NAN;
+          atomicCAS(&A.ctrl->status, 0, (int)GBS_ENAN);
+          if (A.seg_passes) A.seg_passes[s] = 1;
+        }
+        __syncthreads();
+        continue;
+      }
+      const uint32_t key = smem_radix_select<B>(zb, (int)n, (unsigned long long)k, false, 0.f, 0.f, sh.hist,
+                                                &sh.prefix, &sh.known, &sh.rank);
+      if (tid == 0) {
+        if (sh.rank == 0) atomicCAS(&A.ctrl->status, 0, (int)GBS_EINTERNAL);
+        A.out[s] = ukey_value(key, 0.f);
+        if (A.seg_passes) A.seg_passes[s] = 1;
+      }
+      __syncthreads();
+      continue;
+    }
+
+    // ---- large segment: pass 0 (extremes, sum, non-finite and -0 counts) ----
+    {
+      const float sig0 = A.sigma_stats;
+      float x0 = 0.f;
+      if (tid < n && Ops<float>::is_finite(xs[tid])) x0 = xs[tid];
+      const float x0s = x0 * sig0;
+      float mn = INFINITY, mx = -INFINITY, sum = 0.f;
+      unsigned int nnan = 0, nneg = 0, npos = 0, nnz = 0, seen = 0;
+      auto f = [&](float v) {
+        ++seen;
+        if (fabsf(v) <= FLT_MAX) {
+          mn = fminf(mn, v);
+          mx = fmaxf(mx, v);
+          sum += fmaf(v, sig0, -x0s);
+          nnz += (__float_as_uint(v) == 0x80000000u);
+        } else {
+          nnan += (v != v);
+          nneg += (v == -INFINITY);
+          npos += (v == INFINITY);
+        }
+      };
+      cta_stream<B>(xs, g, f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      }
+      if (lane == 0) { sh.mn[tid >> 5] = mn; sh.mx[tid >> 5] = mx; }
+      const unsigned int nfin = seen - nnan - nneg - npos;
+      Sum6 v6;
+      v6.u[0] = nnan; v6.u[1] = nneg; v6.u[2] = npos; v6.u[3] = nnz; v6.u[4] = nfin;
+      v6.d = (double)sum / (double)sig0 + (double)nfin * (double)x0;
+      const Sum6 r6 = cta_sum6<B>(v6, sh.sum6);
+      if (tid == 0) {
+        float bm = sh.mn[0], bM = sh.mx[0];
+        for (int w = 1; w < NW; ++w) { bm = fminf(bm, sh.mn[w]); bM = fmaxf(bM, sh.mx[w]); }
+        sh.m = bm; sh.M = bM;
+        sh.n_nan = (long long)r6.u[0]; sh.nneg = (long long)r6.u[1]; sh.npos = (long long)r6.u[2];
+        sh.nnz = (long long)r6.u[3]; sh.sum = r6.d;
+        sh.passes = 1; sh.it = 0; sh.use_bisect = 0; sh.stalled = 0; sh.first = 0; sh.phase = 0;
+        sh.how = GBS_HOW_NONE; sh.clt_res = -1; sh.result = 0.f;
+        if (sh.n_nan > 0) {
+          sh.phase = 3; sh.result = NAN;
+        } else if (k <= sh.nneg) {
+          sh.phase = 1; sh.result = -INFINITY;
+        } else if (k > n - sh.npos) {
+          sh.phase = 1; sh.result = INFINITY;
+        } else if (!(bm < bM)) {
+          sh.phase = 1; sh.result = bm; sh.clt_res = sh.nneg;
+        } else {
+          sh.a = bm; sh.b = bM;
+          sh.cle_a = sh.nneg + 1; sh.clt_b = n - sh.npos - 1; sh.cle_b = n - sh.npos; sh.first = 1;
+          const double gL = (double)(sh.cle_a - k) + 0.5;
+          const double inner = sh.sum - (double)bm - (double)bM;
+          sh.dF = gL * ((double)bM - (double)bm) + (double)(sh.clt_b - sh.cle_a) * (double)bM - inner;
+        }
+      }
+      __syncthreads();
+    }
+
+    // ---- cutting-plane passes ----
+    const long long per_thread = ((g.nv + B - 1) / B) * 4 + 8;
+    while (sh.phase == 0) {
+      if (tid == 0) {   // step 1.1 (with the key-midpoint safeguard)
+        const long long pop = sh.cle_b - sh.cle_a;
+        sh.compact = pop <= CAP;   // the compacted bracket must fit in shared memory
+        const uint32_t ka = ukey(sh.a), kb = ukey(sh.b);
+        float t;
+        if (kb - ka <= 1u) {
+          // no float strictly inside: every element of (a, b] equals b
+          sh.phase = 1; sh.result = sh.b; sh.clt_res = sh.cle_a;
+        } else {
+          const bool bis = sh.use_bisect || sh.stalled >= 2 || sh.it >= A.maxit;
+          if (bis) {
+            t = inside<float>(ukey_value(ka + (kb - ka) / 2, 0.f), sh.a, sh.b);
+          } else {
+            const double gL = (double)(sh.cle_a - k) + 0.5;
+            const double gR = (double)(sh.clt_b - k) + 0.5;
+            const double w = (double)sh.b - (double)sh.a;
+            t = inside<float>((float)((double)sh.a + (gR * w - sh.dF) / (gR - gL)), sh.a, sh.b);
+          }
+          sh.t = t;
+          sh.sig = cost_scale((double)t - (double)sh.a, per_thread);
+          sh.zcnt = 0;
+        }
+      }
+      __syncthreads();
+      if (sh.phase != 0) break;
+      const float ca = sh.a, ct = sh.t, cb = sh.b, nsig = -sh.sig, tsig = sh.t * sh.sig;
+      const int first = sh.first, compact = sh.compact;
+      unsigned int lt = 0, le = 0, xa = 0, xb = 0;
+      float S = 0.f;
+      auto fcore = [&](float v) { core(v, ca, ct, nsig, tsig, lt, le, S); };
+      auto ffirst = [&](float v) {
+        core(v, ca, ct, nsig, tsig, lt, le, S);
+        xa += (v <= ca);
+        xb += (v < cb);
+      };
+      auto keep = [&](float v) { return (v > ca) & (v <= cb); };
+      if (first) {
+        if (compact) cta_stream_compact<B>(xs, g, ffirst, keep, zb, &sh.zcnt);
+        else cta_stream<B>(xs, g, ffirst);
+      } else {
+        if (compact) cta_stream_compact<B>(xs, g, fcore, keep, zb, &sh.zcnt);
+        else cta_stream<B>(xs, g, fcore);
+      }
+      Sum6 v6;
+      v6.u[0] = lt; v6.u[1] = le; v6.u[2] = xa; v6.u[3] = xb; v6.u[4] = 0; v6.d = (double)S;
+      const Sum6 r6 = cta_sum6<B>(v6, sh.sum6);   // also orders every append before the reads below
+      if (tid == 0) {   // steps 1.3-1.4
+        sh.passes++;
+        const long long clt = (long long)r6.u[0], cle = (long long)r6.u[1];
+        bool resolved = false;
+        if (sh.first) {
+          const long long cle_m = (long long)r6.u[2], clt_M = (long long)r6.u[3];
+          sh.first = 0;
+          if (cle_m >= k) {
+            sh.phase = 1; sh.result = sh.a; sh.clt_res = sh.nneg; resolved = true;
+          } else if (clt_M < k) {
+            sh.phase = 1; sh.result = sh.b; sh.clt_res = clt_M; resolved = true;
+          } else {
+            const double cmn = (double)(cle_m - sh.nneg), cmx = (double)(n - sh.npos - clt_M);
+            const double gL = (double)(cle_m - k) + 0.5;
+            const double inner = sh.sum - cmn * (double)sh.a - cmx * (double)sh.b;
+            sh.cle_a = cle_m; sh.clt_b = clt_M;
+            sh.dF = gL * ((double)sh.b - (double)sh.a) + (double)(clt_M - cle_m) * (double)sh.b - inner;
+          }
+        }
+        if (!resolved) {
+          const long long pop = sh.cle_b - sh.cle_a;
+          if (clt < k && k <= cle) {
+            sh.phase = 1; sh.result = sh.t; sh.clt_res = clt;
+          } else {
+            const double gL = (double)(sh.cle_a - k) + 0.5;
+            const double dphi = gL * ((double)sh.t - (double)sh.a) + r6.d / (double)sh.sig;
+            if (cle < k) {
+              sh.a = sh.t; sh.cle_a = cle; sh.dF -= dphi;
+            } else {
+              sh.b = sh.t; sh.clt_b = clt; sh.cle_b = cle; sh.dF = dphi;
+            }
+            const long long npop = sh.cle_b - sh.cle_a;
+            sh.use_bisect = (!sh.use_bisect) && ((double)npop > 0.75 * (double)pop);
+            sh.stalled = ((double)npop > 0.875 * (double)pop) ? sh.stalled + 1 : 0;
+            sh.it++;
+            if (compact) sh.phase = ((long long)sh.zcnt == pop) ? 2 : 4;
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+    float result = sh.result;
+    if (sh.phase == 2) {
+      const uint32_t key = smem_radix_select<B>(zb, (int)sh.zcnt, (unsigned long long)(k - sh.cle_a), true, sh.a,
+                                                sh.b, sh.hist, &sh.prefix, &sh.known, &sh.rank);
+      if (tid == 0 && sh.rank == 0) atomicCAS(&A.ctrl->status, 0, (int)GBS_EINTERNAL);
+      result = ukey_value(key, 0.f);
+    } else if (sh.phase == 1 && result == 0.f && sh.clt_res >= 0) {
+      result = (k - sh.clt_res) <= sh.nnz ? -0.f : 0.f;
+    }
+    if (tid == 0) {
+      if (sh.phase == 3) atomicCAS(&A.ctrl->status, 0, (int)GBS_ENAN);
+      if (sh.phase == 4) atomicCAS(&A.ctrl->status, 0, (int)GBS_EINTERNAL);
+      A.out[s] = result;
+      if (A.seg_passes) A.seg_passes[s] = sh.passes;
+    }
+    __syncthreads();
+  }
+}
+
+// The launch variants the autotuner chooses from: CTA size and shared-memory capacity
+// for the direct / finishing select.
+struct Variant {
+  int threads, cap;
+  void (*kernel)(SegArgs);
+};
+const Variant kVariants[] = {
+    {512, 12288, seg_kernel<512, 12288>},
+    {512, 24576, seg_kernel<512, 24576>},
+    {1024, 49152, seg_kernel<1024, 49152>},
+    {256, 12288, seg_kernel<256, 12288>},
+};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+}  // namespace
+
+int seg_num_variants() { return kNumVariants; }
+
+gbs_status seg_launch(gbs_ctx* c, const SegLaunch& L, int variant, cudaStream_t stream) {
+  if (variant < 0 || variant >= kNumVariants) return GBS_EINVAL;
+  const Variant& v = kVariants[variant];
+  const size_t smem = (size_t)v.cap * sizeof(float);
+  static bool attr_done[kNumVariants] = {};
+  if (!attr_done[variant]) {
+    if (cudaFuncSetAttribute(v.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return GBS_ECUDA;
+    }
+    attr_done[variant] = true;
+  }
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.kernel, v.threads, smem) != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    return GBS_ECUDA;
+  }
+  const int grid = c->num_sms * occ;
+  if (cudaMemsetAsync(L.ctrl, 0, sizeof(Ctrl), stream) != cudaSuccess) return GBS_ECUDA;
+  seg_schedule_kernel<<<1, 1024, 0, stream>>>(L.off, L.S, L.order, L.ctrl);
+  SegArgs A;
+  A.x = L.x; A.off = L.off; A.S = L.S; A.kk = L.kk; A.out = L.out; A.order = L.order; A.ctrl = L.ctrl;
+  A.maxit = 48;
+  A.seg_passes = L.seg_passes;
+  // pass-0 sums: a thread adds at most ceil(1e6 / threads) * ... terms of a segment; the
+  // scale keeps any float32 partial finite for segments up to 2^31 elements
+  A.sigma_stats = std::ldexp(1.0f, -24);
+  v.kernel<<<grid, v.threads, smem, stream>>>(A);
+  if (cudaGetLastError() != cudaSuccess) return GBS_ECUDA;
+  return GBS_OK;
+}
+
+int seg_variant_threads(int v) { return (v >= 0 && v < kNumVariants) ? kVariants[v].threads : 0; }
+int seg_variant_cap(int v) { return (v >= 0 && v < kNumVariants) ? kVariants[v].cap : 0; }
+
+}  // namespace gbs
+
+// ---------------------------------------------------------------------------------
+// C-ABI.
+// ---------------------------------------------------------------------------------
+namespace {
+gbs_status seg_prepare(gbs_ctx* c, const float* x, const int64_t* off, int32_t S, float* out,
+                       gbs::SegLaunch* L, const int64_t* k) {
+  if (!c || !x || !off || !out || S < 1) return GBS_EINVAL;
+  gbs_status st = gbs_internal_ensure(c, (size_t)S * 2 * sizeof(int));
+  if (st != GBS_OK) return st;
+  L->x = x; L->off = reinterpret_cast<const long long*>(off); L->S = S;
+  L->kk = reinterpret_cast<const long long*>(k); L->out = out;
+  L->order = static_cast<int*>(c->z);
+  L->seg_passes = static_cast<int*>(c->z) + S;
+  L->ctrl = c->ctrl;
+  return GBS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+gbs_status gbs_select_segmented_f32(gbs_ctx* c, const float* x, const int64_t* offsets, int32_t S,
+                                    const int64_t* k, float* out, void* stream) {
+  gbs::SegLaunch L;
+  gbs_status st = seg_prepare(c, x, offsets, S, out, &L, k);
+  if (st != GBS_OK) return st;
+  gbs::DeviceGuard g(c->device);
+  if (!g.ok) return GBS_ECUDA;
+  st = gbs::seg_launch(c, L, c->seg_variant, static_cast<cudaStream_t>(stream));
+  if (st == GBS_OK) {
+    c->last_stream = static_cast<cudaStream_t>(stream);
+    c->last_segments = S;
+  }
+  return st;
+}
+
+gbs_status gbs_segmented_autotune_f32(gbs_ctx* c, const float* x, const int64_t* offsets, int32_t S,
+                                      const int64_t* k, float* out, void* stream, int32_t* chosen,
+                                      float* ms_per_variant, int32_t n_variants) {
+  gbs::SegLaunch L;
+  gbs_status st = seg_prepare(c, x, offsets, S, out, &L, k);
+  if (st != GBS_OK) return st;
+  gbs::DeviceGuard g(c->device);
+  if (!g.ok) return GBS_ECUDA;
+  cudaStream_t strm = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return GBS_ECUDA;
+  int best = -1;
+  float best_ms = 0.f;
+  for (int v = 0; v < gbs::seg_num_variants(); ++v) {
+    float ms = -1.f;
+    if (gbs::seg_launch(c, L, v, strm) == GBS_OK) {   // warm-up
+      cudaEventRecord(e0, strm);
+      gbs_status s2 = GBS_OK;
+      for (int r = 0; r < 2 && s2 == GBS_OK; ++r) s2 = gbs::seg_launch(c, L, v, strm);
+      cudaEventRecord(e1, strm);
+      if (s2 == GBS_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms *= 0.5f;
+      }
+    }
+    cudaGetLastError();
+    if (ms_per_variant && v < n_variants) ms_per_variant[v] = ms;
+    if (ms > 0.f && (best < 0 || ms < best_ms)) {
+      best = v;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0) return GBS_ECUDA;
+  c->seg_variant = best;
+  if (chosen) *chosen = best;
+  c->last_stream = strm;
+  c->last_segments = S;
+  return gbs::seg_launch(c, L, best, strm);   // leaves `out` from the chosen variant
+}
+
+gbs_status gbs_segmented_set_variant(gbs_ctx* c, int32_t variant) {
+  if (!c || variant < 0 || variant >= gbs::seg_num_variants()) return GBS_EINVAL;
+  c->seg_variant = variant;
+  return GBS_OK;
+}
+
+gbs_status gbs_segmented_get_variant(gbs_ctx* c, int32_t* variant, int32_t* threads, int32_t* smem_cap,
+                                     int32_t* n_variants) {
+  if (!c) return GBS_EINVAL;
+  if (variant) *variant = c->seg_variant;
+  if (threads) *threads = gbs::seg_variant_threads(c->seg_variant);
+  if (smem_cap) *smem_cap = gbs::seg_variant_cap(c->seg_variant);
+  if (n_variants) *n_variants = gbs::seg_num_variants();
+  return GBS_OK;
+}
+
+gbs_status gbs_segmented_passes(gbs_ctx* c, int32_t* passes, int32_t S) {
+  if (!c || !passes || S < 1 || S > c->last_segments || !c->z) return GBS_EINVAL;
+  gbs::DeviceGuard g(c->device);
+  if (!g.ok) return GBS_ECUDA;
+  if (cudaStreamSynchronize(c->last_stream) != cudaSuccess ||
+      cudaMemcpy(passes, static_cast<int*>(c->z) + c->last_segments, (size_t)S * sizeof(int),
+                 cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return GBS_ECUDA;
+  }
+  return GBS_OK;
+}
+
+}  // extern "C"

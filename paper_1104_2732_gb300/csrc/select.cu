@@ -14,147 +14,13 @@
 #include <cstdint>
 
 #include "common.cuh"
+#include "elem.cuh"
 #include "layout.cuh"
 #include "select.cuh"
 #include "api_internal.h"
 
 namespace gbs {
 
-// ---------------------------------------------------------------------------------
-// Per-type element operations.  cmp(): the value compared against the iterate
-// (IEEE float for float32, the signed integer key for float64).  img(): float32 image
-// used only for the cost partials.
-// ---------------------------------------------------------------------------------
-template <typename T> struct Ops;
-template <> struct Ops<float> {
-  using C = float;
-  using V = float4;
-  static constexpr int kVec = 4;
-  static __device__ __forceinline__ C cmp(float x) { return x; }
-  static __device__ __forceinline__ float img(float x) { return x; }
-  static __device__ __forceinline__ bool is_nan(float x) { return x != x; }
-  static __device__ __forceinline__ bool is_neginf(float x) { return x == -INFINITY; }
-  static __device__ __forceinline__ bool is_posinf(float x) { return x == INFINITY; }
-  static __device__ __forceinline__ bool is_negzero(float x) { return __float_as_uint(x) == 0x80000000u; }
-  static __device__ __forceinline__ bool is_finite(float x) { return fabsf(x) < INFINITY; }
-  static __device__ __forceinline__ float next_up(float v) { return nextafterf(v, INFINITY); }
-  static __device__ __forceinline__ float next_down(float v) { return nextafterf(v, -INFINITY); }
-  static __device__ __forceinline__ float from_double(double v) { return (float)v; }
-  template <typename Fn>
-  static __device__ __forceinline__ void each(const V& r, Fn& f) { f(r.x); f(r.y); f(r.z); f(r.w); }
-  static __device__ __forceinline__ float get(const V& r, int i) {
-    return i == 0 ? r.x : i == 1 ? r.y : i == 2 ? r.z : r.w;
-  }
-};
-template <> struct Ops<double> {
-  using C = long long;
-  using V = double2;
-  static constexpr int kVec = 2;
-  static __device__ __forceinline__ C cmp(double x) { return (long long)skey(x); }
-  static __device__ __forceinline__ float img(double x) {
-    return f64_to_f32_trunc((uint64_t)__double_as_longlong(x));
-  }
-  static __device__ __forceinline__ uint64_t mag(double x) {
-    return (uint64_t)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-  }
-  static __device__ __forceinline__ bool is_nan(double x) { return mag(x) > 0x7FF0000000000000ull; }
-  static __device__ __forceinline__ bool is_neginf(double x) {
-    return (uint64_t)__double_as_longlong(x) == 0xFFF0000000000000ull;
-  }
-  static __device__ __forceinline__ bool is_posinf(double x) {
-    return (uint64_t)__double_as_longlong(x) == 0x7FF0000000000000ull;
-  }
-  static __device__ __forceinline__ bool is_negzero(double x) {
-    return (uint64_t)__double_as_longlong(x) == 0x8000000000000000ull;
-  }
-  static __device__ __forceinline__ bool is_finite(double x) { return mag(x) < 0x7FF0000000000000ull; }
-  // neighbours on the float64 grid (finite v; -0 and +0 both step to +-denorm_min)
-  static __device__ __forceinline__ double next_up(double v) {
-    long long b = __double_as_longlong(v);
-    if ((b & 0x7FFFFFFFFFFFFFFFll) == 0) return __longlong_as_double(1ll);
-    return __longlong_as_double(b >= 0 ? b + 1 : b - 1);
-  }
-  static __device__ __forceinline__ double next_down(double v) {
-    long long b = __double_as_longlong(v);
-    if ((b & 0x7FFFFFFFFFFFFFFFll) == 0) return __longlong_as_double((long long)0x8000000000000001ull);
-    return __longlong_as_double(b >= 0 ? b - 1 : b + 1);
-  }
-  static __device__ __forceinline__ double from_double(double v) { return v; }
-  template <typename Fn>
-  static __device__ __forceinline__ void each(const V& r, Fn& f) { f(r.x); f(r.y); }
-  static __device__ __forceinline__ double get(const V& r, int i) { return i == 0 ? r.x : r.y; }
-};
-
-__device__ __forceinline__ float4 load_stream(const float4* p) { return __ldcs(p); }
-__device__ __forceinline__ double2 load_stream(const double2* p) { return __ldcs(p); }
-
-constexpr int kUnroll = 4;   // vectors in flight per thread in the streaming loops
-
-// Geometry of the streaming loops over x: an unaligned scalar head, 16-byte vectors,
-// a scalar tail.  Shared with the host's region-capacity bound.
-template <typename T>
-struct Geometry {
-  long long head, nv, tail0, n;
-  __device__ __forceinline__ Geometry(const T* x, long long n_) : n(n_) {
-    constexpr int kVec = Ops<T>::kVec;
-    const unsigned long long addr = (unsigned long long)x;
-    head = (long long)(((16u - (addr & 15u)) & 15u) / sizeof(T));
-    if (head > n) head = n;
-    nv = (n - head) / kVec;
-    tail0 = head + nv * kVec;
-  }
-};
-
-// ---------------------------------------------------------------------------------
-// Per-element cores.
-// ---------------------------------------------------------------------------------
-// One element of a cutting-plane pass (Algorithm 1, step 1.2; the figure's Objective()):
-// lt += [x < t], le += [x <= t], S += [a < x < t] * (t - x) * sigma.
-__device__ __forceinline__ void core(float x, float a, float t, float nsig, float tsig, unsigned& lt,
-                                     unsigned& le, float& S) {
-  asm("{\n\t"
-      ".reg .pred p, q, r;\n\t"
-      ".reg .f32 d;\n\t"
-      "setp.lt.f32 p, %3, %5;\n\t"
-      "setp.le.f32 q, %3, %5;\n\t"
-      "setp.gt.and.f32 r, %3, %4, p;\n\t"
-      "fma.rn.f32 d, %3, %6, %7;\n\t"
-      "@p add.u32 %0, %0, 1;\n\t"
-      "@q add.u32 %1, %1, 1;\n\t"
-      "@r add.f32 %2, %2, d;\n\t"
-      "}"
-      : "+r"(lt), "+r"(le), "+f"(S)
-      : "f"(x), "f"(a), "f"(t), "f"(nsig), "f"(tsig));
-}
-// float64: comparisons on signed integer keys, the cost on the truncated float32 image.
-__device__ __forceinline__ void core(double xv, long long sa, long long st, float nsig, float tsig,
-                                     unsigned& lt, unsigned& le, float& S) {
-  const uint64_t u = (uint64_t)__double_as_longlong(xv);
-  const long long sx = (long long)skey_bits(u);
-  lt += (sx < st);
-  le += (sx <= st);
-  const bool in = (sx > sa) & (sx < st);
-  const float d = fmaf(f64_to_f32_trunc(u), nsig, tsig);
-  S += in ? d : 0.f;
-}
-
-template <typename T> __device__ __forceinline__ typename Ops<T>::C cmp_pos_inf();
-template <> __device__ __forceinline__ float cmp_pos_inf<float>() { return INFINITY; }
-template <> __device__ __forceinline__ long long cmp_pos_inf<double>() { return 0x7FF0000000000000ll; }
-
-// value of a comparison key
-__device__ __forceinline__ float cmp_value(float c, float) { return c; }
-__device__ __forceinline__ double cmp_value(long long c, double) { return skey_value(c); }
-
-template <typename T> struct CmpOf;
-template <> struct CmpOf<float> {
-  static __device__ __forceinline__ float of(float v) { return v; }
-};
-template <> struct CmpOf<double> {
-  static __device__ __forceinline__ long long of(double v) { return (long long)skey(v); }
-};
-
-// Scalar head and tail of x handled by this thread (the first threads of CTA 0).
 template <typename T, typename Fn>
 __device__ __forceinline__ void stream_edges(const T* __restrict__ x, const Geometry<T>& g, Fn& f) {
   const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
@@ -251,34 +117,6 @@ __device__ __forceinline__ void stream_chunks_compact(const T* __restrict__ x, c
 
 // Sums up to 6 per-thread values over the CTA in one exchange (fixed order, so every
 // CTA that sums the same data gets the same bits).  Result valid in every thread.
-struct Sum6 {
-  unsigned long long u[5];
-  double d;
-};
-__device__ __forceinline__ Sum6 block_sum6(Sum6 v, Sum6* scratch /* [kWarps + 1] */) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int i = 0; i < 5; ++i) v.u[i] += __shfl_xor_sync(0xffffffffu, v.u[i], o);
-    v.d += __shfl_xor_sync(0xffffffffu, v.d, o);
-  }
-  __syncthreads();
-  if (lane == 0) scratch[w] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    Sum6 r = scratch[0];
-    for (int i = 1; i < kWarps; ++i) {
-#pragma unroll
-      for (int q = 0; q < 5; ++q) r.u[q] += scratch[i].u[q];
-      r.d += scratch[i].d;
-    }
-    scratch[kWarps] = r;
-  }
-  __syncthreads();
-  return scratch[kWarps];
-}
-
 // ---------------------------------------------------------------------------------
 // The kernel.
 // ---------------------------------------------------------------------------------
@@ -295,33 +133,6 @@ struct BracketState {
   long long clt_res;// #(x < result) for the sign of a zero result
   T result;
 };
-
-template <typename T>
-__device__ __forceinline__ T inside(T tt, T a, T b) {
-  if (!(tt > a)) tt = Ops<T>::next_up(a);
-  if (!(tt < b)) tt = Ops<T>::next_down(b);
-  return tt;
-}
-
-// Power-of-two scale keeping per-thread float32 cost partials finite: a thread sums at
-// most `per_thread` terms, each at most `width` in magnitude.
-__device__ __forceinline__ float cost_scale(double width, long long per_thread) {
-  double bound = (double)per_thread * width;
-  if (!(bound > 0.0)) return 1.f;
-  double lim = 8.0e37 / bound;
-  if (lim >= 1.0) return 1.f;
-  int e = ilogb(lim);
-  if (e < -120) e = -120;
-  return ldexpf(1.f, e);
-}
-
-template <typename T> __device__ __forceinline__ bool is_neg_zero_bits(T v);
-template <> __device__ __forceinline__ bool is_neg_zero_bits<float>(float v) {
-  return __float_as_uint(v) == 0x80000000u;
-}
-template <> __device__ __forceinline__ bool is_neg_zero_bits<double>(double v) {
-  return (uint64_t)__double_as_longlong(v) == 0x8000000000000000ull;
-}
 
 // Grid totals of the pass partials in `slot` (identical in every CTA: fixed order).
 struct Totals {

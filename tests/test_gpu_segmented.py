@@ -1,0 +1,179 @@
+"""GPU parity of the segmented batched select against the CPU oracle.
+
+Every segment's result must be bit-identical to oracle.select.select_kth on that
+segment.  Calls go through the C-ABI (ctypes binding).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import select as osel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    c = lib.Context()
+    yield c
+    c.close()
+
+
+def bits(a):
+    return np.asarray(a, dtype=np.float32).view(np.uint32)
+
+
+def make_batch(sizes, seed, gen=None):
+    rng = np.random.default_rng(seed)
+    parts = []
+    for i, n in enumerate(sizes):
+        if gen is None:
+            parts.append((rng.standard_normal(n) * 10 ** rng.uniform(-3, 3) + rng.uniform(-100, 100)).astype(np.float32))
+        else:
+            parts.append(gen(i, n, rng))
+    off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+    x = np.concatenate(parts) if parts else np.zeros(0, np.float32)
+    return x, off
+
+
+def run(ctx, x, off, k=None):
+    xt = torch.from_numpy(x).cuda()
+    ot = torch.from_numpy(off).cuda()
+    kt = torch.from_numpy(k).cuda() if k is not None else None
+    out = ctx.select_segmented(xt, ot, kt)
+    return out.cpu().numpy()
+
+
+def expect(x, off, k=None):
+    S = off.size - 1
+    want = np.empty(S, dtype=np.float32)
+    for s in range(S):
+        seg = x[off[s]:off[s + 1]]
+        kk = int(k[s]) if k is not None else (seg.size + 1) // 2
+        want[s] = osel.select_kth(seg, kk)
+    return want
+
+
+# sizes around every shared-memory capacity of the launch variants
+EDGE_SIZES = [1, 2, 3, 7, 100, 1000, 4095, 12287, 12288, 12289, 24575, 24576, 24577, 49151, 49152, 49153,
+              100003, 300001]
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_segmented_medians_every_variant(ctx, variant):
+    x, off = make_batch(EDGE_SIZES, seed=70)
+    ctx.set_segmented_variant(variant)
+    try:
+        got = run(ctx, x, off)
+        assert ctx.last_stats()["status"] == 0
+    finally:
+        ctx.set_segmented_variant(1)
+    assert np.array_equal(bits(got), bits(expect(x, off)))
+
+
+def test_segmented_random_ranks(ctx):
+    rng = np.random.default_rng(71)
+    sizes = list(rng.integers(1, 200_000, 300))
+    x, off = make_batch(sizes, seed=72)
+    k = np.array([rng.integers(1, n + 1) for n in sizes], dtype=np.int64)
+    got = run(ctx, x, off, k)
+    assert np.array_equal(bits(got), bits(expect(x, off, k)))
+
+
+def test_segmented_extreme_ranks_and_ties(ctx):
+    def gen(i, n, rng):
+        v = rng.integers(-3, 4, n).astype(np.float32)          # heavy ties
+        if n > 10:
+            v[:3] = [np.inf, -np.inf, -0.0]
+            v[3:6] = 0.0
+        return v
+    sizes = [5, 11, 50_000, 20_000, 70_001, 12_300, 13]
+    x, off = make_batch(sizes, seed=73, gen=gen)
+    for mode in ("first", "second", "last", "mid"):
+        k = np.array([{"first": 1, "second": min(2, n), "last": n, "mid": (n + 1) // 2}[mode] for n in sizes],
+                     dtype=np.int64)
+        got = run(ctx, x, off, k)
+        assert np.array_equal(bits(got), bits(expect(x, off, k))), mode
+
+
+def test_segmented_heavy_tailed_segments(ctx):
+    def gen(i, n, rng):
+        return synth.heavy_mixture(synth.HEAVY_FAMILIES[i % 4], n, seed=int(rng.integers(1 << 30)))
+    sizes = [60_000, 250_000, 1_000_000, 30_000, 500_000, 2_000_000]
+    x, off = make_batch(sizes, seed=74, gen=gen)
+    for frac in (0.01, 0.5, 0.99):
+        k = np.array([max(1, int(frac * n)) for n in sizes], dtype=np.int64)
+        got = run(ctx, x, off, k)
+        assert np.array_equal(bits(got), bits(expect(x, off, k))), frac
+
+
+def test_segmented_invalid_segments_are_flagged(ctx, lib):
+    x, off = make_batch([10, 0, 10], seed=75)
+    got = run(ctx, x, off)
+    with pytest.raises(lib.GbsError) as ei:
+        ctx.last_stats()
+    assert ei.value.status == lib.GBS_EINVAL
+    assert np.isnan(got[1])
+    assert bits(got[0]) == bits(expect(x[:10], np.array([0, 10]))[0])
+    y, off2 = make_batch([1000, 1000], seed=76)
+    y[1500] = np.nan
+    got = run(ctx, y, off2)
+    with pytest.raises(lib.GbsError) as ei:
+        ctx.last_stats()
+    assert ei.value.status == lib.GBS_ENAN
+    assert np.isnan(got[1]) and not np.isnan(got[0])
+
+
+def test_segmented_autotune_and_passes(ctx):
+    sizes = list(synth.segment_sizes(256, seed=77))
+    x, off = make_batch(sizes, seed=78)
+    xt, ot = torch.from_numpy(x).cuda(), torch.from_numpy(off).cuda()
+    out = torch.empty(len(sizes), device="cuda")
+    chosen, ms = ctx.autotune_segmented(xt, ot, None, out)
+    assert 0 <= chosen < len(ms) and ms[chosen] > 0 and ms[chosen] == min(m for m in ms if m > 0)
+    assert np.array_equal(bits(out.cpu().numpy()), bits(expect(x, off)))
+    passes = ctx.segmented_passes(len(sizes))
+    cap = ctx.segmented_variant()["smem_cap"]
+    for n, p in zip(sizes, passes):
+        assert (p == 1) if n <= cap else (p >= 2)
+    ctx.set_segmented_variant(1)
+
+
+def test_segmented_graph_capture_replay(ctx):
+    sizes = list(synth.segment_sizes(128, seed=79))
+    x, off = make_batch(sizes, seed=80)
+    xt, ot = torch.from_numpy(x).cuda(), torch.from_numpy(off).cuda()
+    out = torch.zeros(len(sizes), device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx.select_segmented(xt, ot, None, out, stream=s)   # sizes the workspace before capture
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ctx.select_segmented(xt, ot, None, out, stream=s)
+    out.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(bits(out.cpu().numpy()), bits(expect(x, off)))
+    # replay on new data of the same shape
+    x2, _ = make_batch(sizes, seed=81)
+    xt.copy_(torch.from_numpy(x2))
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(bits(out.cpu().numpy()), bits(expect(x2, off)))
+
+
+def test_segmented_full_size_batch_sampled(ctx):
+    """The benchmark batch: 4096 normal arrays, sizes log-uniform in [1e3, 1e6]; every
+    segment above the largest shared-memory capacity and a random sample of the rest are
+    checked against the oracle."""
+    x, off = synth.segmented(4096, seed=5)
+    sizes = np.diff(off)
+    got = run(ctx, x, off)
+    rng = np.random.default_rng(82)
+    check = set(np.nonzero(sizes > 49152)[0][:200].tolist()) | set(rng.choice(4096, 200, replace=False).tolist())
+    for s in sorted(check):
+        seg = x[off[s]:off[s + 1]]
+        assert bits(got[s]) == bits(np.float32(osel.select_kth(seg, (seg.size + 1) // 2))), s
