@@ -143,6 +143,63 @@ def run_reference(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def bench_segmented(gbs, ctx, torch, np, args):
+    """4096 float32 normal arrays, sizes log-uniform in [1e3, 1e6], medians: the batched
+    call captured in a CUDA graph (autotuned launch variant) against a plain loop of
+    single-array selects over the same segments."""
+    import synth
+    x_host, off = synth.segmented(4096, seed=5)
+    S = off.size - 1
+    total = int(off[-1])
+    x = torch.from_numpy(x_host).cuda()
+    ot = torch.from_numpy(off).cuda()
+    out = torch.empty(S, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        chosen, tune_ms = ctx.autotune_segmented(x, ot, None, out, stream=stream)
+        ctx.select_segmented(x, ot, None, out, stream=stream)
+    stream.synchronize()
+    passes = ctx.segmented_passes(S)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        ctx.select_segmented(x, ot, None, out, stream=stream)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(3, args.steps)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    # the plain form: one single-array select per segment
+    outs = torch.empty(S, device="cuda")
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record()
+    for s_ in range(S):
+        n_s = int(off[s_ + 1] - off[s_])
+        ctx.select_kth(x[int(off[s_]):int(off[s_ + 1])], (n_s + 1) // 2, out=outs[s_:s_ + 1])
+    p1.record()
+    torch.cuda.synchronize()
+    plain_ms = p0.elapsed_time(p1)
+    same = bool(torch.equal(out.view(torch.int32), outs.view(torch.int32)))
+    sizes = np.diff(off)
+    big = sizes > ctx.segmented_variant()["smem_cap"]
+    return {
+        "workload": f"{S} float32 normal arrays, sizes log-uniform [1e3, 1e6], total {total} elements, medians",
+        "metric": "selections/s", "value": S / (ms * 1e-3), "gelem_s": total / (ms * 1e-3) / 1e9,
+        "ms_per_batch": ms, "graph": True, "variant": chosen, "variant_ms": tune_ms,
+        "plain_loop_ms": plain_ms, "plain_selections_s": S / (plain_ms * 1e-3),
+        "speedup_vs_plain": plain_ms / ms, "identical_to_plain": same,
+        "mean_passes_large_segments": float(np.mean(np.array(passes)[big])) if big.any() else None,
+        "bytes_read_per_batch": int(sum(p * n * 4 for p, n in zip(passes, sizes))),
+        "achieved_gbs": sum(p * n * 4 for p, n in zip(passes, sizes)) / (ms * 1e-3) / 1e9,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -150,6 +207,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--only-single", action="store_true", help="time the single-array select only")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -274,6 +332,12 @@ def main():
     torch.cuda.synchronize()
     sort_ms = s0.elapsed_time(s1) / 3
 
+    # ---------------- other rows of the hot path ----------------
+    rows = {}
+    if not args.only_single:
+        del pinned
+        rows["segmented"] = bench_segmented(gbs, ctx, torch, np, args)
+
     # ---------------- CPU oracle baseline (rank 0 only) ----------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -310,6 +374,7 @@ def main():
                          "peak_kind": f"{peak_kind} hbm_gbs", "kernel": "select_kernel<float>"},
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
+            "rows": rows,
             "detail": {
                 "ms_per_selection": dict(zip([str(k) for k in ks], sel_ms)),
                 "passes": [r["passes"] for r in records],

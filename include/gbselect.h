@@ -190,6 +190,30 @@ gbs_status gbs_segmented_get_variant(gbs_ctx* ctx, int32_t* variant, int32_t* th
  * memory).  Synchronises that call's stream.  passes: S int32, host. */
 gbs_status gbs_segmented_passes(gbs_ctx* ctx, int32_t* passes, int32_t S);
 
+/* Squared residuals of the linear model (Sec. 5, Eq. (model)) for C candidates:
+ * S[c*n + i] = (y_i - sum_j X[i*p + j] * theta[c*p + j])^2, candidate-major.
+ * X: n x p row-major float32; y: n; theta: p x C column-major (candidate c's p
+ * coefficients contiguous); S: C*n floats; all device.  1 <= p <= 16.
+ * precision 0: float32 FMAs on the CUDA cores; 1: the product X*theta on the tensor
+ * cores as three TF32 products (hi*hi + hi*lo + lo*hi of a two-term split of each
+ * operand, float32 accumulation), which keeps float32 accuracy. */
+gbs_status gbs_residual_sq_f32(gbs_ctx* ctx, const float* X, const float* y, int64_t n, int32_t p,
+                               const float* theta, int32_t C, float* S, int32_t precision, void* stream);
+
+/* LMS and LTS objectives (Sec. 5) of C candidates: lms_out[c] = s_(k_lms) and
+ * lts_out[c] = sum of the h_lts smallest s_i, where s_i are the squared residuals of
+ * candidate c computed as in gbs_residual_sq_f32 (float32) and the LTS sum is accumulated
+ * in float64 (Eq. (med_reg): all s below q = s_(h) plus (h - #(s < q)) q).
+ * lms_out: C floats, lts_out: C doubles, device.  precision as in gbs_residual_sq_f32.
+ * batched 1: one segmented select over all candidates in its trimmed-sum mode (the LMS
+ * rank from the same compacted bracket when it lies inside, else a second batched
+ * select for the few candidates where it does not); batched 0: one single-array select
+ * per candidate and rank plus a summing kernel.  Allocates a C*n-float buffer on first
+ * use (synchronously); 1 <= k_lms, h_lts <= n. */
+gbs_status gbs_lms_lts_f32(gbs_ctx* ctx, const float* X, const float* y, int64_t n, int32_t p, const float* theta,
+                           int32_t C, int64_t k_lms, int64_t h_lts, float* lms_out, double* lts_out,
+                           int32_t precision, int32_t batched, void* stream);
+
 /* Synchronises the stream of the last call on ctx and copies its record to *out. */
 gbs_status gbs_last_stats(gbs_ctx* ctx, gbs_run_stats* out);
 

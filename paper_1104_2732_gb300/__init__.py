@@ -81,6 +81,9 @@ _SIGS = {
     "gbs_segmented_get_variant": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                             C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "gbs_segmented_passes": (C.c_int, [_P, C.POINTER(C.c_int32), C.c_int32]),
+    "gbs_residual_sq_f32": (C.c_int, [_P, _P, _P, _I64, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P]),
+    "gbs_lms_lts_f32": (C.c_int, [_P, _P, _P, _I64, C.c_int32, _P, C.c_int32, _I64, _I64, _P, _P, C.c_int32,
+                                  C.c_int32, _P]),
     "gbs_status_string": (C.c_char_p, [C.c_int]),
 }
 
@@ -267,6 +270,43 @@ class Context:
         buf = (C.c_int32 * int(S))()
         _check(gbs_segmented_passes(self._h, buf, int(S)), "gbs_segmented_passes")
         return list(buf)
+
+    # -------------------------------------------------------------- robust regression
+    def _reg_args(self, X, y, theta):
+        import torch
+        X, y, theta = _as_input(X), _as_input(y), _as_input(theta)
+        for t in (X, y, theta):
+            if t.dtype != torch.float32:
+                raise TypeError("X, y and theta must be float32")
+        n, p = X.shape
+        if theta.dim() != 2 or theta.shape[1] != p:
+            raise ValueError("theta must be (C, p): one row of p coefficients per candidate")
+        return X, y, theta, n, p, theta.shape[0]
+
+    def residual_sq(self, X, y, theta, precision=1, out=None, stream=None):
+        """(C, n) float32 squared residuals (y - X theta_c)^2; theta is (C, p)."""
+        import torch
+        X, y, theta, n, p, Cn = self._reg_args(X, y, theta)
+        if out is None:
+            out = torch.empty(Cn, n, dtype=torch.float32, device=X.device)
+        _check(gbs_residual_sq_f32(self._h, C.c_void_p(X.data_ptr()), C.c_void_p(y.data_ptr()), n, p,
+                                   C.c_void_p(theta.data_ptr()), Cn, C.c_void_p(out.data_ptr()), int(precision),
+                                   _stream_ptr(stream)), "gbs_residual_sq")
+        return out
+
+    def lms_lts(self, X, y, theta, k=None, h=None, precision=1, batched=True, stream=None):
+        """(LMS, LTS) per candidate: s_(k) and the sum of the h smallest s (float64)."""
+        import torch
+        X, y, theta, n, p, Cn = self._reg_args(X, y, theta)
+        k = (n + 1) // 2 if k is None else int(k)
+        h = (n + p + 1) // 2 if h is None else int(h)
+        lms = torch.empty(Cn, dtype=torch.float32, device=X.device)
+        lts = torch.empty(Cn, dtype=torch.float64, device=X.device)
+        _check(gbs_lms_lts_f32(self._h, C.c_void_p(X.data_ptr()), C.c_void_p(y.data_ptr()), n, p,
+                               C.c_void_p(theta.data_ptr()), Cn, k, h, C.c_void_p(lms.data_ptr()),
+                               C.c_void_p(lts.data_ptr()), int(precision), int(bool(batched)), _stream_ptr(stream)),
+               "gbs_lms_lts")
+        return lms, lts
 
     def last_stats(self, raise_on_error=True):
         """Synchronises the last call's stream and returns its record as a dict."""

@@ -32,9 +32,15 @@ struct gbs_ctx {
   int last_grid = 0;
   int seg_variant = 1;          // launch variant of the segmented select (autotuned)
   int last_segments = 0;
+  // LMS / LTS: residual matrix and per-candidate arrays
+  void* lms_buf = nullptr;
+  size_t lms_bytes = 0;
+  int lms_off_C = 0;
+  long long lms_off_n = 0;
 };
 
 // Grows the workspace so that its z area holds at least z_bytes.  Synchronous.
 gbs_status gbs_internal_ensure(gbs_ctx* c, size_t z_bytes);
 // Frees the resources other subsystems attached to the context.
 void gbs_internal_release(gbs_ctx* c);
+void gbs_internal_release_lms(gbs_ctx* c);

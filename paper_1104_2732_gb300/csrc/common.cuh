@@ -103,8 +103,9 @@ struct __align__(128) Ctrl {
   unsigned int bar_gen;
   int abort;
   int status;
-  unsigned long long w_count;     // spare counter
-  unsigned long long pad[13];
+  unsigned long long w_count;     // work-queue head of the segmented launch
+  unsigned long long w_len;       // work-queue length of the segmented launch
+  unsigned long long pad[12];
 };
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {

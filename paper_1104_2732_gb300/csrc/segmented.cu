@@ -27,12 +27,13 @@ constexpr int kSchedBuckets = 64;
 
 // Buckets segment ids by floor(log2(size)), largest bucket first; also checks offsets.
 __global__ void seg_schedule_kernel(const long long* __restrict__ off, int S, int* __restrict__ order,
-                                    Ctrl* ctrl) {
+                                    const int* __restrict__ mask, Ctrl* ctrl) {
   __shared__ unsigned int hist[kSchedBuckets];
   __shared__ unsigned int base[kSchedBuckets];
   for (int i = threadIdx.x; i < kSchedBuckets; i += blockDim.x) hist[i] = 0;
   __syncthreads();
   for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    if (mask && !mask[s]) continue;
     const long long n = off[s + 1] - off[s];
     if (n < 0) atomicCAS(&ctrl->status, 0, (int)GBS_EINVAL);
     const int b = n <= 1 ? 0 : 63 - __clzll((unsigned long long)n);
@@ -45,9 +46,11 @@ __global__ void seg_schedule_kernel(const long long* __restrict__ off, int S, in
       base[i] = acc;
       acc += hist[i];
     }
+    ctrl->w_len = acc;
   }
   __syncthreads();
   for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    if (mask && !mask[s]) continue;
     const long long n = off[s + 1] - off[s];
     const int b = n <= 1 ? 0 : 63 - __clzll((unsigned long long)n);
     order[atomicAdd(&base[kSchedBuckets - 1 - b], 1u)] = s;
@@ -253,12 +256,24 @@ struct SegShared {
   int seg;
   // bracket state (thread 0 writes, all read)
   float a, b, t, m, M, sig, result;
-  long long cle_a, clt_b, cle_b, nneg, npos, nnz, n_nan, clt_res;
+  long long cle_a, clt_b, cle_b, nneg, npos, nnz, n_nan, clt_res, cle_res;
+  long long cle_a0;   // #(x <= a) of the bracket that was compacted
+  float a0, b0;       // that bracket
   double dF, sum;
   int it, use_bisect, stalled, compact, first, phase, how, passes;
 };
 
-template <int B, int CAP>
+// Sum of the elements below q and their number, over this thread's share of buf[0, m)
+// (the whole CTA: reduced into sh.sum6 by the caller).
+template <int B>
+__device__ __forceinline__ void below_sums(const float* buf, int m, float q, float& sum, unsigned int& cnt) {
+  for (int i = threadIdx.x; i < m; i += B) {
+    const float v = buf[i];
+    if (v < q) { sum += v; ++cnt; }
+  }
+}
+
+template <int B, int CAP, bool LTS>
 __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
   extern __shared__ __align__(16) float zb[];   // CAP floats
   __shared__ SegShared sh;
@@ -267,17 +282,19 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
   for (;;) {
     if (tid == 0) {
       const unsigned long long q = atomicAdd(&A.ctrl->w_count, 1ull);
-      sh.seg = q < (unsigned long long)A.S ? A.order[q] : -1;
+      sh.seg = q < A.ctrl->w_len ? A.order[q] : -1;
     }
     __syncthreads();
     const int s = sh.seg;
     if (s < 0) break;
     const long long o0 = A.off[s];
     const long long n = A.off[s + 1] - o0;
-    const long long k = A.kk ? A.kk[s] : (n + 1) / 2;
-    if (n < 1 || k < 1 || k > n) {
+    const long long k = A.kk ? A.kk[s] : (A.k_const > 0 ? A.k_const : (n + 1) / 2);
+    const long long k2 = LTS ? (A.kk2 ? A.kk2[s] : (A.k2_const > 0 ? A.k2_const : (n + 1) / 2)) : 0;
+    if (n < 1 || k < 1 || k > n || (LTS && (k2 < 1 || k2 > n))) {
       if (tid == 0) {
         A.out[s] = NAN;
+        if (LTS) { A.out2[s] = NAN; A.outsum[s] = NAN; A.flags[s] = 0; }
         atomicCAS(&A.ctrl->status, 0, (int)GBS_EINVAL);
         if (A.seg_passes) A.seg_passes[s] = 0;
       }
@@ -301,6 +318,7 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
       if (r6.u[0] > 0) {
         if (tid == 0) {
           A.out[s] = NAN;
+          if (LTS) { A.out2[s] = NAN; A.outsum[s] = NAN; A.flags[s] = 0; }
           atomicCAS(&A.ctrl->status, 0, (int)GBS_ENAN);
           if (A.seg_passes) A.seg_passes[s] = 1;
         }
@@ -309,10 +327,27 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
       }
       const uint32_t key = smem_radix_select<B>(zb, (int)n, (unsigned long long)k, false, 0.f, 0.f, sh.hist,
                                                 &sh.prefix, &sh.known, &sh.rank);
+      const float q = ukey_value(key, 0.f);
       if (tid == 0) {
         if (sh.rank == 0) atomicCAS(&A.ctrl->status, 0, (int)GBS_EINTERNAL);
-        A.out[s] = ukey_value(key, 0.f);
+        A.out[s] = q;
         if (A.seg_passes) A.seg_passes[s] = 1;
+      }
+      if (LTS) {
+        // trimmed sum: the k smallest = everything below q plus (k - #below) copies of q
+        float bs = 0.f;
+        unsigned int bc = 0;
+        below_sums<B>(zb, (int)n, q, bs, bc);
+        Sum6 w6;
+        w6.u[0] = bc; w6.u[1] = w6.u[2] = w6.u[3] = w6.u[4] = 0; w6.d = (double)bs;
+        const Sum6 t6 = cta_sum6<B>(w6, sh.sum6);
+        const uint32_t key2 = smem_radix_select<B>(zb, (int)n, (unsigned long long)k2, false, 0.f, 0.f, sh.hist,
+                                                   &sh.prefix, &sh.known, &sh.rank);
+        if (tid == 0) {
+          A.outsum[s] = t6.d + (double)(k - (long long)t6.u[0]) * (double)q;
+          A.out2[s] = ukey_value(key2, 0.f);
+          A.flags[s] = 0;
+        }
       }
       __syncthreads();
       continue;
@@ -358,7 +393,7 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
         sh.n_nan = (long long)r6.u[0]; sh.nneg = (long long)r6.u[1]; sh.npos = (long long)r6.u[2];
         sh.nnz = (long long)r6.u[3]; sh.sum = r6.d;
         sh.passes = 1; sh.it = 0; sh.use_bisect = 0; sh.stalled = 0; sh.first = 0; sh.phase = 0;
-        sh.how = GBS_HOW_NONE; sh.clt_res = -1; sh.result = 0.f;
+        sh.how = GBS_HOW_NONE; sh.clt_res = -1; sh.cle_res = -1; sh.result = 0.f;
         if (sh.n_nan > 0) {
           sh.phase = 3; sh.result = NAN;
         } else if (k <= sh.nneg) {
@@ -409,24 +444,47 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
       const float ca = sh.a, ct = sh.t, cb = sh.b, nsig = -sh.sig, tsig = sh.t * sh.sig;
       const int first = sh.first, compact = sh.compact;
       unsigned int lt = 0, le = 0, xa = 0, xb = 0;
-      float S = 0.f;
+      float S = 0.f, sle = 0.f;
       auto fcore = [&](float v) { core(v, ca, ct, nsig, tsig, lt, le, S); };
       auto ffirst = [&](float v) {
         core(v, ca, ct, nsig, tsig, lt, le, S);
         xa += (v <= ca);
         xb += (v < cb);
       };
+      // trimmed-sum mode: the compacting pass also sums the elements at or below a
+      auto fcore_s = [&](float v) {
+        core(v, ca, ct, nsig, tsig, lt, le, S);
+        if (v <= ca) sle += v;
+      };
+      auto ffirst_s = [&](float v) {
+        ffirst(v);
+        if (v <= ca) sle += v;
+      };
       auto keep = [&](float v) { return (v > ca) & (v <= cb); };
       if (first) {
-        if (compact) cta_stream_compact<B>(xs, g, ffirst, keep, zb, &sh.zcnt);
-        else cta_stream<B>(xs, g, ffirst);
+        if (compact) {
+          if (LTS) cta_stream_compact<B>(xs, g, ffirst_s, keep, zb, &sh.zcnt);
+          else cta_stream_compact<B>(xs, g, ffirst, keep, zb, &sh.zcnt);
+        } else {
+          cta_stream<B>(xs, g, ffirst);
+        }
       } else {
-        if (compact) cta_stream_compact<B>(xs, g, fcore, keep, zb, &sh.zcnt);
-        else cta_stream<B>(xs, g, fcore);
+        if (compact) {
+          if (LTS) cta_stream_compact<B>(xs, g, fcore_s, keep, zb, &sh.zcnt);
+          else cta_stream_compact<B>(xs, g, fcore, keep, zb, &sh.zcnt);
+        } else {
+          cta_stream<B>(xs, g, fcore);
+        }
       }
       Sum6 v6;
       v6.u[0] = lt; v6.u[1] = le; v6.u[2] = xa; v6.u[3] = xb; v6.u[4] = 0; v6.d = (double)S;
       const Sum6 r6 = cta_sum6<B>(v6, sh.sum6);   // also orders every append before the reads below
+      double sle_tot = 0.0;
+      if (LTS && compact) {
+        Sum6 w6;
+        w6.u[0] = w6.u[1] = w6.u[2] = w6.u[3] = w6.u[4] = 0; w6.d = (double)sle;
+        sle_tot = cta_sum6<B>(w6, sh.sum6).d;
+      }
       if (tid == 0) {   // steps 1.3-1.4
         sh.passes++;
         const long long clt = (long long)r6.u[0], cle = (long long)r6.u[1];
@@ -435,9 +493,9 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
           const long long cle_m = (long long)r6.u[2], clt_M = (long long)r6.u[3];
           sh.first = 0;
           if (cle_m >= k) {
-            sh.phase = 1; sh.result = sh.a; sh.clt_res = sh.nneg; resolved = true;
+            sh.phase = 1; sh.result = sh.a; sh.clt_res = sh.nneg; sh.cle_res = cle_m; resolved = true;
           } else if (clt_M < k) {
-            sh.phase = 1; sh.result = sh.b; sh.clt_res = clt_M; resolved = true;
+            sh.phase = 1; sh.result = sh.b; sh.clt_res = clt_M; sh.cle_res = n - sh.npos; resolved = true;
           } else {
             const double cmn = (double)(cle_m - sh.nneg), cmx = (double)(n - sh.npos - clt_M);
             const double gL = (double)(cle_m - k) + 0.5;
@@ -448,8 +506,11 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
         }
         if (!resolved) {
           const long long pop = sh.cle_b - sh.cle_a;
+          if (compact) {   // the bracket just compacted and the sum below it
+            sh.cle_a0 = sh.cle_a; sh.a0 = sh.a; sh.b0 = sh.b; sh.sum = sle_tot;
+          }
           if (clt < k && k <= cle) {
-            sh.phase = 1; sh.result = sh.t; sh.clt_res = clt;
+            sh.phase = 1; sh.result = sh.t; sh.clt_res = clt; sh.cle_res = cle;
           } else {
             const double gL = (double)(sh.cle_a - k) + 0.5;
             const double dphi = gL * ((double)sh.t - (double)sh.a) + r6.d / (double)sh.sig;
@@ -471,12 +532,57 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
 
     float result = sh.result;
     if (sh.phase == 2) {
-      const uint32_t key = smem_radix_select<B>(zb, (int)sh.zcnt, (unsigned long long)(k - sh.cle_a), true, sh.a,
-                                                sh.b, sh.hist, &sh.prefix, &sh.known, &sh.rank);
+      // the compacted bracket (a0, b0] holds ranks cle_a0 + 1 .. cle_a0 + zcnt
+      const int m = (int)sh.zcnt;
+      const uint32_t key = smem_radix_select<B>(zb, m, (unsigned long long)(k - sh.cle_a0), true, sh.a0, sh.b0,
+                                                sh.hist, &sh.prefix, &sh.known, &sh.rank);
       if (tid == 0 && sh.rank == 0) atomicCAS(&A.ctrl->status, 0, (int)GBS_EINTERNAL);
       result = ukey_value(key, 0.f);
-    } else if (sh.phase == 1 && result == 0.f && sh.clt_res >= 0) {
-      result = (k - sh.clt_res) <= sh.nnz ? -0.f : 0.f;
+      if (LTS) {
+        float bs = 0.f;
+        unsigned int bc = 0;
+        below_sums<B>(zb, m, result, bs, bc);
+        Sum6 w6;
+        w6.u[0] = bc; w6.u[1] = w6.u[2] = w6.u[3] = w6.u[4] = 0; w6.d = (double)bs;
+        const Sum6 t6 = cta_sum6<B>(w6, sh.sum6);
+        const long long below = sh.cle_a0 + (long long)t6.u[0];
+        const bool inside2 = sh.cle_a0 < k2 && k2 <= sh.cle_a0 + m;
+        float r2 = NAN;
+        if (inside2) {
+          const uint32_t key2 = smem_radix_select<B>(zb, m, (unsigned long long)(k2 - sh.cle_a0), true, sh.a0,
+                                                     sh.b0, sh.hist, &sh.prefix, &sh.known, &sh.rank);
+          r2 = ukey_value(key2, 0.f);
+        }
+        if (tid == 0) {
+          A.outsum[s] = sh.sum + t6.d + (double)(k - below) * (double)result;
+          A.out2[s] = r2;
+          A.flags[s] = inside2 ? 0 : 1;
+        }
+      }
+    } else if (sh.phase == 1) {
+      if (result == 0.f && sh.clt_res >= 0) result = (k - sh.clt_res) <= sh.nnz ? -0.f : 0.f;
+      if (LTS) {
+        // resolved by counts: one more pass for the sum below the result
+        const float q = result;
+        float bs = 0.f;
+        unsigned int bc = 0;
+        auto fb = [&](float v) { if (v < q) { bs += v; ++bc; } };
+        cta_stream<B>(xs, g, fb);
+        Sum6 w6;
+        w6.u[0] = bc; w6.u[1] = w6.u[2] = w6.u[3] = w6.u[4] = 0; w6.d = (double)bs;
+        const Sum6 t6 = cta_sum6<B>(w6, sh.sum6);
+        if (tid == 0) {
+          sh.passes++;
+          A.outsum[s] = t6.d + (double)(k - (long long)t6.u[0]) * (double)q;
+          const bool same = sh.clt_res >= 0 && sh.clt_res < k2 && k2 <= sh.cle_res;
+          A.out2[s] = same ? q : NAN;
+          A.flags[s] = same ? 0 : 1;
+        }
+      }
+    } else if (LTS && tid == 0) {
+      A.out2[s] = NAN;
+      A.outsum[s] = NAN;
+      A.flags[s] = 0;
     }
     if (tid == 0) {
       if (sh.phase == 3) atomicCAS(&A.ctrl->status, 0, (int)GBS_ENAN);
@@ -493,12 +599,13 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
 struct Variant {
   int threads, cap;
   void (*kernel)(SegArgs);
+  void (*kernel_lts)(SegArgs);
 };
 const Variant kVariants[] = {
-    {512, 12288, seg_kernel<512, 12288>},
-    {512, 24576, seg_kernel<512, 24576>},
-    {1024, 49152, seg_kernel<1024, 49152>},
-    {256, 12288, seg_kernel<256, 12288>},
+    {512, 12288, seg_kernel<512, 12288, false>, seg_kernel<512, 12288, true>},
+    {512, 24576, seg_kernel<512, 24576, false>, seg_kernel<512, 24576, true>},
+    {1024, 49152, seg_kernel<1024, 49152, false>, seg_kernel<1024, 49152, true>},
+    {256, 12288, seg_kernel<256, 12288, false>, seg_kernel<256, 12288, true>},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -509,31 +616,35 @@ int seg_num_variants() { return kNumVariants; }
 gbs_status seg_launch(gbs_ctx* c, const SegLaunch& L, int variant, cudaStream_t stream) {
   if (variant < 0 || variant >= kNumVariants) return GBS_EINVAL;
   const Variant& v = kVariants[variant];
+  const bool lts = L.outsum != nullptr;
+  void (*kern)(SegArgs) = lts ? v.kernel_lts : v.kernel;
   const size_t smem = (size_t)v.cap * sizeof(float);
-  static bool attr_done[kNumVariants] = {};
-  if (!attr_done[variant]) {
-    if (cudaFuncSetAttribute(v.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  static bool attr_done[2][kNumVariants] = {};
+  if (!attr_done[lts][variant]) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
       cudaGetLastError();
       return GBS_ECUDA;
     }
-    attr_done[variant] = true;
+    attr_done[lts][variant] = true;
   }
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.kernel, v.threads, smem) != cudaSuccess || occ < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, v.threads, smem) != cudaSuccess || occ < 1) {
     cudaGetLastError();
     return GBS_ECUDA;
   }
   const int grid = c->num_sms * occ;
   if (cudaMemsetAsync(L.ctrl, 0, sizeof(Ctrl), stream) != cudaSuccess) return GBS_ECUDA;
-  seg_schedule_kernel<<<1, 1024, 0, stream>>>(L.off, L.S, L.order, L.ctrl);
+  seg_schedule_kernel<<<1, 1024, 0, stream>>>(L.off, L.S, L.order, L.mask, L.ctrl);
   SegArgs A;
   A.x = L.x; A.off = L.off; A.S = L.S; A.kk = L.kk; A.out = L.out; A.order = L.order; A.ctrl = L.ctrl;
   A.maxit = 48;
   A.seg_passes = L.seg_passes;
+  A.k_const = L.k_const; A.k2_const = L.k2_const;
+  A.kk2 = L.kk2; A.out2 = L.out2; A.outsum = L.outsum; A.flags = L.flags;
   // pass-0 sums: a thread adds at most ceil(1e6 / threads) * ... terms of a segment; the
   // scale keeps any float32 partial finite for segments up to 2^31 elements
   A.sigma_stats = std::ldexp(1.0f, -24);
-  v.kernel<<<grid, v.threads, smem, stream>>>(A);
+  kern<<<grid, v.threads, smem, stream>>>(A);
   if (cudaGetLastError() != cudaSuccess) return GBS_ECUDA;
   return GBS_OK;
 }
@@ -557,6 +668,8 @@ gbs_status seg_prepare(gbs_ctx* c, const float* x, const int64_t* off, int32_t S
   L->order = static_cast<int*>(c->z);
   L->seg_passes = static_cast<int*>(c->z) + S;
   L->ctrl = c->ctrl;
+  L->mask = nullptr; L->kk2 = nullptr; L->out2 = nullptr; L->outsum = nullptr; L->flags = nullptr;
+  L->k_const = 0; L->k2_const = 0;
   return GBS_OK;
 }
 }  // namespace

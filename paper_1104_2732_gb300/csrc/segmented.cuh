@@ -18,6 +18,14 @@ struct SegArgs {
   int maxit;
   float sigma_stats;
   int* seg_passes;        // [S] passes over each segment, or nullptr
+  // trimmed-sum mode (LTS): kk holds h; the kernel also writes
+  //   outsum[s] = sum of the h smallest elements and out2[s] = the kk2[s]-th smallest
+  //   when that rank lies in the compacted bracket, else flags[s] = 1
+  const long long* kk2;
+  float* out2;
+  double* outsum;
+  int* flags;
+  long long k_const, k2_const;   // ranks used for every segment when kk / kk2 are null (0: median)
 };
 
 struct SegLaunch {
@@ -29,12 +37,19 @@ struct SegLaunch {
   int* order;
   Ctrl* ctrl;
   int* seg_passes;
+  const int* mask;        // [S]: only segments with mask[s] != 0 are selected (nullptr: all)
+  const long long* kk2;   // trimmed-sum mode (see SegArgs); nullptr otherwise
+  float* out2;
+  double* outsum;
+  int* flags;
+  long long k_const, k2_const;
 };
 
 int seg_num_variants();
 int seg_variant_threads(int v);
 int seg_variant_cap(int v);
-// Enqueues the schedule kernel and the persistent segmented kernel of `variant`.
+// Enqueues the schedule kernel and the persistent segmented kernel of `variant`
+// (trimmed-sum mode when L.outsum is set).
 gbs_status seg_launch(gbs_ctx* c, const SegLaunch& L, int variant, cudaStream_t stream);
 
 }  // namespace gbs

@@ -1,0 +1,149 @@
+"""GPU parity of the LMS / LTS objectives (Sec. 5) against the float64 oracle.
+
+Tolerance: each LMS and LTS must be within 1e-5 relative of the float64 oracle.  The
+squared residuals are float32 (split-precision TF32 x 3 or float32 FMAs); order
+statistics are 1-Lipschitz in the sup norm, so |LMS - LMS64| <= max_i |s_i - s64_i|
+and |LTS - LTS64| <= h max_i |s_i - s64_i|: the tests also check the GPU's residuals
+against float64 and that the GPU's selection on its own residuals is bit-exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import regression as oreg
+from oracle import select as osel
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-5
+# LTS sums: float32 partials of at most a few hundred terms per thread, float64 beyond
+SUM_REL = 2e-6
+
+
+def resid_bound(X, y, th, p, precision):
+    """Bound on |s_gpu - s64| per element: the residual's error is at most
+    c * (|y| + sum_j |x_j theta_j|), c = (p+2) u for float32 FMAs and additionally
+    4 * 2^-22 for the TF32 x 3 products (u = 2^-24); squaring doubles it."""
+    u = 2.0 ** -24
+    c = (p + 2) * u + (4 * 2.0 ** -22 if precision == 1 else 0.0)
+    scale = (np.abs(y)[None, :].astype(np.float64)
+             + (np.abs(X.astype(np.float64)) @ np.abs(th.T.astype(np.float64))).T)
+    r64 = np.abs(oreg.residuals(X, y, th.T)).T
+    d = c * scale
+    return 2 * d * (r64 + d) + u * r64 * r64 + 1e-30
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    c = lib.Context()
+    yield c
+    c.close()
+
+
+def problem(n, p, C, seed):
+    X, y, _ = synth.regression(n, p, seed)
+    th = synth.elemental_thetas(X, y, C, seed + 1)          # (p, C)
+    return X, y, np.ascontiguousarray(th.T)                   # theta as (C, p)
+
+
+def to_dev(*arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_residuals_match_float64(ctx, precision):
+    X, y, th = problem(5003, 8, 70, seed=90)
+    Xt, yt, tt = to_dev(X, y, th)
+    S = ctx.residual_sq(Xt, yt, tt, precision=precision).cpu().numpy()
+    r64 = oreg.residuals(X, y, th.T)                           # (n, C)
+    s64 = (r64 * r64).T
+    assert np.all(np.abs(S - s64) <= resid_bound(X, y, th, 8, precision))
+
+
+@pytest.mark.parametrize("p", [1, 3, 8, 12, 16])
+def test_residual_tensor_core_layout(ctx, p):
+    """TF32 x 3 and float32 FMA residuals agree for every p (fragment layout check)."""
+    X, y, th = problem(777, p, 37, seed=91)
+    Xt, yt, tt = to_dev(X, y, th)
+    a = ctx.residual_sq(Xt, yt, tt, precision=0).cpu().numpy()
+    b = ctx.residual_sq(Xt, yt, tt, precision=1).cpu().numpy()
+    s64 = (oreg.residuals(X, y, th.T) ** 2).T
+    assert np.all(np.abs(a - s64) <= resid_bound(X, y, th, p, 0))
+    assert np.all(np.abs(b - s64) <= resid_bound(X, y, th, p, 1))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("batched", [False, True])
+def test_lms_lts_match_float64_oracle(ctx, precision, batched):
+    n, p, C = 20001, 8, 96
+    X, y, th = problem(n, p, C, seed=92)
+    k, h = (n + 1) // 2, (n + p + 1) // 2
+    Xt, yt, tt = to_dev(X, y, th)
+    lms, lts = ctx.lms_lts(Xt, yt, tt, k=k, h=h, precision=precision, batched=batched)
+    assert ctx.last_stats()["status"] == 0
+    lms, lts = lms.cpu().numpy(), lts.cpu().numpy()
+    want_lms, want_lts = oreg.lms_lts(X, y, th.T, k, h)
+    assert np.all(np.abs(lms - want_lms) <= REL * np.abs(want_lms)), np.max(np.abs(lms / want_lms - 1))
+    assert np.all(np.abs(lts - want_lts) <= REL * np.abs(want_lts)), np.max(np.abs(lts / want_lts - 1))
+    # the selection itself is exact on the GPU's own residuals
+    S = ctx.residual_sq(Xt, yt, tt, precision=precision).cpu().numpy()
+    for c in range(0, C, 7):
+        assert np.float32(lms[c]).view(np.uint32) == np.float32(osel.select_kth(S[c], k)).view(np.uint32)
+        assert lts[c] == pytest.approx(oreg.lts(S[c], h), rel=SUM_REL)
+
+
+def test_lms_lts_special_case_theta_zero(ctx):
+    """p = 1, theta = 0: the residuals are y, LMS = median(y^2) exactly."""
+    n = 9999
+    y = synth.uniform(n, seed=93) - np.float32(0.5)
+    X = np.ones((n, 1), np.float32)
+    th = np.zeros((3, 1), np.float32)
+    Xt, yt, tt = to_dev(X, y, th)
+    for batched in (False, True):
+        lms, lts = ctx.lms_lts(Xt, yt, tt, k=(n + 1) // 2, h=(n + 1) // 2, precision=1, batched=batched)
+        s32 = (y * y).astype(np.float32)
+        assert lms.cpu().numpy()[0] == osel.select_kth(s32, (n + 1) // 2)
+        assert lts.cpu().numpy()[0] == pytest.approx(oreg.lts(s32, (n + 1) // 2), rel=SUM_REL)
+
+
+def test_lms_lts_ranks_far_apart(ctx):
+    """h far from k: the LMS rank lies outside the compacted bracket, the second batched
+    select must supply it."""
+    n, p, C = 50000, 4, 40
+    X, y, th = problem(n, p, C, seed=94)
+    Xt, yt, tt = to_dev(X, y, th)
+    k, h = n // 10, (9 * n) // 10
+    lms, lts = ctx.lms_lts(Xt, yt, tt, k=k, h=h, precision=1, batched=True)
+    S = ctx.residual_sq(Xt, yt, tt, precision=1).cpu().numpy()
+    for c in range(C):
+        assert np.float32(lms.cpu().numpy()[c]).view(np.uint32) == np.float32(osel.select_kth(S[c], k)).view(np.uint32)
+        assert lts.cpu().numpy()[c] == pytest.approx(oreg.lts(S[c], h), rel=SUM_REL)
+
+
+def test_lms_lts_full_size_sampled(ctx):
+    """The benchmark problem: n = 1e6, p = 8, 30% contaminated rows, 2048 elemental
+    candidates; 12 sampled candidates against the float64 oracle."""
+    n, p, C = 1_000_000, 8, 2048
+    X, y, th = problem(n, p, C, seed=6)
+    k, h = (n + 1) // 2, (n + p + 1) // 2
+    Xt, yt, tt = to_dev(X, y, th)
+    lms, lts = ctx.lms_lts(Xt, yt, tt, k=k, h=h, precision=1, batched=True)
+    lms, lts = lms.cpu().numpy(), lts.cpu().numpy()
+    rng = np.random.default_rng(95)
+    for c in rng.choice(C, 12, replace=False):
+        wl, wt = oreg.lms_lts(X, y, th[c:c + 1].T, k, h)
+        assert abs(lms[c] - wl[0]) <= REL * abs(wl[0])
+        assert abs(lts[c] - wt[0]) <= REL * abs(wt[0])
+
+
+def test_lms_lts_rejects_bad_arguments(ctx, lib):
+    X, y, th = problem(100, 8, 4, seed=96)
+    Xt, yt, tt = to_dev(X, y, th)
+    with pytest.raises(lib.GbsError):
+        ctx.lms_lts(Xt, yt, tt, k=0, h=50)
+    with pytest.raises(lib.GbsError):
+        ctx.lms_lts(Xt, yt, tt, k=50, h=101)
+    X17 = torch.zeros(10, 17, device="cuda")
+    with pytest.raises(lib.GbsError):
+        ctx.residual_sq(X17, torch.zeros(10, device="cuda"), torch.zeros(2, 17, device="cuda"))
