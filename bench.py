@@ -200,6 +200,53 @@ def bench_segmented(gbs, ctx, torch, np, args):
     }
 
 
+def bench_lms(gbs, ctx, torch, np, args):
+    """LMS / LTS of 2048 elemental candidates on n = 1e6, p = 8 (30% contaminated rows):
+    the chosen form (TF32 x 3 tensor-core residuals + batched trimmed-sum select) against
+    the plain form (float32 CUDA-core residuals + one single-array select per candidate
+    and rank), with the relative error of sampled candidates against the float64 oracle."""
+    import synth
+    from oracle import regression as oreg
+    n, p, C = 1_000_000, 8, 2048
+    X, y, _ = synth.regression(n, p, 6)
+    th = np.ascontiguousarray(synth.elemental_thetas(X, y, C, 7).T)
+    k, h = (n + 1) // 2, (n + p + 1) // 2
+    Xt, yt, tt = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (X, y, th))
+
+    def timed(precision, batched, reps):
+        ctx.lms_lts(Xt, yt, tt, k=k, h=h, precision=precision, batched=batched)   # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            out = ctx.lms_lts(Xt, yt, tt, k=k, h=h, precision=precision, batched=batched)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    chosen_ms, (lms_c, lts_c) = timed(1, True, max(3, args.steps // 2))
+    plain_ms, (lms_p, lts_p) = timed(0, False, 1)
+    lms_c, lts_c = lms_c.cpu().numpy(), lts_c.cpu().numpy()
+    lms_p, lts_p = lms_p.cpu().numpy(), lts_p.cpu().numpy()
+    rng = np.random.default_rng(8)
+    sample = rng.choice(C, 8, replace=False)
+    err = {"chosen": [0.0, 0.0], "plain": [0.0, 0.0]}
+    for c in sample:
+        wl, wt = oreg.lms_lts(X, y, th[c:c + 1].T, k, h)
+        for name, l, t in (("chosen", lms_c, lts_c), ("plain", lms_p, lts_p)):
+            err[name][0] = max(err[name][0], abs(l[c] / wl[0] - 1))
+            err[name][1] = max(err[name][1], abs(t[c] / wt[0] - 1))
+    return {
+        "workload": "LMS/LTS, n=1e6, p=8, 30% contaminated rows, 2048 elemental candidates, k=(n+1)/2, h=(n+p+1)/2",
+        "metric": "candidates/s", "value": C / (chosen_ms * 1e-3), "ms": chosen_ms,
+        "plain_value": C / (plain_ms * 1e-3), "plain_ms": plain_ms, "speedup_vs_plain": plain_ms / chosen_ms,
+        "max_rel_err_vs_float64": {"lms_chosen": err["chosen"][0], "lts_chosen": err["chosen"][1],
+                                   "lms_plain": err["plain"][0], "lts_plain": err["plain"][1],
+                                   "candidates_sampled": int(sample.size), "target": 1e-5},
+        "residual_bytes_written": C * n * 4,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -337,6 +384,7 @@ def main():
     if not args.only_single:
         del pinned
         rows["segmented"] = bench_segmented(gbs, ctx, torch, np, args)
+        rows["lms_lts"] = bench_lms(gbs, ctx, torch, np, args)
 
     # ---------------- CPU oracle baseline (rank 0 only) ----------------
     cpu = None
