@@ -214,6 +214,50 @@ gbs_status gbs_lms_lts_f32(gbs_ctx* ctx, const float* X, const float* y, int64_t
                            int32_t C, int64_t k_lms, int64_t h_lts, float* lms_out, double* lts_out,
                            int32_t precision, int32_t batched, void* stream);
 
+/* ---- Learned starting bracket (no counterpart in the paper; it replaces the starting
+ * bracket of Algorithm 1, step 0).  A sketch of x -- 1024 samples x[j*floor(n/1024)],
+ * sorted; features: the 32 sample quantiles at sorted positions 16+32i standardised by
+ * the sample mean mu and population spread sd, asinh of the standardised sample min and
+ * max, asinh(mu/sd) and log(sd)/16 -- feeds a 36-64-64-2 MLP with GELU hidden layers
+ * whose outputs (c, omega) propose (mu + sd(c - e^omega), mu + sd(c + e^omega)] for the
+ * median.  With gbs_config.use_learned set and a model loaded, a median select of
+ * n >= 65536 checks the proposal by counts in its first pass (and compacts it when it
+ * holds the answer); a side that fails falls back to the data's extreme.  Results are
+ * identical with or without a model; only the pass count changes.
+ * Parameters: 6658 float32, order W1[64][36], b1[64], W2[64][64], b2[64], W3[2][64], b3[2]. */
+gbs_status gbs_bracket_model_set(gbs_ctx* ctx, const float* weights, int32_t count);   /* host array */
+gbs_status gbs_bracket_model_get(gbs_ctx* ctx, float* weights, int32_t count);         /* host array */
+/* Checkpoint: "GBSBRKT1", u32 version 1, n_in, n_hid, n_out, n_params, u64 Adam step, then
+ * weights, Adam first and second moments (float32, little-endian). */
+gbs_status gbs_bracket_model_save(gbs_ctx* ctx, const char* path);
+gbs_status gbs_bracket_model_load(gbs_ctx* ctx, const char* path);
+/* Sketch features of x (n >= 1024): feat 36 floats, musd {mu, sd} 2 doubles; device. */
+gbs_status gbs_bracket_features_f32(gbs_ctx* ctx, const float* x, int64_t n, float* feat, double* musd,
+                                    void* stream);
+/* Proposed bracket for the median of x: out = {a, b, valid} (3 doubles, device). */
+gbs_status gbs_bracket_propose_f32(gbs_ctx* ctx, const float* x, int64_t n, double* out, void* stream);
+/* Network outputs (c, omega) for B feature rows: F B x 36, out B x 2 (device). */
+gbs_status gbs_bracket_forward(gbs_ctx* ctx, const float* F, int32_t B, float* out, void* stream);
+/* Gradient of the mean batch loss (z - c)^2 + rho_0.99(|z - c| - e^omega),
+ * rho_tau(u) = u (tau - [u < 0]), for B rows F (B x 36) and labels Z (B): grad 6658 floats,
+ * loss 1 double (device). */
+gbs_status gbs_bracket_grad(gbs_ctx* ctx, const float* F, const float* Z, int32_t B, float* grad, double* loss,
+                            void* stream);
+/* Trains the loaded model with Adam (beta 0.9 / 0.999, eps 1e-8) for `steps` batches of
+ * `batch` rows of (F, Z) (device, N rows), reshuffled every epoch from `seed`.
+ * loss_hist: `steps` floats (host) or NULL.  Synchronous. */
+gbs_status gbs_bracket_train(gbs_ctx* ctx, const float* F, const float* Z, int32_t N, int32_t batch,
+                             int32_t steps, float lr, uint64_t seed, float* loss_hist, void* stream);
+/* Training array on the device from Philox4x32-10 (counters (i, j, hi(i), 0), key seed):
+ * family 0 N(0,1); 1 Student-t with integer nu = p0 in [1, 64]; 2 lognormal(0, p0);
+ * 3 N(0,1) replaced with probability p0 by N(p1, p2); then loc + scale * value. */
+gbs_status gbs_generate_training_array_f32(gbs_ctx* ctx, float* x, int64_t n, int32_t family, float p0, float p1,
+                                           float p2, float loc, float scale, uint64_t seed, void* stream);
+/* Raw Philox4x32-10 (Salmon et al., SC'11) for m (counter, key) pairs: counters 4m,
+ * keys 2m, out 4m uint32 (device). */
+gbs_status gbs_philox4x32_10(gbs_ctx* ctx, const uint32_t* counters, const uint32_t* keys, uint32_t* out, int32_t m,
+                             void* stream);
+
 /* Synchronises the stream of the last call on ctx and copies its record to *out. */
 gbs_status gbs_last_stats(gbs_ctx* ctx, gbs_run_stats* out);
 

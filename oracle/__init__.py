@@ -14,5 +14,6 @@ Modules
 select      exact order statistics, counts, the pinball cost, Kelley's cutting plane
 regression  LMS / LTS objectives of robust regression
 bracket     sketch features and the bracket-proposal MLP (float64 forward/backward)
+philox      the Philox4x32-10 counter-based generator (for the training-data generator)
 """
-from . import select, regression, bracket  # noqa: F401
+from . import select, regression, bracket, philox  # noqa: F401

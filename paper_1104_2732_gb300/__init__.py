@@ -84,6 +84,19 @@ _SIGS = {
     "gbs_residual_sq_f32": (C.c_int, [_P, _P, _P, _I64, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P]),
     "gbs_lms_lts_f32": (C.c_int, [_P, _P, _P, _I64, C.c_int32, _P, C.c_int32, _I64, _I64, _P, _P, C.c_int32,
                                   C.c_int32, _P]),
+    "gbs_bracket_model_set": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int32]),
+    "gbs_bracket_model_get": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int32]),
+    "gbs_bracket_model_save": (C.c_int, [_P, C.c_char_p]),
+    "gbs_bracket_model_load": (C.c_int, [_P, C.c_char_p]),
+    "gbs_bracket_features_f32": (C.c_int, [_P, _P, _I64, _P, _P, _P]),
+    "gbs_bracket_propose_f32": (C.c_int, [_P, _P, _I64, _P, _P]),
+    "gbs_bracket_forward": (C.c_int, [_P, _P, C.c_int32, _P, _P]),
+    "gbs_bracket_grad": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P, _P]),
+    "gbs_bracket_train": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_uint64,
+                                    C.POINTER(C.c_float), _P]),
+    "gbs_generate_training_array_f32": (C.c_int, [_P, _P, _I64, C.c_int32, C.c_float, C.c_float, C.c_float,
+                                                  C.c_float, C.c_float, C.c_uint64, _P]),
+    "gbs_philox4x32_10": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P]),
     "gbs_status_string": (C.c_char_p, [C.c_int]),
 }
 
@@ -307,6 +320,84 @@ class Context:
                                C.c_void_p(lts.data_ptr()), int(precision), int(bool(batched)), _stream_ptr(stream)),
                "gbs_lms_lts")
         return lms, lts
+
+    # -------------------------------------------------------------- learned bracket
+    N_PARAMS = 6658
+
+    def set_bracket_model(self, weights):
+        import numpy as np
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).ravel())
+        _check(gbs_bracket_model_set(self._h, w.ctypes.data_as(C.POINTER(C.c_float)), w.size), "gbs_bracket_model_set")
+
+    def get_bracket_model(self):
+        import numpy as np
+        w = np.empty(self.N_PARAMS, dtype=np.float32)
+        _check(gbs_bracket_model_get(self._h, w.ctypes.data_as(C.POINTER(C.c_float)), w.size), "gbs_bracket_model_get")
+        return w
+
+    def save_bracket_model(self, path):
+        _check(gbs_bracket_model_save(self._h, os.fsencode(path)), "gbs_bracket_model_save")
+
+    def load_bracket_model(self, path):
+        _check(gbs_bracket_model_load(self._h, os.fsencode(path)), "gbs_bracket_model_load")
+
+    def bracket_features(self, x, stream=None):
+        import torch
+        x = _as_input(x)
+        feat = torch.empty(36, dtype=torch.float32, device=x.device)
+        musd = torch.empty(2, dtype=torch.float64, device=x.device)
+        _check(gbs_bracket_features_f32(self._h, C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(feat.data_ptr()),
+                                        C.c_void_p(musd.data_ptr()), _stream_ptr(stream)), "gbs_bracket_features")
+        return feat, musd
+
+    def bracket_propose(self, x, stream=None):
+        import torch
+        x = _as_input(x)
+        out = torch.empty(3, dtype=torch.float64, device=x.device)
+        _check(gbs_bracket_propose_f32(self._h, C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(out.data_ptr()),
+                                       _stream_ptr(stream)), "gbs_bracket_propose")
+        return out
+
+    def bracket_forward(self, F, stream=None):
+        import torch
+        F = _as_input(F)
+        out = torch.empty(F.shape[0], 2, dtype=torch.float32, device=F.device)
+        _check(gbs_bracket_forward(self._h, C.c_void_p(F.data_ptr()), F.shape[0], C.c_void_p(out.data_ptr()),
+                                   _stream_ptr(stream)), "gbs_bracket_forward")
+        return out
+
+    def bracket_grad(self, F, Z, stream=None):
+        import torch
+        F, Z = _as_input(F), _as_input(Z)
+        grad = torch.empty(self.N_PARAMS, dtype=torch.float32, device=F.device)
+        loss = torch.empty(1, dtype=torch.float64, device=F.device)
+        _check(gbs_bracket_grad(self._h, C.c_void_p(F.data_ptr()), C.c_void_p(Z.data_ptr()), F.shape[0],
+                                C.c_void_p(grad.data_ptr()), C.c_void_p(loss.data_ptr()), _stream_ptr(stream)),
+               "gbs_bracket_grad")
+        return grad, loss
+
+    def bracket_train(self, F, Z, batch, steps, lr=1e-3, seed=0, stream=None):
+        F, Z = _as_input(F), _as_input(Z)
+        hist = (C.c_float * int(steps))()
+        _check(gbs_bracket_train(self._h, C.c_void_p(F.data_ptr()), C.c_void_p(Z.data_ptr()), F.shape[0], int(batch),
+                                 int(steps), float(lr), int(seed), hist, _stream_ptr(stream)), "gbs_bracket_train")
+        return list(hist)
+
+    def generate_training_array(self, out, family, p0=0.0, p1=0.0, p2=1.0, loc=0.0, scale=1.0, seed=0, stream=None):
+        out = _as_input(out)
+        _check(gbs_generate_training_array_f32(self._h, C.c_void_p(out.data_ptr()), out.numel(), int(family),
+                                               float(p0), float(p1), float(p2), float(loc), float(scale), int(seed),
+                                               _stream_ptr(stream)), "gbs_generate_training_array")
+        return out
+
+    def philox(self, counters, keys, stream=None):
+        import torch
+        counters, keys = _as_input(counters), _as_input(keys)
+        m = counters.numel() // 4
+        out = torch.empty(4 * m, dtype=torch.int32, device=counters.device)
+        _check(gbs_philox4x32_10(self._h, C.c_void_p(counters.data_ptr()), C.c_void_p(keys.data_ptr()),
+                                 C.c_void_p(out.data_ptr()), m, _stream_ptr(stream)), "gbs_philox4x32_10")
+        return out
 
     def last_stats(self, raise_on_error=True):
         """Synchronises the last call's stream and returns its record as a dict."""

@@ -37,6 +37,10 @@ struct gbs_ctx {
   size_t lms_bytes = 0;
   int lms_off_C = 0;
   long long lms_off_n = 0;
+  // bracket-proposal network: weights | Adam m | Adam v | gradient | scalars (device)
+  float* model = nullptr;
+  int model_loaded = 0;
+  long long adam_t = 0;
 };
 
 // Grows the workspace so that its z area holds at least z_bytes.  Synchronous.
@@ -44,3 +48,4 @@ gbs_status gbs_internal_ensure(gbs_ctx* c, size_t z_bytes);
 // Frees the resources other subsystems attached to the context.
 void gbs_internal_release(gbs_ctx* c);
 void gbs_internal_release_lms(gbs_ctx* c);
+void gbs_internal_release_model(gbs_ctx* c);

@@ -109,6 +109,7 @@ extern "C" gbs_status gbs_select_kth_f32_noalloc(const float* x, int64_t n, int6
   A.z_elems = zel;
   A.stats_out = nullptr;
   A.eval_out = nullptr;
+  A.proposal = nullptr;
   // The array keeps the previous call's contents: the barrier and status words must
   // start at zero (the radix histograms are cleared by the kernel itself).
   if (cudaMemsetAsync(A.ctrl, 0, sizeof(Ctrl), strm) != cudaSuccess ||

@@ -1,4 +1,7 @@
 // Per-context resources of the subsystems beyond the single-array select.
 #include "api_internal.h"
 
-void gbs_internal_release(gbs_ctx* c) { gbs_internal_release_lms(c); }
+void gbs_internal_release(gbs_ctx* c) {
+  gbs_internal_release_lms(c);
+  gbs_internal_release_model(c);
+}

@@ -18,6 +18,7 @@
 #include "layout.cuh"
 #include "select.cuh"
 #include "api_internal.h"
+#include "bracket.cuh"
 
 namespace gbs {
 
@@ -128,6 +129,9 @@ struct BracketState {
   float sigma;
   int it, use_bisect, stalled, compact;
   int first;        // 1: the multiplicities of the extremes are still estimates
+  int dfv;          // 1: dF = Phi(b) - Phi(a) is known (else the next iterate bisects)
+  int plain_start;  // 1: the bracket started at the data's extremes
+  int learned;      // proposal: 0 none, 1 used, 2 failed its count check on a side
   int phase;        // 0 run, 1 done, 2 finish, 3 NaN, 4 internal error
   int how;          // GBS_HOW_* of a resolved result
   long long clt_res;// #(x < result) for the sign of a zero result
@@ -231,6 +235,56 @@ __device__ __noinline__ bool stats_pass(const T* __restrict__ x, const Geometry<
   stream_edges(x, geo, f);
   stream_chunks(x, geo, false, f);
   out.mn = mn; out.mx = mx; out.nnan = nnan; out.nneg = nneg; out.npos = npos; out.seen = seen; out.sum = sum;
+  return true;
+}
+
+// Per-thread accumulators of the checks of a proposed bracket (a, b] in pass 0.
+struct ProposalAcc {
+  unsigned int la, lblt, lble;   // #(x <= a), #(x < b), #(x <= b)
+  float sab;                     // sum over a < x < b of (b - x), scaled
+};
+
+// Pass 0 with a proposed bracket: pass 0's work, the counts at a and b, the cost from a
+// to b, and the elements of (a, b] compacted into this CTA's region.
+template <typename T>
+__device__ __noinline__ bool stats_pass_learned(const T* __restrict__ x, const Geometry<T>& geo, float sig,
+                                                float x0s, typename Ops<T>::C ca, typename Ops<T>::C cb,
+                                                float nsab, float bsab, T* __restrict__ zr, unsigned int* s_cnt,
+                                                StatsAcc<T>& out, ProposalAcc& pa) {
+  using C = typename Ops<T>::C;
+  C mn = cmp_pos_inf<T>(), mx = -cmp_pos_inf<T>();
+  unsigned int nnan = 0, nneg = 0, npos = 0, seen = 0, la = 0, lblt = 0, lble = 0;
+  float sum = 0.f, sab = 0.f;
+  auto f = [&](T v) {
+    ++seen;
+    const C cv = CmpOf<T>::of(v);
+    if (Ops<T>::is_finite(v)) {
+      mn = cv < mn ? cv : mn;
+      mx = cv > mx ? cv : mx;
+      sum += fmaf(Ops<T>::img(v), sig, -x0s);
+    } else {
+      nnan += Ops<T>::is_nan(v);
+      nneg += Ops<T>::is_neginf(v);
+      npos += Ops<T>::is_posinf(v);
+    }
+    la += (cv <= ca);
+    lblt += (cv < cb);
+    lble += (cv <= cb);
+    const bool in = (cv > ca) & (cv < cb);
+    const float d = fmaf(Ops<T>::img(v), nsab, bsab);
+    sab += in ? d : 0.f;
+  };
+  auto keep = [&](T v) { const C cv = CmpOf<T>::of(v); return (cv > ca) & (cv <= cb); };
+  if ((long long)blockIdx.x * kThreads + threadIdx.x < geo.head + (geo.n - geo.tail0)) {
+    auto fk = [&](T v) {
+      f(v);
+      if (keep(v)) zr[atomicAdd(s_cnt, 1u)] = v;
+    };
+    stream_edges(x, geo, fk);
+  }
+  stream_chunks_compact(x, geo, false, f, keep, zr, s_cnt);
+  out.mn = mn; out.mx = mx; out.nnan = nnan; out.nneg = nneg; out.npos = npos; out.seen = seen; out.sum = sum;
+  pa.la = la; pa.lblt = lblt; pa.lble = lble; pa.sab = sab;
   return true;
 }
 
@@ -338,6 +392,16 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     return;
   }
 
+  // learned bracket proposal (the same decision in every CTA)
+  T prop_a = T(0), prop_b = T(0);
+  bool prop_ok = false;
+  if (A.proposal != nullptr && A.mode == kModeSelect) {
+    const double pa0 = __ldcg(&A.proposal[0]), pb0 = __ldcg(&A.proposal[1]), pv = __ldcg(&A.proposal[2]);
+    prop_a = Ops<T>::from_double(pa0);
+    prop_b = Ops<T>::from_double(pb0);
+    prop_ok = pv > 0.5 && Ops<T>::is_finite(prop_a) && Ops<T>::is_finite(prop_b) && prop_a < prop_b;
+  }
+
   // ---------------- pass 0: finite extremes, sum, non-finite counts (Sec. 3, step 0) ----------------
   {
     const float sig = A.sigma_stats;
@@ -352,7 +416,20 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     }
     const float x0s = x0 * sig;
     StatsAcc<T> sa;
-    if (!stats_pass<T>(A.x, geo, sig, x0s, sa)) return;
+    ProposalAcc pa;
+    pa.la = pa.lblt = pa.lble = 0; pa.sab = 0.f;
+    float sig_ab = 1.f;
+    if (prop_ok) {
+      sig_ab = cost_scale((double)Ops<T>::img(prop_b) - (double)Ops<T>::img(prop_a), per_thread);
+      if (tid == 0) s_zcnt = 0;
+      __syncthreads();
+      if (!stats_pass_learned<T>(A.x, geo, sig, x0s, CmpOf<T>::of(prop_a), CmpOf<T>::of(prop_b), -sig_ab,
+                                 Ops<T>::img(prop_b) * sig_ab, A.z + region_start(bid, nch, G, Ops<T>::kVec),
+                                 &s_zcnt, sa, pa))
+        return;
+    } else {
+      if (!stats_pass<T>(A.x, geo, sig, x0s, sa)) return;
+    }
     C mn = sa.mn, mx = sa.mx;
     const unsigned int nnan = sa.nnan, nneg = sa.nneg, npos = sa.npos, seen = sa.seen;
     const float sum = sa.sum;
@@ -372,6 +449,13 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     const unsigned long long b_fin = block_sum<unsigned long long>(nfin, s_u64);
     const double own = (double)sum / (double)sig + (double)nfin * (double)x0;
     const double b_sum = block_sum<double>(own, s_f64);
+    Sum6 p6;
+    p6.u[0] = pa.la; p6.u[1] = pa.lblt; p6.u[2] = pa.lble; p6.u[3] = 0; p6.u[4] = 0; p6.d = (double)pa.sab;
+    if (prop_ok) {
+      __syncthreads();
+      p6.u[3] = tid == 0 ? s_zcnt : 0u;
+    }
+    const Sum6 b6 = prop_ok ? block_sum6(p6, s_sum6) : p6;
     if (tid == 0) {
       C bm = s_m[0], bM = s_M[0];
       for (int w = 1; w < kWarps; ++w) {
@@ -382,6 +466,8 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
       sp.n_nan = b_nan; sp.n_neginf = b_neg; sp.n_posinf = b_pos; sp.n_negzero = 0; sp.n_finite = b_fin;
       sp.mn = (double)cmp_value(bm, T()); sp.mx = (double)cmp_value(bM, T());
       sp.c_mn = 0; sp.c_mx = 0; sp.sum = b_sum;
+      sp.c_le_a = b6.u[0]; sp.c_lt_b = b6.u[1]; sp.c_le_b = b6.u[2]; sp.c_reg = b6.u[3];
+      sp.s_ab = b6.d / (double)sig_ab;
       A.spart[bid] = sp;
     }
   }
@@ -413,10 +499,22 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     __shared__ double s_mm[kWarps], s_MM[kWarps];
     if (lane == 0) { s_mm[tid >> 5] = m; s_MM[tid >> 5] = M; }
     const Sum6 r = block_sum6(v, s_sum6);   // its barriers also publish s_mm / s_MM
+    Sum6 w;
+    w.u[0] = w.u[1] = w.u[2] = w.u[3] = w.u[4] = 0;
+    w.d = 0.0;
+    if (prop_ok) {
+      for (unsigned int i = tid; i < G; i += kThreads) {
+        const StatsPartial* p = &A.spart[i];
+        w.u[0] += __ldcg(&p->c_le_a); w.u[1] += __ldcg(&p->c_lt_b); w.u[2] += __ldcg(&p->c_le_b);
+        w.u[3] += __ldcg(&p->c_reg); w.d += __ldcg(&p->s_ab);
+      }
+      w = block_sum6(w, s_sum6);
+    }
     if (tid == 0) {
       StatsPartial t;
       t.n_nan = r.u[0]; t.n_neginf = r.u[1]; t.n_posinf = r.u[2]; t.n_finite = r.u[3];
       t.n_negzero = 0; t.c_mn = t.c_mx = 0; t.sum = r.d;
+      t.c_le_a = w.u[0]; t.c_lt_b = w.u[1]; t.c_le_b = w.u[2]; t.c_reg = w.u[3]; t.s_ab = w.d;
       t.mn = s_mm[0]; t.mx = s_MM[0];
       for (int w = 1; w < kWarps; ++w) {
         t.mn = s_mm[w] < t.mn ? s_mm[w] : t.mn;
@@ -452,6 +550,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
   if (tid == 0) {
     BracketState<T> br;
     br.it = 0; br.use_bisect = 0; br.stalled = 0; br.compact = 0; br.phase = 0; br.first = 0;
+    br.dfv = 1; br.plain_start = 1; br.learned = 0;
     br.how = GBS_HOW_NONE; br.clt_res = -1;
     br.result = T(0); br.sigma = 1.f;
     br.a = T(0); br.b = T(0); br.t = T(0); br.cle_a = 0; br.clt_b = 0; br.cle_b = 0; br.dF = 0.0;
@@ -475,6 +574,27 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
         const double gL = (double)(br.cle_a - k) + 0.5;
         const double inner = st.sum - (double)m - (double)M;
         br.dF = gL * ((double)M - (double)m) + (double)(br.clt_b - br.cle_a) * (double)M - inner;
+        if (prop_ok) {
+          // the proposed bracket (a, b] was checked by counts in pass 0
+          const long long pla = (long long)st.c_le_a, plb_lt = (long long)st.c_lt_b, plb = (long long)st.c_le_b;
+          const bool va = pla < k, vb = k <= plb;
+          br.learned = (va && vb) ? 1 : 2;
+          if (va && vb && plb_lt < k) {          // x_(k) is b itself
+            br.phase = 1; br.result = prop_b; br.how = GBS_HOW_HIT; br.clt_res = plb_lt;
+          } else if (va && vb) {
+            br.a = prop_a; br.b = prop_b; br.cle_a = pla; br.clt_b = plb_lt; br.cle_b = plb;
+            br.first = 0; br.plain_start = 0;
+            br.dF = ((double)(pla - k) + 0.5) * ((double)prop_b - (double)prop_a) + st.s_ab;
+            if (plb - pla <= A.cap)                // already compacted: straight to the finish
+              br.phase = ((long long)st.c_reg == plb - pla) ? 2 : 4;
+          } else if (vb) {                       // (m, b]: a falls back to the minimum
+            br.b = prop_b; br.clt_b = plb_lt; br.cle_b = plb; br.plain_start = 0; br.dfv = 0;
+          } else if (va) {                       // (a, M]: b falls back to the maximum
+            br.a = prop_a; br.cle_a = pla; br.first = 0; br.plain_start = 0; br.dfv = 0;
+            // #(x < M) is still an estimate: the next pass bisects and counts it exactly
+            br.first = 1;
+          }
+        }
       }
     }
     s_br = br;
@@ -491,7 +611,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
       const double gL = (double)(br.cle_a - k) + 0.5;
       const double gR = (double)(br.clt_b - k) + 0.5;
       T t;
-      if (br.use_bisect) {
+      if (br.use_bisect || !br.dfv) {
         const U ka = ukey(br.a), kb = ukey(br.b);
         const U mid = ka + (kb - ka) / 2;
         t = inside<T>(ukey_value(mid, T()), br.a, br.b);
@@ -558,10 +678,12 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
           nb.phase = 1; nb.result = br.b; nb.how = GBS_HOW_MAX; nb.clt_res = clt_M; resolved = true;
         } else {
           nb.cle_a = cle_m; nb.clt_b = clt_M;
-          const double cmn = (double)(cle_m - nneg), cmx = (double)(n - npos - clt_M);
-          const double gL = (double)(cle_m - k) + 0.5;
-          const double inner = st.sum - cmn * (double)br.a - cmx * (double)br.b;
-          nb.dF = gL * ((double)br.b - (double)br.a) + (double)(clt_M - cle_m) * (double)br.b - inner;
+          if (br.plain_start) {
+            const double cmn = (double)(cle_m - nneg), cmx = (double)(n - npos - clt_M);
+            const double gL = (double)(cle_m - k) + 0.5;
+            const double inner = st.sum - cmn * (double)br.a - cmx * (double)br.b;
+            nb.dF = gL * ((double)br.b - (double)br.a) + (double)(clt_M - cle_m) * (double)br.b - inner;
+          }
         }
         if (resolved && bid == 0 && br.it < kMaxIt) s_pops[br.it] = 0;
       }
@@ -576,7 +698,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
           if (cle < k) {
             nb.a = br.t; nb.cle_a = cle; nb.dF = nb.dF - dphi;
           } else {
-            nb.b = br.t; nb.clt_b = clt; nb.cle_b = cle; nb.dF = dphi;
+            nb.b = br.t; nb.clt_b = clt; nb.cle_b = cle; nb.dF = dphi; nb.dfv = 1;
           }
           const long long npop = nb.cle_b - nb.cle_a;
           if (bid == 0 && br.it < kMaxIt) s_pops[br.it] = npop;
@@ -606,7 +728,8 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     // ---------------- exact finish: radix select inside (a, b] ----------------
     const int slot = (pass - 1) & 1;
     // region offsets (exclusive prefix of the per-CTA compaction counts)
-    for (unsigned int i = tid; i < G; i += kThreads) s_off[i + 1] = __ldcg(&A.part[slot * G + i].c_reg);
+    for (unsigned int i = tid; i < G; i += kThreads)
+      s_off[i + 1] = pass == 0 ? __ldcg(&A.spart[i].c_reg) : __ldcg(&A.part[slot * G + i].c_reg);
     if (tid == 0) s_off[0] = 0;
     __syncthreads();
     if (tid == 0) {
@@ -726,7 +849,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     rs->bisect_steps = s_nb;
     rs->finish_rounds = rounds;
     rs->grid = (int)G;
-    rs->learned = 0;
+    rs->learned = fin.learned;
     rs->n = n; rs->k = k;
     rs->finish_pop = fpop;
     const int ni = pass < kMaxIt ? pass : kMaxIt;
@@ -776,6 +899,13 @@ float stats_sigma(long long n, int grid) {
   return std::ldexp(1.0f, -(e + 2));
 }
 
+inline gbs_status launch_propose(gbs_ctx* c, const float* x, long long n, double* p, cudaStream_t s) {
+  return launch_propose_f32(c, x, n, p, s);
+}
+inline gbs_status launch_propose(gbs_ctx* c, const double* x, long long n, double* p, cudaStream_t s) {
+  return launch_propose_f64(c, x, n, p, s);
+}
+
 template <typename T>
 gbs_status launch_select(gbs_ctx* c, const T* x, long long n, long long k, T* out, int mode,
                                 double a, double t, gbs_array_stats* sout, gbs_cost_eval* eout,
@@ -797,9 +927,15 @@ gbs_status launch_select(gbs_ctx* c, const T* x, long long n, long long k, T* ou
   A.ctrl = c->ctrl; A.part = c->part; A.spart = c->spart; A.ghist = c->ghist;
   A.z = reinterpret_cast<T*>(c->z); A.z_elems = zel;
   A.rs = c->rs; A.stats_out = sout; A.eval_out = eout;
+  A.proposal = nullptr;
   if (cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), stream) != cudaSuccess) return GBS_ECUDA;
   if (mode == kModeSelect && cudaMemsetAsync(c->rs, 0, sizeof(gbs_run_stats), stream) != cudaSuccess)
     return GBS_ECUDA;
+  // learned starting bracket for a median of a large enough array
+  if (mode == kModeSelect && c->cfg.use_learned && c->model_loaded && k == (n + 1) / 2 && n >= kLearnMinN) {
+    double* prop = reinterpret_cast<double*>(c->aux);
+    if (launch_propose(c, x, n, prop, stream) == GBS_OK) A.proposal = prop;
+  }
   void* args[] = {&A};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)select_kernel<T>, dim3(grid), dim3(kThreads), args,
                                               0, stream);

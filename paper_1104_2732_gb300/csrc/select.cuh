@@ -26,6 +26,10 @@ struct __align__(16) StatsPartial {
   unsigned long long c_mn, c_mx;   // multiplicities of the finite min / max (IEEE equality)
   double mn, mx;                   // finite min / max (+inf / -inf if none)
   double sum;                      // sum of the finite elements
+  // a proposed bracket (a, b] checked in pass 0
+  unsigned long long c_le_a, c_lt_b, c_le_b;   // #(x <= a), #(x < b), #(x <= b)
+  unsigned long long c_reg;                    // elements of (a, b] this CTA compacted
+  double s_ab;                                 // sum over a < x < b of (b - x)
 };
 
 template <typename T>
@@ -46,6 +50,7 @@ struct SelArgs {
   T* z;                            // compaction area, regions at region_start(g)
   long long z_elems;               // its size in elements
   gbs_run_stats* rs;               // device record of this call
+  const double* proposal;          // learned bracket {a, b, valid} for pass 0, or nullptr
   gbs_array_stats* stats_out;      // kModeStats
   gbs_cost_eval* eval_out;         // kModeEval
 };

@@ -76,3 +76,14 @@ def test_sketch_indexing_and_features():
 def test_constant_array_features_finite():
     f, mu, sd = ob.sketch_features(np.full(4096, 2.5, dtype=np.float32))
     assert sd == 1.0 and np.all(np.isfinite(f))
+
+
+def test_philox_known_answer_vectors():
+    """Philox4x32-10 against the published known-answer vectors (Random123, Salmon et al.)."""
+    import json
+    import os
+    from oracle.philox import philox4x32_10
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.json")))
+    for v in g["vectors"]:
+        out = philox4x32_10([int(c, 16) for c in v["counter"]], [int(k, 16) for k in v["key"]])
+        assert ["%08x" % o for o in out] == v["output"]
