@@ -247,6 +247,78 @@ def bench_lms(gbs, ctx, torch, np, args):
     }
 
 
+def bench_learned(gbs, ctx, torch, np, args, x_big=None):
+    """Median select from the data's extremes against the same select started from the
+    trained network's proposed bracket (results must be identical), on (1) held-out
+    arrays of the training distribution (generator seeds 2e6 + i, n in [2^20, 2^24]) with
+    L2 flushed before every timed select, and (2) the 2^27 single-array workload."""
+    from paper_1104_2732_gb300 import train_bracket as tb
+    model = os.path.join(ROOT, "paper_1104_2732_gb300", "bracket_model.bin")
+    if not os.path.exists(model):
+        return {"unavailable": "no trained model"}
+    ctx.load_bracket_model(model)
+    flush = torch.empty(1 << 26, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+    count = 200
+    rng = np.random.default_rng(2 * 10 ** 6)
+    buf = torch.empty(1 << 24, device="cuda")
+    outs = torch.empty(2, device="cuda")
+    passes = {0: [], 1: []}
+    ms = {0: 0.0, 1: 0.0}
+    elems = 0
+    same = True
+    used = 0
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for i in range(count):
+        n, fam, p0, p1, p2, loc, scale = tb.draw_params(rng)
+        x = buf[:n]
+        ctx.generate_training_array(x, fam, p0, p1, p2, loc, scale, seed=2 * 10 ** 6 + i)
+        k = (n + 1) // 2
+        elems += n
+        for mode in (0, 1):
+            ctx.set_config(use_learned=mode)
+            flush.zero_()
+            ev[0].record()
+            ctx.select_kth(x, k, out=outs[mode:mode + 1])
+            ev[1].record()
+            st = ctx.last_stats()      # synchronises
+            ms[mode] += ev[0].elapsed_time(ev[1])
+            passes[mode].append(st["passes"])
+            used += int(mode == 1 and st["learned"] == 1)
+        same = same and bool(outs[0].view(torch.int32) == outs[1].view(torch.int32))
+    row = {
+        "workload": f"{count} held-out arrays, n log-uniform [2^20, 2^24], normal / Student-t / lognormal / "
+                    "contaminated, random location and scale; medians; L2 flushed before each select",
+        "metric": "selections/s", "value": count / (ms[1] * 1e-3), "plain_value": count / (ms[0] * 1e-3),
+        "speedup_vs_plain": ms[0] / ms[1],
+        "mean_passes_learned": float(np.mean(passes[1])), "mean_passes_plain": float(np.mean(passes[0])),
+        "p90_passes_learned": float(np.percentile(passes[1], 90)),
+        "p90_passes_plain": float(np.percentile(passes[0], 90)),
+        "proposal_valid_fraction": used / count, "identical_results": same,
+        "gelem_s_learned": elems / (ms[1] * 1e-3) / 1e9, "gelem_s_plain": elems / (ms[0] * 1e-3) / 1e9,
+    }
+    if x_big is not None:
+        n = x_big.numel()
+        k = (n + 1) // 2
+        res = {}
+        for mode in (0, 1):
+            ctx.set_config(use_learned=mode)
+            for _ in range(2):
+                ctx.select_kth(x_big, k, out=outs[mode:mode + 1])
+            torch.cuda.synchronize()
+            ev[0].record()
+            for _ in range(5):
+                ctx.select_kth(x_big, k, out=outs[mode:mode + 1])
+            ev[1].record()
+            st = ctx.last_stats()
+            res[mode] = (ev[0].elapsed_time(ev[1]) / 5, st["passes"], st["learned"])
+        row["median_2e27"] = {"ms_plain": res[0][0], "ms_learned": res[1][0], "passes_plain": res[0][1],
+                              "passes_learned": res[1][1], "proposal": res[1][2],
+                              "speedup": res[0][0] / res[1][0],
+                              "identical": bool(outs[0].view(torch.int32) == outs[1].view(torch.int32))}
+    ctx.set_config(use_learned=0)
+    return row
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -385,6 +457,7 @@ def main():
         del pinned
         rows["segmented"] = bench_segmented(gbs, ctx, torch, np, args)
         rows["lms_lts"] = bench_lms(gbs, ctx, torch, np, args)
+        rows["learned_bracket"] = bench_learned(gbs, ctx, torch, np, args, x_big=x)
 
     # ---------------- CPU oracle baseline (rank 0 only) ----------------
     cpu = None

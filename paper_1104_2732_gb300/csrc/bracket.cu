@@ -99,60 +99,70 @@ __device__ __forceinline__ float gelu_grad(float u) {
 
 // Sketch of x in one CTA of 1024 threads: features (36 floats) into f, mean and spread
 // into *mu, *sd.  Returns false (in every thread) if a sample is not finite or n < 1024.
+// The sample is sorted on its totalOrder keys (integer compares; the float64 pipe of this
+// GPU is narrow): a bitonic network whose stages of distance < 32 run in registers by
+// warp shuffles and whose 15 longer stages go through a double-buffered shared array.
+// One warp then forms the float64 mean, spread and quantile features.
 template <typename T>
-__device__ bool sketch(const T* __restrict__ x, long long n, double* sv, float* f, double* red, double* mu,
-                       double* sd, int* bad) {
-  const int tid = threadIdx.x;
-  if (tid == 0) *bad = n < kSample ? 1 : 0;
-  __syncthreads();
-  if (*bad) return false;
+__device__ bool sketch(const T* __restrict__ x, long long n, double* sv, float* f, double* mu, double* sd) {
+  using K = decltype(ukey(T()));
+  __shared__ K kb[2][kSample];
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (n < kSample) return false;
   const long long stride = n / kSample;
-  const double v = (double)x[tid * stride];
-  if (!isfinite(v)) *bad = 1;
-  sv[tid] = v;
-  __syncthreads();
-  if (*bad) return false;
-  for (int k = 2; k <= kSample; k <<= 1) {     // bitonic sort, ascending
+  const T v = x[tid * stride];
+  if (__syncthreads_or(!isfinite(v))) return false;
+  K key = ukey(v);
+  int buf = 0;
+  for (int k = 2; k <= kSample; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
-      const int p = tid ^ j;
-      if (p > tid) {
-        const double a = sv[tid], b = sv[p];
-        const bool up = (tid & k) == 0;
-        if (up ? (a > b) : (a < b)) { sv[tid] = b; sv[p] = a; }
+      K other;
+      if (j >= 32) {
+        kb[buf][tid] = key;
+        __syncthreads();
+        other = kb[buf][tid ^ j];
+        buf ^= 1;
+      } else {
+        other = __shfl_xor_sync(0xffffffffu, key, j);
       }
-      __syncthreads();
+      const bool keep_min = ((tid & j) == 0) == ((tid & k) == 0);
+      key = keep_min ? (other < key ? other : key) : (other > key ? other : key);
     }
   }
-  // mean and population spread of the sample (fixed-order tree)
-  double s = sv[tid];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((tid & 31) == 0) red[tid >> 5] = s;
+  sv[tid] = (double)ukey_value(key, T());
   __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int w = 0; w < 32; ++w) t += red[w];
-    *mu = t / kSample;
+  if (tid < 32) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int i = 0; i < kSample / 32; i += 4) {
+      s0 += sv[(i + 0) * 32 + lane];
+      s1 += sv[(i + 1) * 32 + lane];
+      s2 += sv[(i + 2) * 32 + lane];
+      s3 += sv[(i + 3) * 32 + lane];
+    }
+    double s = (s0 + s1) + (s2 + s3);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const double m = s / kSample;
+    double q0 = 0.0, q1 = 0.0;
+    for (int i = 0; i < kSample / 32; i += 2) {
+      const double d0 = sv[i * 32 + lane] - m, d1 = sv[(i + 1) * 32 + lane] - m;
+      q0 = fma(d0, d0, q0);
+      q1 = fma(d1, d1, q1);
+    }
+    double q = q0 + q1;
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    double d = sqrt(q / kSample);
+    d = d > 0.0 ? d : 1.0;
+    f[lane] = (float)((sv[16 + 32 * lane] - m) / d);           // 32 quantiles (kQuant == 32)
+    if (lane < 3) {
+      const double z = lane == 0 ? (sv[0] - m) / d : lane == 1 ? (sv[kSample - 1] - m) / d : m / d;
+      f[32 + lane] = asinhf((float)z);
+    }
+    if (lane == 3) f[35] = logf((float)d) * (1.0f / 16.0f);
+    if (lane == 0) {
+      *mu = m;
+      *sd = d;
+    }
   }
-  __syncthreads();
-  const double dmu = sv[tid] - *mu;
-  double q = dmu * dmu;
-  for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-  __syncthreads();
-  if ((tid & 31) == 0) red[tid >> 5] = q;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int w = 0; w < 32; ++w) t += red[w];
-    double d = sqrt(t / kSample);
-    *sd = d > 0.0 ? d : 1.0;
-  }
-  __syncthreads();
-  const double m = *mu, d = *sd;
-  if (tid < kQuant) f[tid] = (float)((sv[16 + 32 * tid] - m) / d);
-  if (tid == 32) f[32] = (float)asinh((sv[0] - m) / d);
-  if (tid == 33) f[33] = (float)asinh((sv[kSample - 1] - m) / d);
-  if (tid == 34) f[34] = (float)asinh(m / d);
-  if (tid == 35) f[35] = (float)(log(d) / 16.0);
   __syncthreads();
   return true;
 }
@@ -181,20 +191,75 @@ __device__ void mlp_forward_cta(const float* __restrict__ W, const float* f, flo
 }
 
 // Proposed bracket {a, b, valid} for the median of x.
+// The same network evaluated by a CTA of 1024 threads: warp w computes outputs w and
+// w + 32 of each hidden layer (and output w of the last, for w < 2), its lanes splitting
+// the dot product.  Each warp loads its weight rows into registers (coalesced) before the
+// sketch, so that their latency hides behind the sort.
+struct WarpRows {
+  float w1[2][2], w2[2][2], w3[2], b1[2], b2[2], b3;
+  __device__ void load(const float* __restrict__ W) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int j = warp + 32 * r;
+      w1[r][0] = W[kOffW1 + j * kIn + lane];
+      w1[r][1] = lane + 32 < kIn ? W[kOffW1 + j * kIn + 32 + lane] : 0.f;
+      w2[r][0] = W[kOffW2 + j * kHid + lane];
+      w2[r][1] = W[kOffW2 + j * kHid + 32 + lane];
+      b1[r] = W[kOffB1 + j];
+      b2[r] = W[kOffB2 + j];
+    }
+    const int o = warp < kOut ? warp : 0;
+    w3[0] = W[kOffW3 + o * kHid + lane];
+    w3[1] = W[kOffW3 + o * kHid + 32 + lane];
+    b3 = W[kOffB3 + o];
+  }
+};
+
+__device__ __forceinline__ float warp_dot(float a0, float a1, const float* v, int len) {
+  const int lane = threadIdx.x & 31;
+  float u = a0 * v[lane];
+  if (lane + 32 < len) u = fmaf(a1, v[lane + 32], u);
+  for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+  return u;
+}
+
+__device__ void mlp_forward_warps(const WarpRows& R, const float* f, float* h1, float* h2, float* o) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const float u = warp_dot(R.w1[r][0], R.w1[r][1], f, kIn);
+    if (lane == 0) h1[warp + 32 * r] = gelu(u + R.b1[r]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const float u = warp_dot(R.w2[r][0], R.w2[r][1], h1, kHid);
+    if (lane == 0) h2[warp + 32 * r] = gelu(u + R.b2[r]);
+  }
+  __syncthreads();
+  if (warp < kOut) {
+    const float u = warp_dot(R.w3[0], R.w3[1], h2, kHid);
+    if (lane == 0) o[warp] = u + R.b3;
+  }
+  __syncthreads();
+}
+
+// Proposal for the median of x: prop = {a, b, valid} (one CTA of 1024 threads).
 template <typename T>
 __global__ void __launch_bounds__(1024) propose_kernel(const T* __restrict__ x, long long n,
                                                        const float* __restrict__ W, double* __restrict__ prop) {
   __shared__ double sv[kSample];
-  __shared__ double red[32];
   __shared__ float f[kIn], h1[kHid], h2[kHid], o[kOut];
   __shared__ double mu, sd;
-  __shared__ int bad;
-  const bool ok = sketch<T>(x, n, sv, f, red, &mu, &sd, &bad);
+  WarpRows R;
+  R.load(W);
+  const bool ok = sketch<T>(x, n, sv, f, &mu, &sd);
   if (!ok) {
     if (threadIdx.x == 0) { prop[0] = 0.0; prop[1] = 0.0; prop[2] = 0.0; }
     return;
   }
-  mlp_forward_cta(W, f, h1, h2, o);
+  mlp_forward_warps(R, f, h1, h2, o);
   if (threadIdx.x == 0) {
     const double c = o[0];
     const double om = fmin(fmax((double)o[1], -30.0), 30.0);
@@ -212,11 +277,9 @@ template <typename T>
 __global__ void __launch_bounds__(1024) features_kernel(const T* __restrict__ x, long long n,
                                                         float* __restrict__ feat, double* __restrict__ musd) {
   __shared__ double sv[kSample];
-  __shared__ double red[32];
   __shared__ float f[kIn];
   __shared__ double mu, sd;
-  __shared__ int bad;
-  const bool ok = sketch<T>(x, n, sv, f, red, &mu, &sd, &bad);
+  const bool ok = sketch<T>(x, n, sv, f, &mu, &sd);
   if (threadIdx.x < kIn) feat[threadIdx.x] = ok ? f[threadIdx.x] : NAN;
   if (threadIdx.x == 0) {
     musd[0] = ok ? mu : NAN;

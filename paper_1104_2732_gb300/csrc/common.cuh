@@ -99,13 +99,16 @@ __device__ __forceinline__ float f64_to_f32_trunc(uint64_t u) {
 // Control block of a persistent launch (zeroed by the host before every launch).
 // ---------------------------------------------------------------------------------
 struct __align__(128) Ctrl {
-  unsigned int bar_count;
-  unsigned int bar_gen;
+  unsigned int bar_count;         // grid barrier: arrivals so far (only grows within a launch)
+  unsigned int bar_unused;
   int abort;
   int status;
   unsigned long long w_count;     // work-queue head of the segmented launch
   unsigned long long w_len;       // work-queue length of the segmented launch
   unsigned long long pad[12];
+  // totals of a cutting-plane pass, three slots used in rotation: c_lt, c_le, #(x <= a),
+  // #(x < b), compacted count, and the cost sum S in fixed point (see kSFixBits)
+  unsigned long long acc[3][8];
 };
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
@@ -128,23 +131,29 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 // CTA) if the wait gave up or another CTA aborted; the caller must then return.  The
 // wait is bounded by kWaitLimitNs; on expiry the CTA sets status = GBS_ETIMEOUT and
 // abort = 1 so that every other waiter also leaves.
+__device__ __forceinline__ unsigned int atom_add_acq_rel_u32(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+// Grid barrier of a cooperative launch.  One acquire-release arrival per CTA on a counter
+// that only grows: barrier number e is passed once the counter reaches (e + 1) * nblocks,
+// and since no CTA can arrive at barrier e + 1 before barrier e is complete, a CTA reads e
+// from the value its own arrival returned.  The wait is bounded: after kWaitLimitNs the
+// CTA records GBS_ETIMEOUT, raises the abort flag and returns false, as does every CTA
+// that sees the abort flag raised.
 __device__ __forceinline__ bool grid_sync(Ctrl* c, unsigned int nblocks) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    unsigned int gen = ld_acquire_u32(&c->bar_gen);
-    __threadfence();
-    unsigned int arrived = atomicAdd(&c->bar_count, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(&c->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&c->bar_gen, 1u);
-      if (ld_relaxed_i32(&c->abort)) ok = 0;
-    } else {
-      unsigned long long t0 = globaltimer();
+    const unsigned int old = atom_add_acq_rel_u32(&c->bar_count, 1u);
+    const unsigned int target = (old / nblocks + 1u) * nblocks;
+    if (old + 1u != target) {
+      const unsigned long long t0 = globaltimer();
       unsigned int polls = 0;
-      while (ld_acquire_u32(&c->bar_gen) == gen) {
+      while (ld_acquire_u32(&c->bar_count) < target) {
         if (ld_relaxed_i32(&c->abort)) { ok = 0; break; }
         if ((++polls & 63u) == 0 && globaltimer() - t0 > kWaitLimitNs) {
           atomicCAS(&c->status, 0, (int)GBS_ETIMEOUT);
@@ -152,10 +161,10 @@ __device__ __forceinline__ bool grid_sync(Ctrl* c, unsigned int nblocks) {
           ok = 0;
           break;
         }
-        __nanosleep(32);
+        __nanosleep(20);
       }
     }
-    __threadfence();
+    if (ok && ld_relaxed_i32(&c->abort)) ok = 0;
     s_ok = ok;
   }
   __syncthreads();

@@ -175,6 +175,30 @@ __device__ __forceinline__ Sum6 block_sum6(Sum6 v, Sum6* scratch /* [kWarps + 1]
   return scratch[kWarps];
 }
 
+// The same sum, valid in thread 0 only (no broadcast).
+__device__ __forceinline__ Sum6 block_sum6_t0(Sum6 v, Sum6* scratch /* [kWarps] */) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) v.u[i] += __shfl_xor_sync(0xffffffffu, v.u[i], o);
+    v.d += __shfl_xor_sync(0xffffffffu, v.d, o);
+  }
+  __syncthreads();
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  Sum6 r = v;
+  if (threadIdx.x == 0) {
+    r = scratch[0];
+    for (int i = 1; i < kWarps; ++i) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) r.u[q] += scratch[i].u[q];
+      r.d += scratch[i].d;
+    }
+  }
+  return r;
+}
+
 
 template <typename T>
 __device__ __forceinline__ T inside(T tt, T a, T b) {
@@ -185,14 +209,25 @@ __device__ __forceinline__ T inside(T tt, T a, T b) {
 
 // Power-of-two scale keeping per-thread float32 cost partials finite: a thread sums at
 // most `per_thread` terms, each at most `width` in magnitude.
+// Power-of-two scale sigma of the float32 cost partials: a thread sums at most per_thread
+// terms sigma * (t - x) with 0 <= t - x <= width, and sigma * per_thread * width lies in
+// [1, 2) (sigma is clamped to [2^-120, 2^120]; see cost_fix_bits for the clamped case).
 __device__ __forceinline__ float cost_scale(double width, long long per_thread) {
-  double bound = (double)per_thread * width;
-  if (!(bound > 0.0)) return 1.f;
-  double lim = 8.0e37 / bound;
-  if (lim >= 1.0) return 1.f;
-  int e = ilogb(lim);
-  if (e < -120) e = -120;
+  const double bound = (double)per_thread * width;
+  if (!(bound > 0.0) || !isfinite(bound)) return 1.f;
+  int e = -ilogb(bound);
+  e = e < -120 ? -120 : (e > 120 ? 120 : e);
   return ldexpf(1.f, e);
+}
+
+// Fraction bits of the fixed-point image of the scaled cost sums: 40 when sigma was not
+// clamped (a CTA sum of 512 threads is below 2^10, a grid total below 2^21, far inside
+// 64 bits); fewer when the clamp left sigma * per_thread * width above 2.
+constexpr int kSFixBits = 40;
+__device__ __forceinline__ int cost_fix_bits(double width, long long per_thread, float sigma) {
+  const double b = (double)per_thread * width * (double)sigma;
+  if (!(b >= 2.0) || !isfinite(b)) return kSFixBits;
+  return kSFixBits - ilogb(b);
 }
 
 template <typename T> __device__ __forceinline__ bool is_neg_zero_bits(T v);

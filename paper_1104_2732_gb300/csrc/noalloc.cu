@@ -63,9 +63,9 @@ gbs_status setup_current_device(int dev, DeviceSetup* out) {
       cudaGetLastError();
       return GBS_ECUDA;
     }
-    int bps = select_occupancy_f32();
-    bps = bps < 1 ? 1 : (bps > 2 ? 2 : bps);
-    int grid = sms * bps;
+    // one CTA per SM: inputs here are at most 4 MiB, where the per-pass barrier and
+    // reductions cost more with more CTAs
+    int grid = sms;
     if (grid > kNoAllocMaxGrid) grid = kNoAllocMaxGrid;
     s.base = static_cast<unsigned char*>(p);
     s.grid = grid;

@@ -127,6 +127,7 @@ struct BracketState {
   long long cle_a, clt_b, cle_b;
   double dF;
   float sigma;
+  int fx;           // fraction bits of the fixed-point cost total of this pass
   int it, use_bisect, stalled, compact;
   int first;        // 1: the multiplicities of the extremes are still estimates
   int dfv;          // 1: dF = Phi(b) - Phi(a) is known (else the next iterate bisects)
@@ -552,7 +553,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     br.it = 0; br.use_bisect = 0; br.stalled = 0; br.compact = 0; br.phase = 0; br.first = 0;
     br.dfv = 1; br.plain_start = 1; br.learned = 0;
     br.how = GBS_HOW_NONE; br.clt_res = -1;
-    br.result = T(0); br.sigma = 1.f;
+    br.result = T(0); br.sigma = 1.f; br.fx = kSFixBits;
     br.a = T(0); br.b = T(0); br.t = T(0); br.cle_a = 0; br.clt_b = 0; br.cle_b = 0; br.dF = 0.0;
     if (st.n_nan > 0) {
       br.phase = 3;
@@ -563,17 +564,33 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
       br.phase = 1; br.result = T(INFINITY); br.how = GBS_HOW_POSINF;
     } else {
       const T m = (T)st.mn, M = (T)st.mx;
+      const T a0 = Ops<T>::next_down(m);
       if (!(m < M)) {             // every finite element has the same value
         br.phase = 1; br.result = m; br.how = GBS_HOW_MIN; br.clt_res = nneg;
+      } else if (k == nneg + 1) { // the smallest finite element, whatever its multiplicity
+        br.phase = 1; br.result = m; br.how = GBS_HOW_MIN; br.clt_res = nneg;
+      } else if (k == n - npos) { // the largest finite element
+        br.phase = 1; br.result = M; br.how = GBS_HOW_MAX; br.clt_res = 0;
       } else {
-        // Multiplicities of the extremes are not known yet: start from the paper's
-        // closed forms for unique extremes (Sec. 3, step 0); the first pass counts
-        // #(x <= m) and #(x < M) and corrects the state.
-        br.a = m; br.b = M;
-        br.cle_a = nneg + 1; br.clt_b = n - npos - 1; br.cle_b = n - npos; br.first = 1;
-        const double gL = (double)(br.cle_a - k) + 0.5;
-        const double inner = st.sum - (double)m - (double)M;
-        br.dF = gL * ((double)M - (double)m) + (double)(br.clt_b - br.cle_a) * (double)M - inner;
+        if (Ops<T>::is_finite(a0)) {
+          // (a0, M] with a0 the float below m: #(x <= a0) = n_-inf and #(x <= M) =
+          // n - n_+inf are exact, and so is Phi(M) - Phi(a0), from the sum of the finite
+          // elements; #(x < M) takes the paper's unique-extreme closed form (Sec. 3,
+          // step 0) until b first moves.
+          br.a = a0; br.b = M;
+          br.cle_a = nneg; br.clt_b = n - npos - 1; br.cle_b = n - npos; br.first = 0;
+          const double gL = (double)(nneg - k) + 0.5;
+          const double nfin = (double)(n - nneg - npos);
+          br.dF = gL * ((double)M - (double)a0) + nfin * (double)M - st.sum;
+        } else {
+          // m is the lowest finite value: start at (m, M] from the unique-extreme closed
+          // forms; the first pass counts #(x <= m) and #(x < M) and corrects the state.
+          br.a = m; br.b = M;
+          br.cle_a = nneg + 1; br.clt_b = n - npos - 1; br.cle_b = n - npos; br.first = 1;
+          const double gL = (double)(br.cle_a - k) + 0.5;
+          const double inner = st.sum - (double)m - (double)M;
+          br.dF = gL * ((double)M - (double)m) + (double)(br.clt_b - br.cle_a) * (double)M - inner;
+        }
         if (prop_ok) {
           // the proposed bracket (a, b] was checked by counts in pass 0
           const long long pla = (long long)st.c_le_a, plb_lt = (long long)st.c_lt_b, plb = (long long)st.c_le_b;
@@ -590,9 +607,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
           } else if (vb) {                       // (m, b]: a falls back to the minimum
             br.b = prop_b; br.clt_b = plb_lt; br.cle_b = plb; br.plain_start = 0; br.dfv = 0;
           } else if (va) {                       // (a, M]: b falls back to the maximum
-            br.a = prop_a; br.cle_a = pla; br.first = 0; br.plain_start = 0; br.dfv = 0;
-            // #(x < M) is still an estimate: the next pass bisects and counts it exactly
-            br.first = 1;
+            br.a = prop_a; br.cle_a = pla; br.plain_start = 0; br.dfv = 0;
           }
         }
       }
@@ -623,7 +638,9 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
         if (bid == 0) s_nk++;
       }
       br.t = t;
-      br.sigma = cost_scale((double)Ops<T>::img(t) - (double)Ops<T>::img(br.a), per_thread);
+      const double width = (double)Ops<T>::img(t) - (double)Ops<T>::img(br.a);
+      br.sigma = cost_scale(width, per_thread);
+      br.fx = cost_fix_bits(width, per_thread, br.sigma);
       s_br = br;
     }
     __syncthreads();
@@ -653,16 +670,38 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     v6.u[0] = lt; v6.u[1] = le; v6.u[2] = xa; v6.u[3] = xb;
     v6.u[4] = (compact && tid == 0) ? s_zcnt : 0u;   // the CTA's count, once
     v6.d = (double)S;
-    const Sum6 b6 = block_sum6(v6, s_sum6);
-    PassPartial pp;
-    pp.c_lt = b6.u[0]; pp.c_le = b6.u[1]; pp.c_aux = b6.u[2]; pp.c_aux2 = b6.u[3]; pp.c_reg = b6.u[4];
-    pp.S = b6.d;
+    const Sum6 b6 = block_sum6_t0(v6, s_sum6);
     const int slot = pass & 1;
-    if (tid == 0) A.part[slot * G + bid] = pp;
+    if (tid == 0) {
+      // the CTA's partial (its compacted count locates its region in the finish) and its
+      // share of the pass totals: integer adds, so the totals do not depend on the order
+      // in which CTAs arrive; S goes in as a fixed-point integer
+      PassPartial pp;
+      pp.c_lt = b6.u[0]; pp.c_le = b6.u[1]; pp.c_aux = b6.u[2]; pp.c_aux2 = b6.u[3]; pp.c_reg = b6.u[4];
+      pp.S = b6.d;
+      A.part[slot * G + bid] = pp;
+      unsigned long long* acc = A.ctrl->acc[pass % 3];
+#pragma unroll
+      for (int q = 0; q < 5; ++q)
+        if (b6.u[q]) atomicAdd(&acc[q], b6.u[q]);
+      const unsigned long long sfix = __double2ull_rn(ldexp(b6.d, s_br.fx));
+      if (sfix) atomicAdd(&acc[5], sfix);
+      if (bid == 0) {   // the slot of the next pass (last read before the previous barrier)
+        unsigned long long* nxt = A.ctrl->acc[(pass + 1) % 3];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) nxt[q] = 0ull;
+      }
+    }
     if (!grid_sync(A.ctrl, G)) return;
     stamp();
-    const Totals tt = grid_totals(A.part + slot * G, G, s_sum6);
     if (tid == 0) {   // steps 1.3-1.4
+      Totals tt;
+      {
+        const unsigned long long* acc = A.ctrl->acc[pass % 3];
+        tt.c_lt = __ldcg(&acc[0]); tt.c_le = __ldcg(&acc[1]); tt.c_aux = __ldcg(&acc[2]);
+        tt.c_aux2 = __ldcg(&acc[3]); tt.c_reg = __ldcg(&acc[4]);
+        tt.S = ldexp((double)__ldcg(&acc[5]), -s_br.fx);
+      }
       const BracketState<T> br = s_br;
       BracketState<T> nb = br;
       const long long clt = (long long)tt.c_lt, cle = (long long)tt.c_le;
@@ -771,19 +810,35 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
         const unsigned long long s1 = s_off[r + 1] < hi_i ? s_off[r + 1] : hi_i;
         const T* zr = A.z + region_start(r, nch, G, Ops<T>::kVec);
         const unsigned long long rbase = s_off[r];
-        // warp-uniform sweep; equal digits within a warp are merged before the atomic
-        for (unsigned long long i0 = s0 + (unsigned long long)warp * 32; i0 < s1; i0 += kThreads) {
-          const unsigned long long i = i0 + lane;
-          unsigned int d = kBins;
-          if (i < s1) {
-            const T v = __ldcg(zr + (i - rbase));
-            const U key = ukey(v);
-            const bool inb = (v > fa) && (v <= fb);
-            const bool match = known == 0 || (U)(key >> (W - known)) == prefix;
-            if (inb && match) d = (unsigned int)(key >> sh) & dmask;
+        // warp-uniform sweep, kFinU elements per lane loaded before any is used; warps
+        // with no element in the bracket skip the histogram, and a warp whose active
+        // lanes share one digit (a run of equal values) adds once
+        constexpr int kFinU = 8;
+        for (unsigned long long i0 = s0 + (unsigned long long)warp * 32; i0 < s1;
+             i0 += (unsigned long long)kThreads * kFinU) {
+          T v[kFinU];
+#pragma unroll
+          for (int j = 0; j < kFinU; ++j) {
+            const unsigned long long i = i0 + (unsigned long long)j * kThreads + lane;
+            v[j] = i < s1 ? __ldcg(zr + (i - rbase)) : fa;   // fa is outside (a, b]
           }
-          const unsigned int same = __match_any_sync(0xffffffffu, d);
-          if (d < kBins && lane == __ffs(same) - 1) atomicAdd(&s_hist[d], (unsigned int)__popc(same));
+#pragma unroll
+          for (int j = 0; j < kFinU; ++j) {
+            const U key = ukey(v[j]);
+            const bool inb = (v[j] > fa) && (v[j] <= fb);
+            const bool match = known == 0 || (U)(key >> (W - known)) == prefix;
+            const unsigned int d = (inb && match) ? (unsigned int)(key >> sh) & dmask : kBins;
+            const unsigned int act = __ballot_sync(0xffffffffu, d < kBins);
+            if (act) {
+              const int l0 = __ffs(act) - 1;
+              const unsigned int d0 = __shfl_sync(0xffffffffu, d, l0);
+              if (__all_sync(0xffffffffu, d == kBins || d == d0)) {
+                if (lane == l0) atomicAdd(&s_hist[d0], (unsigned int)__popc(act));
+              } else if (d < kBins) {
+                atomicAdd(&s_hist[d], 1u);
+              }
+            }
+          }
         }
       }
       __syncthreads();
@@ -834,7 +889,8 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     // a zero result found by counts: -0 sorts before +0, so count the -0 elements
     unsigned long long d0 = 0, d1 = 0, nz = 0;
     if (!aux_pass(T(0), T(0), &d0, &d1, &nz)) return;
-    result = (k - fin.clt_res) <= (long long)nz ? T(-0.0) : T(0.0);
+    // x_(k) is a zero: it is -0 when k - #(x < 0) is at most the number of -0 elements
+    result = (k - (long long)d1) <= (long long)nz ? T(-0.0) : T(0.0);
     extra = 1;
   }
 
@@ -872,13 +928,16 @@ template <typename T> constexpr int vec_of() { return 16 / (int)sizeof(T); }
 // Persistent grid: every SM holds the same number of CTAs (co-residency is required by
 // the grid-wide barrier; the launch is cooperative).
 template <typename T>
-int grid_for(gbs_ctx* c) {
+int grid_for(gbs_ctx* c, long long n) {
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, select_kernel<T>, kThreads, 0) != cudaSuccess) {
     cudaGetLastError();
     occ = 1;
   }
-  int bps = c->cfg.blocks_per_sm > 0 ? c->cfg.blocks_per_sm : 2;
+  // one CTA per SM below 32 MiB of input (the per-pass barrier and reductions dominate
+  // there and cost more with more CTAs), two above (more loads in flight per SM)
+  const int bps_auto = (double)n * sizeof(T) >= 32.0 * 1048576.0 ? 2 : 1;
+  int bps = c->cfg.blocks_per_sm > 0 ? c->cfg.blocks_per_sm : bps_auto;
   bps = std::max(1, std::min(bps, occ));
   return std::min(kMaxGrid, c->num_sms * bps);
 }
@@ -912,7 +971,7 @@ gbs_status launch_select(gbs_ctx* c, const T* x, long long n, long long k, T* ou
                                 cudaStream_t stream) {
   DeviceGuard g(c->device);
   if (!g.ok) return GBS_ECUDA;
-  const int grid = grid_for<T>(c);
+  const int grid = grid_for<T>(c, n);
   const long long zel = z_elems_for<T>(n, grid);
   const size_t zb = mode == kModeSelect ? (size_t)zel * sizeof(T) : 0;
   gbs_status s = gbs_internal_ensure(c, zb);
@@ -979,10 +1038,10 @@ gbs_status reserve_select(gbs_ctx* c, long long n, int elem_bytes) {
   DeviceGuard g(c->device);
   if (!g.ok) return GBS_ECUDA;
   if (elem_bytes == 4) {
-    const int grid = grid_for<float>(c);
+    const int grid = grid_for<float>(c, n);
     return gbs_internal_ensure(c, (size_t)z_elems_for<float>(n, grid) * 4);
   }
-  const int grid = grid_for<double>(c);
+  const int grid = grid_for<double>(c, n);
   return gbs_internal_ensure(c, (size_t)z_elems_for<double>(n, grid) * 8);
 }
 
