@@ -62,11 +62,13 @@ __device__ __forceinline__ void stream_chunks(const T* __restrict__ x, const Geo
 }
 
 // As stream_chunks, and every element with keep(element) is appended to `zr` (counter
-// *cnt in shared memory): one warp-wide prefix sum per chunk.
+// *cnt in shared memory).  Per chunk, a warp-wide prefix sum places the warp's kept
+// elements in its shared-memory staging buffer `wb` (room for the warp's whole share of
+// a chunk), from where the warp copies them to `zr` with consecutive, coalesced stores.
 template <typename T, typename Fn, typename Keep>
 __device__ __forceinline__ void stream_chunks_compact(const T* __restrict__ x, const Geometry<T>& g, bool rev,
                                                       Fn& f, Keep& keep, T* __restrict__ zr,
-                                                      unsigned int* cnt) {
+                                                      unsigned int* cnt, T* wb) {
   using V = typename Ops<T>::V;
   constexpr int kVec = Ops<T>::kVec;
   const int lane = threadIdx.x & 31;
@@ -105,13 +107,16 @@ __device__ __forceinline__ void stream_chunks_compact(const T* __restrict__ x, c
     if (total) {
       unsigned int b0 = 0;
       if (lane == 31) b0 = atomicAdd(cnt, total);
-      b0 = __shfl_sync(0xffffffffu, b0, 31);
-      unsigned int pos = b0 + incl - k;
+      unsigned int pos = incl - k;
 #pragma unroll
       for (int u = 0; u < kVPT; ++u)
 #pragma unroll
         for (int e = 0; e < kVec; ++e)
-          if (mask & (1u << (u * kVec + e))) zr[pos++] = Ops<T>::get(r[u], e);
+          if (mask & (1u << (u * kVec + e))) wb[pos++] = Ops<T>::get(r[u], e);
+      b0 = __shfl_sync(0xffffffffu, b0, 31);
+      __syncwarp();
+      for (unsigned int i = lane; i < total; i += 32) zr[b0 + i] = wb[i];
+      __syncwarp();
     }
   }
 }
@@ -172,7 +177,7 @@ template <typename T, bool FIRST, bool COMPACT>
 __device__ __noinline__ bool cut_pass(const T* __restrict__ x, const Geometry<T>& geo, bool rev,
                                       typename Ops<T>::C ca, typename Ops<T>::C ct, typename Ops<T>::C cb,
                                       float nsig, float tsig, T* __restrict__ zr, unsigned int* s_cnt,
-                                      PassAcc& acc) {
+                                      T* wb, PassAcc& acc) {
   using C = typename Ops<T>::C;
   using V = typename Ops<T>::V;
   unsigned int lt = 0, le = 0, xa = 0, xb = 0;
@@ -194,7 +199,7 @@ __device__ __noinline__ bool cut_pass(const T* __restrict__ x, const Geometry<T>
       };
       stream_edges(x, geo, fk);
     }
-    stream_chunks_compact(x, geo, rev, f, keep, zr, s_cnt);
+    stream_chunks_compact(x, geo, rev, f, keep, zr, s_cnt, wb);
   } else {
     stream_edges(x, geo, f);
     stream_chunks(x, geo, rev, f);
@@ -241,39 +246,39 @@ __device__ __noinline__ bool stats_pass(const T* __restrict__ x, const Geometry<
 
 // Per-thread accumulators of the checks of a proposed bracket (a, b] in pass 0.
 struct ProposalAcc {
-  unsigned int la, lblt, lble;   // #(x <= a), #(x < b), #(x <= b)
-  float sab;                     // sum over a < x < b of (b - x), scaled
+  unsigned int la, lblt;   // #(x <= a), #(x < b); #(x <= b) = #(x <= a) + #compacted
+  float sab;               // sum over a < x < b of (b - x), scaled
 };
 
-// Pass 0 with a proposed bracket: pass 0's work, the counts at a and b, the cost from a
-// to b, and the elements of (a, b] compacted into this CTA's region.
+// Pass 0 with a proposed bracket: pass 0's extremes and non-finite counts, the counts at
+// a and b, the cost from a to b, and the elements of (a, b] compacted into this CTA's
+// region.  The sum of x is not formed: with a proposal, Phi(b) - Phi(a) comes from the
+// cost term, and a side that fails its check starts without it.
 template <typename T>
 __device__ __noinline__ bool stats_pass_learned(const T* __restrict__ x, const Geometry<T>& geo, float sig,
                                                 float x0s, typename Ops<T>::C ca, typename Ops<T>::C cb,
                                                 float nsab, float bsab, T* __restrict__ zr, unsigned int* s_cnt,
-                                                StatsAcc<T>& out, ProposalAcc& pa) {
+                                                T* wb, StatsAcc<T>& out, ProposalAcc& pa) {
   using C = typename Ops<T>::C;
   C mn = cmp_pos_inf<T>(), mx = -cmp_pos_inf<T>();
-  unsigned int nnan = 0, nneg = 0, npos = 0, seen = 0, la = 0, lblt = 0, lble = 0;
-  float sum = 0.f, sab = 0.f;
+  unsigned int nnan = 0, nneg = 0, npos = 0, seen = 0, la = 0, lblt = 0;
+  float sab = 0.f;
   auto f = [&](T v) {
     ++seen;
     const C cv = CmpOf<T>::of(v);
     if (Ops<T>::is_finite(v)) {
       mn = cv < mn ? cv : mn;
       mx = cv > mx ? cv : mx;
-      sum += fmaf(Ops<T>::img(v), sig, -x0s);
     } else {
       nnan += Ops<T>::is_nan(v);
       nneg += Ops<T>::is_neginf(v);
       npos += Ops<T>::is_posinf(v);
     }
-    la += (cv <= ca);
-    lblt += (cv < cb);
-    lble += (cv <= cb);
-    const bool in = (cv > ca) & (cv < cb);
+    const bool le_a = cv <= ca, lt_b = cv < cb;
+    la += le_a;
+    lblt += lt_b;
     const float d = fmaf(Ops<T>::img(v), nsab, bsab);
-    sab += in ? d : 0.f;
+    sab += (!le_a && lt_b && cv > ca) ? d : 0.f;
   };
   auto keep = [&](T v) { const C cv = CmpOf<T>::of(v); return (cv > ca) & (cv <= cb); };
   if ((long long)blockIdx.x * kThreads + threadIdx.x < geo.head + (geo.n - geo.tail0)) {
@@ -283,9 +288,10 @@ __device__ __noinline__ bool stats_pass_learned(const T* __restrict__ x, const G
     };
     stream_edges(x, geo, fk);
   }
-  stream_chunks_compact(x, geo, false, f, keep, zr, s_cnt);
-  out.mn = mn; out.mx = mx; out.nnan = nnan; out.nneg = nneg; out.npos = npos; out.seen = seen; out.sum = sum;
-  pa.la = la; pa.lblt = lblt; pa.lble = lble; pa.sab = sab;
+  stream_chunks_compact(x, geo, false, f, keep, zr, s_cnt, wb);
+  (void)sig; (void)x0s;
+  out.mn = mn; out.mx = mx; out.nnan = nnan; out.nneg = nneg; out.npos = npos; out.seen = seen; out.sum = 0.f;
+  pa.la = la; pa.lblt = lblt; pa.sab = sab;
   return true;
 }
 
@@ -318,7 +324,11 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
   __shared__ StatsPartial s_st;
   __shared__ Sum6 s_sum6[kWarps + 1];
 
-  __shared__ unsigned long long s_off[kMaxGrid + 1];   // region offsets of the finish
+  // region offsets of the finish, and before it the warps' compaction staging buffers
+  __shared__ __align__(16) unsigned char s_big[kChunkBytes > 8 * (kMaxGrid + 1) ? kChunkBytes
+                                                                                 : 8 * (kMaxGrid + 1)];
+  unsigned long long* s_off = reinterpret_cast<unsigned long long*>(s_big);
+  T* const s_wb = reinterpret_cast<T*>(s_big) + (tid >> 5) * (kChunkBytes / sizeof(T) / kWarps);
 
   const Geometry<T> geo(A.x, n);
   const long long nch = chunk_count(geo.nv);
@@ -418,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     const float x0s = x0 * sig;
     StatsAcc<T> sa;
     ProposalAcc pa;
-    pa.la = pa.lblt = pa.lble = 0; pa.sab = 0.f;
+    pa.la = pa.lblt = 0; pa.sab = 0.f;
     float sig_ab = 1.f;
     if (prop_ok) {
       sig_ab = cost_scale((double)Ops<T>::img(prop_b) - (double)Ops<T>::img(prop_a), per_thread);
@@ -426,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
       __syncthreads();
       if (!stats_pass_learned<T>(A.x, geo, sig, x0s, CmpOf<T>::of(prop_a), CmpOf<T>::of(prop_b), -sig_ab,
                                  Ops<T>::img(prop_b) * sig_ab, A.z + region_start(bid, nch, G, Ops<T>::kVec),
-                                 &s_zcnt, sa, pa))
+                                 &s_zcnt, s_wb, sa, pa))
         return;
     } else {
       if (!stats_pass<T>(A.x, geo, sig, x0s, sa)) return;
@@ -451,7 +461,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     const double own = (double)sum / (double)sig + (double)nfin * (double)x0;
     const double b_sum = block_sum<double>(own, s_f64);
     Sum6 p6;
-    p6.u[0] = pa.la; p6.u[1] = pa.lblt; p6.u[2] = pa.lble; p6.u[3] = 0; p6.u[4] = 0; p6.d = (double)pa.sab;
+    p6.u[0] = pa.la; p6.u[1] = pa.lblt; p6.u[2] = 0; p6.u[3] = 0; p6.u[4] = 0; p6.d = (double)pa.sab;
     if (prop_ok) {
       __syncthreads();
       p6.u[3] = tid == 0 ? s_zcnt : 0u;
@@ -467,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
       sp.n_nan = b_nan; sp.n_neginf = b_neg; sp.n_posinf = b_pos; sp.n_negzero = 0; sp.n_finite = b_fin;
       sp.mn = (double)cmp_value(bm, T()); sp.mx = (double)cmp_value(bM, T());
       sp.c_mn = 0; sp.c_mx = 0; sp.sum = b_sum;
-      sp.c_le_a = b6.u[0]; sp.c_lt_b = b6.u[1]; sp.c_le_b = b6.u[2]; sp.c_reg = b6.u[3];
+      sp.c_le_a = b6.u[0]; sp.c_lt_b = b6.u[1]; sp.c_le_b = b6.u[0] + b6.u[3]; sp.c_reg = b6.u[3];
       sp.s_ab = b6.d / (double)sig_ab;
       A.spart[bid] = sp;
     }
@@ -655,11 +665,11 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     T* zr = A.z + region_start(bid, nch, G, Ops<T>::kVec);
     bool ok;
     if (first) {
-      if (compact) ok = cut_pass<T, true, true>(A.x, geo, rev, ca, ct, cb, nsig, tsig, zr, &s_zcnt, acc);
-      else ok = cut_pass<T, true, false>(A.x, geo, rev, ca, ct, cb, nsig, tsig, zr, &s_zcnt, acc);
+      if (compact) ok = cut_pass<T, true, true>(A.x, geo, rev, ca, ct, cb, nsig, tsig, zr, &s_zcnt, s_wb, acc);
+      else ok = cut_pass<T, true, false>(A.x, geo, rev, ca, ct, cb, nsig, tsig, zr, &s_zcnt, s_wb, acc);
     } else {
-      if (compact) ok = cut_pass<T, false, true>(A.x, geo, rev, ca, ct, cb, nsig, tsig, zr, &s_zcnt, acc);
-      else ok = cut_pass<T, false, false>(A.x, geo, rev, ca, ct, cb, nsig, tsig, zr, &s_zcnt, acc);
+      if (compact) ok = cut_pass<T, false, true>(A.x, geo, rev, ca, ct, cb, nsig, tsig, zr, &s_zcnt, s_wb, acc);
+      else ok = cut_pass<T, false, false>(A.x, geo, rev, ca, ct, cb, nsig, tsig, zr, &s_zcnt, s_wb, acc);
     }
     if (!ok) return;
     if (bid == 0 && tid == 0 && pass < kMaxIt) s_tstream[pass] = globaltimer();
