@@ -53,31 +53,44 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs; only
+    samples whose timestamp falls inside the region (host clock) are summarised."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, period_ms=20):
         self.index = index
+        self.period_ms = period_ms
         self.proc = None
         self.lines = []
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            deadline = time.time() + 5.0
+            while not self.lines and time.time() < deadline:   # sampler running before the region
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def start(self):
+        self.t0 = time.time()
+
+    def stop(self):
+        self.t1 = time.time()
+        time.sleep(2.5 * self.period_ms / 1000.0)   # let the sample that covers the end arrive
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -87,23 +100,39 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(text, fmt).timestamp()
+            except ValueError:
+                pass
+        return None
+
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        sm, mx, reasons, inside = [], None, set(), 0
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for recv, line in self.lines:
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 8:
+            if len(parts) < 9:
+                continue
+            ts = self._stamp(parts[0])
+            t = ts if ts is not None else recv
+            if self.t0 is not None and not (self.t0 - 0.001 <= t <= (self.t1 or t) + 0.001):
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx = float(parts[1])
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[4:8]):
+            inside += 1
+            for nm, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": inside,
+                "region_s": (self.t1 - self.t0) if self.t0 and self.t1 else None}
 
 
 def cpu_oracle_time(x, ks):
@@ -116,27 +145,33 @@ def cpu_oracle_time(x, ks):
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the CPU oracle on the host cores, on a bounded sample of the workload."""
+    """Reference arm: the CPU oracle on the host cores, on a bounded sample of the workload.
+
+    Each step selects the median of one contiguous slice of the 2^27 array; the slice
+    length is chosen so that the K + W oracle calls take about a minute in total (the
+    full array on every step when K is small)."""
     import numpy as np
     import synth
     n = 1 << N_LOG2
     x = synth.heavy_mixture(FAMILY, n, seed=SEED)
-    ks = ranks_for(n)
-    # each step: the median rank on the full array (the five ranks cost ~5x as much)
-    for _ in range(args.warmup):
-        cpu_oracle_time(x, ks[2:3])
-    times = [cpu_oracle_time(x, ks[2:3]) for _ in range(args.steps)]
+    budget_elems = 1.6e9          # ~1 min of the oracle at ~25-30 Melem/s
+    m = int(min(n, max(1 << 20, budget_elems / max(1, args.steps + args.warmup))))
+    slices = [x[(i * m) % (n - m + 1):(i * m) % (n - m + 1) + m] for i in range(args.steps + args.warmup)]
+    for i in range(args.warmup):
+        cpu_oracle_time(slices[i], [(m + 1) // 2])
+    times = [cpu_oracle_time(slices[args.warmup + i], [(m + 1) // 2]) for i in range(args.steps)]
     t = sum(times)
-    value = args.steps * n / t / 1e9
+    value = args.steps * m / t / 1e9
     line = {
         "impl": "reference", "metric": "k-th select Gelem/s (n=2^27 float32)", "value": value,
         "unit": "Gelem/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"single-array k-th select, n=2^27 float32 {FAMILY} (+5% dups, 10 inf)",
-                   "ranks": "median rank per step", "l2": "input larger than L2"},
+                   "ranks": "median rank of a slice per step", "slice_elements": m,
+                   "l2": "input larger than L2"},
         "cpu_baseline": {"value": value, "unit": "Gelem/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} median selections on the full 2^27 array"},
+                         "sample": f"{args.steps} medians of contiguous {m}-element slices of the 2^27 array"},
         "e2e": {"value": value, "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     if rank == 0:
@@ -319,10 +354,151 @@ def bench_learned(gbs, ctx, torch, np, args, x_big=None):
     return row
 
 
+def _bits(t, torch):
+    return t.view(torch.int32 if t.dtype == torch.float32 else torch.int64)
+
+
+def bench_small(gbs, ctx, torch, np, args):
+    """n = 10^6 uniform [0, 1) float32 (seed 0), median (k = 500000): 4 MB, L2-resident and
+    latency-bound.  Device time per selection over 200 back-to-back calls, passes, and the
+    CPU oracle on the same array (best / median of 10 runs after 2 warm-ups)."""
+    import synth
+    from oracle import select as osel
+    x_h = synth.uniform(1_000_000, seed=0)
+    x = torch.from_numpy(x_h).cuda()
+    k = 500_000
+    out = torch.empty(1, device="cuda")
+    for _ in range(5):
+        ctx.select_kth(x, k, out=out)
+    st = ctx.last_stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 200
+    e0.record()
+    for _ in range(reps):
+        ctx.select_kth(x, k, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) / reps * 1e3
+    for _ in range(2):
+        osel.select_kth(x_h, k)
+    cpu = []
+    for _ in range(10):
+        t0 = time.perf_counter()
+        want = osel.select_kth(x_h, k)
+        cpu.append((time.perf_counter() - t0) * 1e6)
+    same = bool(np.asarray(out.cpu().numpy()[0], np.float32).view(np.uint32)
+                == np.asarray(want, np.float32).view(np.uint32))
+    return {"workload": "median of n=1e6 uniform [0,1) float32, seed 0", "metric": "us/selection",
+            "value": us, "passes": st["passes"], "how": st["how"], "grid": st["grid"],
+            "cpu_oracle_us_best": min(cpu), "cpu_oracle_us_median": statistics.median(cpu), "cpu_cores": 1,
+            "identical_to_oracle": same}
+
+
+def bench_f64(gbs, ctx, torch, np, args):
+    """n = 2^26 float64 mixture (seed 4), the five ranks per step, 10 steps; bytes per
+    call = (passes x n + compacted) x 8 against the measured HBM bandwidth; torch.sort of
+    the same array as the comparator."""
+    import synth
+    n = 1 << 26
+    x = torch.from_numpy(synth.heavy_mixture(FAMILY, n, seed=SEED, dtype=np.float64)).cuda()
+    ctx.reserve(n, 8)
+    ks = ranks_for(n)
+    out = torch.empty(len(ks), dtype=torch.float64, device="cuda")
+    recs = []
+    for i, k in enumerate(ks):
+        ctx.select_kth(x, k, out=out[i:i + 1])
+        recs.append(ctx.last_stats())
+    steps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        for i, k in enumerate(ks):
+            ctx.select_kth(x, k, out=out[i:i + 1])
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    alg = sum((r["passes"] * n + r["finish_pop"]) * 8 for r in recs)
+    peaks, kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    for _ in range(2):
+        torch.sort(x)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for _ in range(3):
+        torch.sort(x)
+    s1.record()
+    torch.cuda.synchronize()
+    sort_ms = s0.elapsed_time(s1) / 3
+    res = {"workload": f"n=2^26 float64 {FAMILY} (+5% duplicates, 10 +-inf), ranks {ks}", "metric": "Gelem/s",
+           "value": len(ks) * n / (ms * 1e-3) / 1e9, "ms_per_step": ms, "passes": [r["passes"] for r in recs],
+           "hbm_frac": alg / (ms * 1e-3) / 1e9 / hbm, "peak_kind": f"{kind} hbm_gbs",
+           "torch_sort_ms": sort_ms, "speedup_vs_torch_sort_per_selection": sort_ms / (ms / len(ks))}
+    del x
+    torch.cuda.empty_cache()
+    return res
+
+
+def bench_families(gbs, ctx, torch, np, args):
+    """The three single-family 2^27 float32 arrays (normal seed 1, lognormal(0,2) seed 2,
+    Student-t nu=1 seed 3; each +5% duplicates of its median and 10 +-inf), five ranks
+    per step, 5 steps each."""
+    import synth
+    n = 1 << N_LOG2
+    ks = ranks_for(n)
+    out = torch.empty(len(ks), dtype=torch.float32, device="cuda")
+    res = {}
+    for fam, seed in (("normal", 1), ("lognormal", 2), ("cauchy", 3)):
+        x = torch.from_numpy(synth.heavy_mixture(fam, n, seed=seed)).cuda()
+        recs = []
+        for i, k in enumerate(ks):
+            ctx.select_kth(x, k, out=out[i:i + 1])
+            recs.append(ctx.last_stats())
+        steps = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            for i, k in enumerate(ks):
+                ctx.select_kth(x, k, out=out[i:i + 1])
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[fam] = {"gelem_s": len(ks) * n / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+                    "passes": [r["passes"] for r in recs], "how": [r["how"] for r in recs]}
+        del x
+    torch.cuda.empty_cache()
+    return {"workload": "2^27 float32 single-family arrays, 5 ranks per step", "metric": "Gelem/s", **res}
+
+
+def bench_sharded(gbs, ctx, torch, np, args, x):
+    """The 2^27 array as four host-simulated shards on this device (per-shard passes with
+    the library's kernels, totals summed on the host between passes); median; wall time of
+    the host-driven loop, identical result to the single-array select required."""
+    from paper_1104_2732_gb300.sharded import GpuBackend, select_kth_sharded
+    n = x.numel()
+    m = n // 4
+    shards = [x[i * m:(i + 1) * m] if i < 3 else x[3 * m:] for i in range(4)]
+    k = (n + 1) // 2
+    single = float(ctx.select_kth(x, k).item())
+    trace = []
+    select_kth_sharded(shards, k, GpuBackend(ctx), elem_bytes=4)      # warm-up
+    torch.cuda.synchronize()
+    reps = 5
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        trace = []
+        got = select_kth_sharded(shards, k, GpuBackend(ctx), elem_bytes=4, trace=trace)
+    ms = (time.perf_counter() - t0) / reps * 1e3
+    return {"workload": "median of the 2^27 float32 array split into 4 shards on one device",
+            "metric": "ms/selection (host wall clock)", "value": ms, "cutting_plane_passes": len(trace),
+            "identical_to_single_array": bool(np.float32(got).view(np.uint32) == np.float32(single).view(np.uint32))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -380,6 +556,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
+        clk.start()
         start.record(stream)
         j = 0
         for _ in range(args.steps):
@@ -390,6 +567,7 @@ def main():
                 j += 1
         stop.record(stream)
         torch.cuda.synchronize()
+        clk.stop()
     if world > 1:
         dist.barrier()
     ms = start.elapsed_time(stop)
@@ -455,9 +633,13 @@ def main():
     rows = {}
     if not args.only_single:
         del pinned
+        rows["small_n1e6"] = bench_small(gbs, ctx, torch, np, args)
+        rows["sharded_4_shards"] = bench_sharded(gbs, ctx, torch, np, args, x)
+        rows["learned_bracket"] = bench_learned(gbs, ctx, torch, np, args, x_big=x)
         rows["segmented"] = bench_segmented(gbs, ctx, torch, np, args)
         rows["lms_lts"] = bench_lms(gbs, ctx, torch, np, args)
-        rows["learned_bracket"] = bench_learned(gbs, ctx, torch, np, args, x_big=x)
+        rows["f64_n2e26"] = bench_f64(gbs, ctx, torch, np, args)
+        rows["families_f32"] = bench_families(gbs, ctx, torch, np, args)
 
     # ---------------- CPU oracle baseline (rank 0 only) ----------------
     cpu = None

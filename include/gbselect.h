@@ -65,7 +65,8 @@ typedef struct {
                             the cutting plane stops (Sec. 3: "the algorithm stops when the
                             cost of its iteration outweighs the benefit"); 0 = max(n/16, 4096) */
     int32_t maxit;       /* cutting-plane iterations before compaction is forced; 0 = 64 */
-    int32_t blocks_per_sm; /* CTAs per SM of the persistent kernel; 0 = as many as fit (<= 2) */
+    int32_t blocks_per_sm; /* CTAs per SM of the persistent kernel; 0 = 1 below 32 MiB of
+                              input, else 2 (at most what fits) */
     int32_t use_learned; /* 1 = start from the bracket proposed by the loaded model (if any) */
     int32_t reserved[7];
 } gbs_config;
@@ -110,6 +111,31 @@ typedef struct {
     double S;         /* sum over a < x_i < t of (t - x_i) */
     double dphi;      /* Phi(t) - Phi(a) = (c_le_a - k + 1/2)(t - a) + S, Phi = F/n of Eq. (med_objOS) */
 } gbs_cost_eval;
+
+/* State of a sharded selection (see gbs_shard_begin).  Plain data: it may be copied,
+ * broadcast between processes or inspected; only the functions below change it. */
+enum {
+    GBS_SHARD_ITERATE = 0, /* evaluate t on every shard (gbs_cost_pass_*), then gbs_shard_update */
+    GBS_SHARD_DONE = 1,    /* result holds x_(k) */
+    GBS_SHARD_COMPACT = 2, /* compact (a, b] on every shard; x_(k) is the (k - cle_a)-th of them */
+    GBS_SHARD_NAN = 3      /* x holds a NaN: no rank */
+};
+typedef struct {
+    int64_t n, k;          /* global length and rank */
+    int64_t cap;           /* compaction threshold on the bracket population */
+    int32_t maxit;         /* iterates before compaction is forced */
+    int32_t elem_bytes;    /* 4 (float32) or 8 (float64): the grid of the iterates */
+    int32_t phase;         /* GBS_SHARD_* */
+    int32_t how;           /* GBS_HOW_* once DONE */
+    int32_t it;            /* iterates evaluated */
+    int32_t use_bisect, stalled, dfv; /* safeguards, as in the single-array kernel */
+    int64_t n_neginf, n_negzero;      /* #(x = -inf), #(x = -0) */
+    int64_t cle_a, clt_b, cle_b;      /* #(x <= a) (-1 until counted), #(x < b), #(x <= b) */
+    double a, b;           /* bracket: x_(k) lies in (a, b] */
+    double t;              /* next point to evaluate (after gbs_shard_next) */
+    double dF;             /* Phi(b) - Phi(a), Phi = F/n of Eq. (med_objOS) */
+    double result;         /* x_(k) once DONE */
+} gbs_shard_state;
 
 /* Context lifetime.  `device` is the CUDA ordinal the context works on. */
 gbs_status gbs_create(gbs_ctx** ctx, int device);
@@ -263,6 +289,50 @@ gbs_status gbs_last_stats(gbs_ctx* ctx, gbs_run_stats* out);
 
 /* Static, human-readable name of a status code. */
 const char* gbs_status_string(gbs_status s);
+
+/* ---------------------------------------------------------------------------------
+ * Sharded selection.  Algorithm 1 (Sec. 3) over a vector split into shards that are
+ * reduced separately -- on several devices, in several processes, or as sub-ranges of
+ * one array -- with the per-pass results summed by the caller (an all-reduce), as the
+ * paper's multi-GPU remark (Sec. 4) sums the per-device reductions on the host.  The
+ * state functions are host code and need no device; every per-element pass is one of
+ * the library's own kernels on a shard:
+ *   1. every shard: gbs_array_stats_*.  Totals: sums of n, n_nan, n_neginf, n_posinf,
+ *      n_negzero, n_finite and sum; the least `min` and the greatest `max` over the
+ *      shards that hold a finite element (c_le_min and c_lt_max are not used).  Then
+ *      gbs_shard_begin().
+ *   2. while phase == GBS_SHARD_ITERATE: gbs_shard_next() sets t (or moves the state to
+ *      GBS_SHARD_COMPACT); every shard runs gbs_cost_pass_*(k = any valid rank, a, t);
+ *      totals: sums of c_lt_t, c_le_t, c_le_a and S; then gbs_shard_update().
+ *   3. GBS_SHARD_COMPACT: every shard copies its elements of (a, b] with gbs_compact_*;
+ *      x_(k) is element k - cle_a of their union (gbs_select_kth_* on it).
+ * The result is the single-array result bit for bit; the iterates may differ from the
+ * single-array kernel's, whose cost partials are summed in another order.
+ * --------------------------------------------------------------------------------- */
+
+/* Trivial resolution and the starting bracket from the pass-0 totals (Sec. 3, step 0).
+ * cap <= 0 selects max(n/16, 4096); maxit <= 0 selects 64.  EINVAL for bad arguments
+ * or totals whose counts do not add up to n. */
+gbs_status gbs_shard_begin(gbs_shard_state* s, int32_t elem_bytes, int64_t n, int64_t k,
+                           const gbs_array_stats* total, int64_t cap, int32_t maxit);
+/* The next point t strictly inside (a, b) on the element grid: the tangent intersection
+ * of Algorithm 1, step 1.1, or the bracket midpoint in totalOrder keys after a slow
+ * step.  Moves the state to GBS_SHARD_COMPACT instead once (a, b] holds at most cap
+ * elements, after maxit iterates, or after two stalled steps.  EINVAL unless ITERATE. */
+gbs_status gbs_shard_next(gbs_shard_state* s);
+/* Steps 1.3-1.4 from the totals of the pass at (a, t).  EINTERNAL when the totals are
+ * inconsistent (c_le_a differs from the state's, or counts out of order). */
+gbs_status gbs_shard_update(gbs_shard_state* s, const gbs_cost_eval* total);
+
+/* Copies the elements x_i with a < x_i <= b (IEEE comparison; NaN never qualifies) into
+ * z[0..z_cap) in no particular order, and stores how many qualify in *count (host
+ * pointer; the call synchronises `stream`).  x: n elements, device.  z: device, z_cap
+ * elements, owned by the caller.  GBS_ENOMEM when more than z_cap qualify (z then holds
+ * z_cap of them); EINVAL unless a < b. */
+gbs_status gbs_compact_f32(gbs_ctx* ctx, const float* x, int64_t n, double a, double b, float* z,
+                           int64_t z_cap, int64_t* count, void* stream);
+gbs_status gbs_compact_f64(gbs_ctx* ctx, const double* x, int64_t n, double a, double b, double* z,
+                           int64_t z_cap, int64_t* count, void* stream);
 
 #ifdef __cplusplus
 }

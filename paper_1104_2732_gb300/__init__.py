@@ -56,6 +56,17 @@ class gbs_cost_eval(C.Structure):
                 ("S", C.c_double), ("dphi", C.c_double)]
 
 
+class gbs_shard_state(C.Structure):
+    _fields_ = [("n", C.c_int64), ("k", C.c_int64), ("cap", C.c_int64), ("maxit", C.c_int32),
+                ("elem_bytes", C.c_int32), ("phase", C.c_int32), ("how", C.c_int32), ("it", C.c_int32),
+                ("use_bisect", C.c_int32), ("stalled", C.c_int32), ("dfv", C.c_int32), ("n_neginf", C.c_int64),
+                ("n_negzero", C.c_int64), ("cle_a", C.c_int64), ("clt_b", C.c_int64), ("cle_b", C.c_int64),
+                ("a", C.c_double), ("b", C.c_double), ("t", C.c_double), ("dF", C.c_double),
+                ("result", C.c_double)]
+
+
+GBS_SHARD_ITERATE, GBS_SHARD_DONE, GBS_SHARD_COMPACT, GBS_SHARD_NAN = range(4)
+
 _P = C.c_void_p
 _I64 = C.c_int64
 _SIGS = {
@@ -97,6 +108,12 @@ _SIGS = {
     "gbs_generate_training_array_f32": (C.c_int, [_P, _P, _I64, C.c_int32, C.c_float, C.c_float, C.c_float,
                                                   C.c_float, C.c_float, C.c_uint64, _P]),
     "gbs_philox4x32_10": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P]),
+    "gbs_shard_begin": (C.c_int, [C.POINTER(gbs_shard_state), C.c_int32, _I64, _I64, C.POINTER(gbs_array_stats),
+                                  _I64, C.c_int32]),
+    "gbs_shard_next": (C.c_int, [C.POINTER(gbs_shard_state)]),
+    "gbs_shard_update": (C.c_int, [C.POINTER(gbs_shard_state), C.POINTER(gbs_cost_eval)]),
+    "gbs_compact_f32": (C.c_int, [_P, _P, _I64, C.c_double, C.c_double, _P, _I64, C.POINTER(_I64), _P]),
+    "gbs_compact_f64": (C.c_int, [_P, _P, _I64, C.c_double, C.c_double, _P, _I64, C.POINTER(_I64), _P]),
     "gbs_status_string": (C.c_char_p, [C.c_int]),
 }
 
@@ -231,6 +248,19 @@ class Context:
                   C.c_void_p(buf.data_ptr()), _stream_ptr(stream)), "gbs_cost_pass")
         rec = gbs_cost_eval.from_buffer_copy(bytes(buf.cpu().numpy()))
         return {f: getattr(rec, f) for f, _ in gbs_cost_eval._fields_ if f != "pad"}
+
+    def compact(self, x, a, b, z=None, stream=None):
+        """The elements of x in (a, b] (any order), as a view of z (allocated with room
+        for all of x when None)."""
+        import torch
+        x = _as_input(x)
+        if z is None:
+            z = torch.empty(x.numel(), dtype=x.dtype, device=x.device)
+        cnt = _I64(0)
+        fn = globals()["gbs_compact_" + _suffix(x)]
+        _check(fn(self._h, C.c_void_p(x.data_ptr()), x.numel(), float(a), float(b), C.c_void_p(z.data_ptr()),
+                  z.numel(), C.byref(cnt), _stream_ptr(stream)), "gbs_compact")
+        return z[:cnt.value]
 
     # -------------------------------------------------------------- segmented
     def _seg_args(self, x, offsets, k, out):

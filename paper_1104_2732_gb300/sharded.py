@@ -1,0 +1,180 @@
+"""Selection over a vector split into shards: Algorithm 1 (Sec. 3) with the per-pass
+results of the shards summed between passes, as the paper's multi-GPU remark (Sec. 4)
+sums the per-device reductions on the host.
+
+The scalar steps are the library's host functions ``gbs_shard_begin`` /
+``gbs_shard_next`` / ``gbs_shard_update`` (include/gbselect.h); every per-element pass
+runs on a shard through a *backend*, and the per-pass totals are formed by a *comm*:
+
+* backend (per-shard work): ``stats(x) -> dict`` (the gbs_array_stats fields),
+  ``cost_pass(x, a, t) -> dict`` (c_lt_t, c_le_t, c_le_a, S), ``compact(x, a, b) ->
+  shard's elements of (a, b]``, ``select(z, r) -> z_(r)`` and ``concat(list)``.
+  :class:`GpuBackend` runs them with a :class:`~paper_1104_2732_gb300.Context`.
+* comm (totals over processes): ``sum_i64``, ``sum_f64``, ``min_f64``, ``max_f64`` on
+  lists of numbers and ``gather(z)`` of the compacted sets.  :class:`LocalComm` is one
+  process holding every shard (host-simulated shards); :class:`TorchComm` uses
+  ``torch.distributed`` (one or more shards per rank; the collectives are one small
+  all-reduce per pass and one all-gather of at most cap elements at the end).
+
+The result equals the single-array result bit for bit.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+from . import (GBS_OK, GBS_SHARD_COMPACT, GBS_SHARD_DONE, GBS_SHARD_ITERATE, GBS_SHARD_NAN, GBS_ENAN,
+               GbsError, gbs_array_stats, gbs_cost_eval, gbs_shard_begin, gbs_shard_next,
+               gbs_shard_state, gbs_shard_update)
+
+_STAT_SUMS = ("n", "n_nan", "n_neginf", "n_posinf", "n_negzero", "n_finite")
+_EVAL_SUMS = ("c_lt_t", "c_le_t", "c_le_a")
+
+
+def _check(status, what):
+    if status != GBS_OK:
+        raise GbsError(status, what)
+
+
+class LocalComm:
+    """Every shard lives in this process: the totals are the local sums."""
+
+    def sum_i64(self, v):
+        return [int(a) for a in v]
+
+    def sum_f64(self, v):
+        return [float(a) for a in v]
+
+    def min_f64(self, v):
+        return [float(a) for a in v]
+
+    def max_f64(self, v):
+        return [float(a) for a in v]
+
+    def gather(self, z, backend):
+        return z
+
+
+class TorchComm:
+    """Totals over the ranks of a torch.distributed process group (NCCL on devices,
+    gloo on CPU tensors); ``device`` is where the small reduction tensors live."""
+
+    def __init__(self, group=None, device="cpu"):
+        import torch.distributed as dist
+        self.dist = dist
+        self.group = group
+        self.device = device
+
+    def _reduce(self, v, dtype, op):
+        import torch
+        t = torch.tensor(v, dtype=dtype, device=self.device)
+        self.dist.all_reduce(t, op=op, group=self.group)
+        return t.cpu().tolist()
+
+    def sum_i64(self, v):
+        import torch
+        return [int(a) for a in self._reduce(v, torch.int64, self.dist.ReduceOp.SUM)]
+
+    def sum_f64(self, v):
+        import torch
+        return self._reduce(v, torch.float64, self.dist.ReduceOp.SUM)
+
+    def min_f64(self, v):
+        import torch
+        return self._reduce(v, torch.float64, self.dist.ReduceOp.MIN)
+
+    def max_f64(self, v):
+        import torch
+        return self._reduce(v, torch.float64, self.dist.ReduceOp.MAX)
+
+    def gather(self, z, backend):
+        """Concatenation over the ranks (rank order) of each rank's compacted set."""
+        import numpy as np
+        import torch
+        if not isinstance(z, torch.Tensor):
+            z = torch.from_numpy(np.ascontiguousarray(z))
+        world = self.dist.get_world_size(self.group)
+        n = torch.tensor([z.numel()], dtype=torch.int64, device=self.device)
+        sizes = [torch.zeros_like(n) for _ in range(world)]
+        self.dist.all_gather(sizes, n, group=self.group)
+        sizes = [int(s.item()) for s in sizes]
+        m = max(sizes)
+        buf = torch.zeros(m, dtype=z.dtype, device=z.device)
+        buf[:z.numel()] = z
+        parts = [torch.zeros_like(buf) for _ in range(world)]
+        self.dist.all_gather(parts, buf, group=self.group)
+        return backend.concat([p[:s] for p, s in zip(parts, sizes)])
+
+
+class GpuBackend:
+    """Per-shard passes with the library's kernels (shards: contiguous CUDA tensors)."""
+
+    def __init__(self, ctx):
+        self.ctx = ctx
+
+    def stats(self, x):
+        return self.ctx.array_stats(x)
+
+    def cost_pass(self, x, a, t):
+        return self.ctx.cost_pass(x, 1, a, t)
+
+    def compact(self, x, a, b):
+        return self.ctx.compact(x, a, b)
+
+    def concat(self, zs):
+        import torch
+        return torch.cat(list(zs)) if zs else None
+
+    def select(self, z, r):
+        return float(self.ctx.select_kth(z, r).item())
+
+
+def select_kth_sharded(shards, k, backend, comm=None, elem_bytes=4, cap=0, maxit=0, trace=None):
+    """x_(k) of the concatenation of the shards of every process (1-based k).
+
+    ``shards``: this process's shards (any number, empty ones allowed); ``k`` is the rank
+    in the whole vector.  Returns a Python float holding the element (``-0.0`` kept)."""
+    comm = comm or LocalComm()
+    shards = [s for s in shards if s is not None and len(s) > 0]
+    if not shards:
+        raise ValueError("every process needs at least one non-empty shard")
+    # pass 0 on every shard (Sec. 3, step 0), totals over the shards and processes
+    st = [backend.stats(s) for s in shards]
+    sums = comm.sum_i64([sum(int(r[f]) for r in st) for f in _STAT_SUMS])
+    fin = [r for r in st if int(r["n_finite"]) > 0]
+    total = gbs_array_stats()
+    for f, v in zip(_STAT_SUMS, sums):
+        setattr(total, f, v)
+    total.sum = comm.sum_f64([math.fsum(float(r["sum"]) for r in fin)])[0]
+    total.min = comm.min_f64([min((float(r["min"]) for r in fin), default=math.inf)])[0]
+    total.max = comm.max_f64([max((float(r["max"]) for r in fin), default=-math.inf)])[0]
+    if total.n_finite == 0:
+        total.min = total.max = 0.0
+    n = total.n
+    state = gbs_shard_state()
+    _check(gbs_shard_begin(C.byref(state), int(elem_bytes), n, int(k), C.byref(total), int(cap), int(maxit)),
+           "gbs_shard_begin")
+    # cutting-plane passes (Algorithm 1, steps 1.1-1.4)
+    while state.phase == GBS_SHARD_ITERATE:
+        _check(gbs_shard_next(C.byref(state)), "gbs_shard_next")
+        if state.phase != GBS_SHARD_ITERATE:
+            break
+        a, t = state.a, state.t
+        ev = [backend.cost_pass(s, a, t) for s in shards]
+        tot = gbs_cost_eval()
+        for f, v in zip(_EVAL_SUMS, comm.sum_i64([sum(int(r[f]) for r in ev) for f in _EVAL_SUMS])):
+            setattr(tot, f, v)
+        tot.S = comm.sum_f64([math.fsum(float(r["S"]) for r in ev)])[0]
+        if trace is not None:
+            trace.append(t)
+        _check(gbs_shard_update(C.byref(state), C.byref(tot)), "gbs_shard_update")
+    if state.phase == GBS_SHARD_NAN:
+        raise GbsError(GBS_ENAN, "select_kth_sharded")
+    if state.phase == GBS_SHARD_DONE:
+        return state.result
+    # finish: compaction of (a, b] on every shard, selection inside the union (Sec. 3)
+    assert state.phase == GBS_SHARD_COMPACT
+    local = [backend.compact(s, state.a, state.b) for s in shards]
+    z = comm.gather(backend.concat(local), backend)
+    r = int(k - state.cle_a)
+    return backend.select(z, r)
