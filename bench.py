@@ -135,6 +135,38 @@ class ClockSampler:
                 "region_s": (self.t1 - self.t0) if self.t0 and self.t1 else None}
 
 
+SELECT_SOURCES = ("select.cu", "select.cuh", "common.cuh", "elem.cuh", "layout.cuh", "bracket.cuh")
+
+
+def select_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in SELECT_SOURCES:
+        with open(os.path.join(ROOT, "paper_1104_2732_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def select_traffic():
+    """Mean DRAM bytes (read + write) per launch of the select kernel over the five ranks of
+    this workload, from the ncu capture summarised in profiles/select_kernel_f32_n2e27.md,
+    when that capture was taken of the current kernel sources (their sha256 is recorded
+    there); None otherwise."""
+    import re
+    path = os.path.join(ROOT, "profiles", "select_kernel_f32_n2e27.md")
+    if not os.path.exists(path):
+        return None, "no capture"
+    with open(path) as f:
+        text = f.read()
+    m1 = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
+    m2 = re.search(r"kernel_sources_sha256:\s*([0-9a-f]{64})", text)
+    if not (m1 and m2):
+        return None, "no capture"
+    if m2.group(1) != select_sources_sha256():
+        return None, "kernel changed since the capture"
+    return int(m1.group(1)), "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over the 5 ranks"
+
+
 def cpu_oracle_time(x, ks):
     """The CPU oracle as it stands (oracle.select.select_kth, single-threaded numpy)."""
     from oracle import select as osel
@@ -586,6 +618,7 @@ def main():
     bytes_per_call = [(r["passes"] * n + r["finish_pop"]) * 4 for r in records]
     alg_bytes = args.steps * sum(bytes_per_call)
     achieved = alg_bytes / (sum(launch_ms) * 1e-3) / 1e9
+    traffic, traffic_src = select_traffic()
     # per-pass bandwidth from the kernel's own timestamps (pass 0 and Kelley passes)
     pass_gbs, stream_gbs, overhead_us = [], [], []
     for r in records:
@@ -673,7 +706,9 @@ def main():
             "e2e": {"value": e2e_value, "unit": "Gelem/s", "h2d_bytes_per_step": n * 4,
                     "d2h_bytes_per_step": len(ks) * 4},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": alg_bytes / (args.steps * len(ks)),
+                         "traffic_source": traffic_src,
                          "peak_kind": f"{peak_kind} hbm_gbs", "kernel": "select_kernel<float>"},
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
