@@ -268,10 +268,12 @@ def bench_segmented(gbs, ctx, torch, np, args):
 
 
 def bench_lms(gbs, ctx, torch, np, args):
-    """LMS / LTS of 2048 elemental candidates on n = 1e6, p = 8 (30% contaminated rows):
-    the chosen form (TF32 x 3 tensor-core residuals + batched trimmed-sum select) against
-    the plain form (float32 CUDA-core residuals + one single-array select per candidate
-    and rank), with the relative error of sampled candidates against the float64 oracle."""
+    """LMS / LTS of 2048 elemental candidates on n = 1e6, p = 8 (30% contaminated rows), in
+    three forms: fused (TF32 x 3 tensor-core residuals recomputed in every cutting-plane
+    pass, never written), materialised (TF32 x 3 residual matrix + batched trimmed-sum
+    select) and plain (float32 CUDA-core residuals + one single-array select per
+    candidate and rank).  The chosen form is the faster of the first two; relative errors
+    of sampled candidates against the float64 oracle for every form."""
     import synth
     from oracle import regression as oreg
     n, p, C = 1_000_000, 8, 2048
@@ -280,37 +282,54 @@ def bench_lms(gbs, ctx, torch, np, args):
     k, h = (n + 1) // 2, (n + p + 1) // 2
     Xt, yt, tt = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (X, y, th))
 
-    def timed(precision, batched, reps):
-        ctx.lms_lts(Xt, yt, tt, k=k, h=h, precision=precision, batched=batched)   # warm-up
+    def timed(fn, reps):
+        fn()   # warm-up
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(reps):
-            out = ctx.lms_lts(Xt, yt, tt, k=k, h=h, precision=precision, batched=batched)
+            out = fn()
         e1.record()
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps, out
 
-    chosen_ms, (lms_c, lts_c) = timed(1, True, max(3, args.steps // 2))
-    plain_ms, (lms_p, lts_p) = timed(0, False, 1)
-    lms_c, lts_c = lms_c.cpu().numpy(), lts_c.cpu().numpy()
-    lms_p, lts_p = lms_p.cpu().numpy(), lts_p.cpu().numpy()
+    reps = max(3, min(20, args.steps // 5))
+    fused_ms, (lms_f, lts_f, fused_passes) = timed(lambda: ctx.lms_lts_fused(Xt, yt, tt, k=k, h=h), reps)
+    mat_ms, (lms_m, lts_m) = timed(lambda: ctx.lms_lts(Xt, yt, tt, k=k, h=h, precision=1, batched=True), reps)
+    plain_ms, (lms_p, lts_p) = timed(lambda: ctx.lms_lts(Xt, yt, tt, k=k, h=h, precision=0, batched=False), 1)
+    # the residual kernel alone (materialised form): bytes written against HBM
+    S = torch.empty(C, n, dtype=torch.float32, device="cuda")
+    res_ms, _ = timed(lambda: ctx.residual_sq(Xt, yt, tt, precision=1, out=S), reps)
+    del S
+    torch.cuda.empty_cache()
+    peaks, kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    forms = {"fused": (lms_f, lts_f), "materialised": (lms_m, lts_m), "plain": (lms_p, lts_p)}
+    forms = {kk: (a.cpu().numpy(), b.cpu().numpy()) for kk, (a, b) in forms.items()}
     rng = np.random.default_rng(8)
     sample = rng.choice(C, 8, replace=False)
-    err = {"chosen": [0.0, 0.0], "plain": [0.0, 0.0]}
+    err = {kk: [0.0, 0.0] for kk in forms}
     for c in sample:
         wl, wt = oreg.lms_lts(X, y, th[c:c + 1].T, k, h)
-        for name, l, t in (("chosen", lms_c, lts_c), ("plain", lms_p, lts_p)):
+        for name, (l, t) in forms.items():
             err[name][0] = max(err[name][0], abs(l[c] / wl[0] - 1))
             err[name][1] = max(err[name][1], abs(t[c] / wt[0] - 1))
+    chosen = "fused" if fused_ms <= mat_ms else "materialised"
+    chosen_ms = min(fused_ms, mat_ms)
     return {
         "workload": "LMS/LTS, n=1e6, p=8, 30% contaminated rows, 2048 elemental candidates, k=(n+1)/2, h=(n+p+1)/2",
-        "metric": "candidates/s", "value": C / (chosen_ms * 1e-3), "ms": chosen_ms,
+        "metric": "candidates/s", "value": C / (chosen_ms * 1e-3), "ms": chosen_ms, "chosen_form": chosen,
+        "fused_ms": fused_ms, "fused_passes": fused_passes, "materialised_ms": mat_ms,
         "plain_value": C / (plain_ms * 1e-3), "plain_ms": plain_ms, "speedup_vs_plain": plain_ms / chosen_ms,
-        "max_rel_err_vs_float64": {"lms_chosen": err["chosen"][0], "lts_chosen": err["chosen"][1],
-                                   "lms_plain": err["plain"][0], "lts_plain": err["plain"][1],
+        "max_rel_err_vs_float64": {**{f"lms_{kk}": v[0] for kk, v in err.items()},
+                                   **{f"lts_{kk}": v[1] for kk, v in err.items()},
                                    "candidates_sampled": int(sample.size), "target": 1e-5},
-        "residual_bytes_written": C * n * 4,
+        "residual_kernel": {"ms": res_ms, "bytes_written": C * n * 4,
+                            "gbs": C * n * 4 / (res_ms * 1e-3) / 1e9,
+                            "hbm_frac": C * n * 4 / (res_ms * 1e-3) / 1e9 / hbm, "peak_kind": f"{kind} hbm_gbs"},
+        "fused_vs_materialised_max_rel_diff": {
+            "lms": float(np.max(np.abs(forms["fused"][0] / forms["materialised"][0] - 1))),
+            "lts": float(np.max(np.abs(forms["fused"][1] / forms["materialised"][1] - 1)))},
     }
 
 

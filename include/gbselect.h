@@ -240,6 +240,21 @@ gbs_status gbs_lms_lts_f32(gbs_ctx* ctx, const float* X, const float* y, int64_t
                            int32_t C, int64_t k_lms, int64_t h_lts, float* lms_out, double* lts_out,
                            int32_t precision, int32_t batched, void* stream);
 
+/* The same objectives without writing the residual matrix: every pass of the cutting
+ * plane (Algorithm 1, Sec. 3) recomputes s_ic = (y_i - x_i . theta_c)^2 on the tensor
+ * cores (TF32 x 3 split, as precision 1 above) and reduces it per candidate in the
+ * product's epilogue; the passes bracket the ranks k_lms and h_lts together, compact each
+ * candidate's bracket and finish in the segmented select's trimmed-sum mode.  Candidates
+ * whose residuals are not all finite, or whose bracket does not fit the compaction
+ * buffer (49152 elements), are recomputed by the batched form of gbs_lms_lts_f32.
+ * X: n x p row-major, y: n, theta: C x p row-major, all float32 device arrays (any
+ * alignment; p <= 16, n <= 2^31).  Outputs as gbs_lms_lts_f32.  passes (host pointer, may
+ * be NULL) receives the number of passes over the rows.  Synchronises `stream` once per
+ * pass (the host stops when every candidate is ready to compact). */
+gbs_status gbs_lms_lts_fused_f32(gbs_ctx* ctx, const float* X, const float* y, int64_t n, int32_t p,
+                                 const float* theta, int32_t C, int64_t k_lms, int64_t h_lts,
+                                 float* lms_out, double* lts_out, int32_t* passes, void* stream);
+
 /* ---- Learned starting bracket (no counterpart in the paper; it replaces the starting
  * bracket of Algorithm 1, step 0).  A sketch of x -- 1024 samples x[j*floor(n/1024)],
  * sorted; features: the 32 sample quantiles at sorted positions 16+32i standardised by

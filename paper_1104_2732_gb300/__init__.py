@@ -95,6 +95,8 @@ _SIGS = {
     "gbs_residual_sq_f32": (C.c_int, [_P, _P, _P, _I64, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P]),
     "gbs_lms_lts_f32": (C.c_int, [_P, _P, _P, _I64, C.c_int32, _P, C.c_int32, _I64, _I64, _P, _P, C.c_int32,
                                   C.c_int32, _P]),
+    "gbs_lms_lts_fused_f32": (C.c_int, [_P, _P, _P, _I64, C.c_int32, _P, C.c_int32, _I64, _I64, _P, _P,
+                                        C.POINTER(C.c_int32), _P]),
     "gbs_bracket_model_set": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int32]),
     "gbs_bracket_model_get": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int32]),
     "gbs_bracket_model_save": (C.c_int, [_P, C.c_char_p]),
@@ -350,6 +352,22 @@ class Context:
                                C.c_void_p(lts.data_ptr()), int(precision), int(bool(batched)), _stream_ptr(stream)),
                "gbs_lms_lts")
         return lms, lts
+
+    def lms_lts_fused(self, X, y, theta, k=None, h=None, stream=None):
+        """(LMS, LTS, passes): the same objectives with the residuals recomputed in every
+        pass and never written (gbs_lms_lts_fused_f32)."""
+        import torch
+        X, y, theta, n, p, Cn = self._reg_args(X, y, theta)
+        k = (n + 1) // 2 if k is None else int(k)
+        h = (n + p + 1) // 2 if h is None else int(h)
+        lms = torch.empty(Cn, dtype=torch.float32, device=X.device)
+        lts = torch.empty(Cn, dtype=torch.float64, device=X.device)
+        npass = C.c_int32(0)
+        _check(gbs_lms_lts_fused_f32(self._h, C.c_void_p(X.data_ptr()), C.c_void_p(y.data_ptr()), n, p,
+                                     C.c_void_p(theta.data_ptr()), Cn, k, h, C.c_void_p(lms.data_ptr()),
+                                     C.c_void_p(lts.data_ptr()), C.byref(npass), _stream_ptr(stream)),
+               "gbs_lms_lts_fused")
+        return lms, lts, npass.value
 
     # -------------------------------------------------------------- learned bracket
     N_PARAMS = 6658

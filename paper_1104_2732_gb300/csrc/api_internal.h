@@ -37,6 +37,9 @@ struct gbs_ctx {
   size_t lms_bytes = 0;
   int lms_off_C = 0;
   long long lms_off_n = 0;
+  // fused LMS / LTS: split X and theta, per-candidate state, compaction buffers
+  void* fused_buf = nullptr;
+  size_t fused_bytes = 0;
   // bracket-proposal network: weights | Adam m | Adam v | gradient | scalars (device)
   float* model = nullptr;
   int model_loaded = 0;
@@ -48,4 +51,5 @@ gbs_status gbs_internal_ensure(gbs_ctx* c, size_t z_bytes);
 // Frees the resources other subsystems attached to the context.
 void gbs_internal_release(gbs_ctx* c);
 void gbs_internal_release_lms(gbs_ctx* c);
+void gbs_internal_release_fused(gbs_ctx* c);
 void gbs_internal_release_model(gbs_ctx* c);

@@ -3,5 +3,6 @@
 
 void gbs_internal_release(gbs_ctx* c) {
   gbs_internal_release_lms(c);
+  gbs_internal_release_fused(c);
   gbs_internal_release_model(c);
 }

@@ -8,6 +8,7 @@ Cases (inputs from ``synth``; every case holds at most a few GB on the device):
   learned    median of the 2^27 mixture starting from the shipped bracket model
   segmented  the 4096-array batch (seed 5), medians, R batched calls
   lms        LMS/LTS objectives, n = 1e6, p = 8, 512 candidates (seeds 6, 7), TF32x3 + batched
+  lms_fused  the same objectives for 2048 candidates with the residuals recomputed per pass
   propose    the bracket-proposal kernel on a 2^24 array, R calls
 Each case runs W warm-up repetitions, then R timed ones, prints one line with the mean
 device time per repetition and exits 0.
@@ -24,7 +25,7 @@ sys.path.insert(0, os.path.dirname(HERE))
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["select", "select64", "learned", "segmented", "lms", "propose"])
+    ap.add_argument("case", choices=["select", "select64", "learned", "segmented", "lms", "lms_fused", "propose"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
     args = ap.parse_args()
@@ -61,14 +62,17 @@ def main():
 
         def rep():
             ctx.select_segmented(x, offs, out=out)
-    elif case == "lms":
-        n, p, C = 1_000_000, 8, 512
+    elif case in ("lms", "lms_fused"):
+        n, p, C = 1_000_000, 8, (512 if case == "lms" else 2048)
         X, y, _ = synth.regression(n, p, 6)
         theta = np.ascontiguousarray(synth.elemental_thetas(X, y, C, 7).T)      # (C, p)
         Xd, yd, td = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (X, y, theta))
 
         def rep():
-            ctx.lms_lts(Xd, yd, td, (n + 1) // 2, (n + p + 1) // 2, precision=1, batched=1)
+            if case == "lms":
+                ctx.lms_lts(Xd, yd, td, (n + 1) // 2, (n + p + 1) // 2, precision=1, batched=1)
+            else:
+                ctx.lms_lts_fused(Xd, yd, td, (n + 1) // 2, (n + p + 1) // 2)
     else:
         x = torch.empty(1 << 24, device="cuda")
         ctx.generate_training_array(x, 1, 3.0, 0.0, 1.0, 5.0, 2.0, seed=123)

@@ -147,3 +147,94 @@ def test_lms_lts_rejects_bad_arguments(ctx, lib):
     X17 = torch.zeros(10, 17, device="cuda")
     with pytest.raises(lib.GbsError):
         ctx.residual_sq(X17, torch.zeros(10, device="cuda"), torch.zeros(2, 17, device="cuda"))
+
+
+# ---------------------------------------------------------------- fused form
+def check_against_oracle(lms, lts, X, y, th, k, h, cands=None):
+    cands = range(th.shape[0]) if cands is None else cands
+    for c in cands:
+        wl, wt = oreg.lms_lts(X, y, th[c:c + 1].T, k, h)
+        assert abs(lms[c] - wl[0]) <= REL * abs(wl[0]), (c, lms[c], wl[0])
+        assert abs(lts[c] - wt[0]) <= REL * abs(wt[0]), (c, lts[c], wt[0])
+
+
+@pytest.mark.parametrize("p,C", [(8, 96), (8, 130), (3, 37), (1, 5), (12, 37), (16, 20)])
+def test_fused_matches_float64_oracle(ctx, p, C):
+    """Residuals recomputed in every pass (never written): within 1e-5 of the float64
+    oracle for every candidate; C not a multiple of the 128 candidates of a CTA."""
+    n = 20001 if p == 8 else 7777
+    X, y, th = problem(n, p, C, seed=97 + p)
+    k, h = (n + 1) // 2, (n + p + 1) // 2
+    Xt, yt, tt = to_dev(X, y, th)
+    lms, lts, passes = ctx.lms_lts_fused(Xt, yt, tt, k=k, h=h)
+    lms, lts = lms.cpu().numpy(), lts.cpu().numpy()
+    assert 2 <= passes <= 66
+    want_lms, want_lts = oreg.lms_lts(X, y, th.T, k, h)
+    assert np.all(np.abs(lms - want_lms) <= REL * np.abs(want_lms)), np.max(np.abs(lms / want_lms - 1))
+    assert np.all(np.abs(lts - want_lts) <= REL * np.abs(want_lts)), np.max(np.abs(lts / want_lts - 1))
+
+
+def test_fused_theta_zero_is_exact(ctx):
+    """p = 1, theta = 0: s = y^2 exactly, so LMS is the exact order statistic of y^2."""
+    n = 9999
+    y = synth.uniform(n, seed=93) - np.float32(0.5)
+    X = np.ones((n, 1), np.float32)
+    th = np.zeros((3, 1), np.float32)
+    Xt, yt, tt = to_dev(X, y, th)
+    k = (n + 1) // 2
+    lms, lts, _ = ctx.lms_lts_fused(Xt, yt, tt, k=k, h=k)
+    s32 = (y * y).astype(np.float32)
+    assert np.all(lms.cpu().numpy() == osel.select_kth(s32, k))
+    assert lts.cpu().numpy() == pytest.approx(oreg.lts(s32, k), rel=SUM_REL)
+
+
+def test_fused_exact_fit_all_residuals_zero(ctx):
+    """y = X theta exactly (small integers): every residual is 0, LMS = LTS = 0."""
+    rng = np.random.default_rng(98)
+    n, p = 4096, 4
+    X = rng.integers(-3, 4, (n, p)).astype(np.float32)
+    th = rng.integers(-3, 4, (2, p)).astype(np.float32)
+    y = (X @ th[0]).astype(np.float32)
+    Xt, yt, tt = to_dev(X, y, th)
+    lms, lts, _ = ctx.lms_lts_fused(Xt, yt, tt)
+    assert lms.cpu().numpy()[0] == 0.0 and lts.cpu().numpy()[0] == 0.0
+    check_against_oracle(lms.cpu().numpy(), lts.cpu().numpy(), X, y, th, (n + 1) // 2, (n + p + 1) // 2, [1])
+
+
+def test_fused_ranks_far_apart_use_the_batched_form(ctx):
+    """k and h far apart: the bracket holding both exceeds the compaction buffer, so the
+    candidates are finished by the materialising batched form; results still match."""
+    n, p, C = 200000, 4, 20
+    X, y, th = problem(n, p, C, seed=94)
+    Xt, yt, tt = to_dev(X, y, th)
+    k, h = n // 10, (9 * n) // 10
+    lms, lts, _ = ctx.lms_lts_fused(Xt, yt, tt, k=k, h=h)
+    check_against_oracle(lms.cpu().numpy(), lts.cpu().numpy(), X, y, th, k, h)
+
+
+def test_fused_nan_row_matches_batched_form(ctx):
+    n, p, C = 5000, 8, 6
+    X, y, th = problem(n, p, C, seed=99)
+    X[17, 2] = np.nan
+    Xt, yt, tt = to_dev(X, y, th)
+    lms, lts, _ = ctx.lms_lts_fused(Xt, yt, tt)
+    assert np.all(np.isnan(lms.cpu().numpy()))
+
+
+def test_fused_full_size_against_oracle_and_batched(ctx):
+    """The benchmark problem (n = 1e6, p = 8, 30% contaminated rows, 2048 candidates):
+    12 sampled candidates against the float64 oracle, every candidate within 2e-5 of the
+    materialising TF32 x 3 batched form (each is within 1e-5 of float64)."""
+    n, p, C = 1_000_000, 8, 2048
+    X, y, th = problem(n, p, C, seed=6)
+    k, h = (n + 1) // 2, (n + p + 1) // 2
+    Xt, yt, tt = to_dev(X, y, th)
+    lms, lts, passes = ctx.lms_lts_fused(Xt, yt, tt, k=k, h=h)
+    lms, lts = lms.cpu().numpy(), lts.cpu().numpy()
+    assert passes <= 20
+    bl, bt = ctx.lms_lts(Xt, yt, tt, k=k, h=h, precision=1, batched=True)
+    bl, bt = bl.cpu().numpy(), bt.cpu().numpy()
+    assert np.all(np.abs(lms - bl) <= 2 * REL * np.abs(bl))
+    assert np.all(np.abs(lts - bt) <= 2 * REL * np.abs(bt))
+    rng = np.random.default_rng(95)
+    check_against_oracle(lms, lts, X, y, th, k, h, rng.choice(C, 12, replace=False))
