@@ -22,9 +22,7 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s
 
 // ---------------------------------------------------------------------------------
 // Keys.  ukey(): unsigned totalOrder key (-inf < ... < -0 < +0 < ... < +inf) used by
-// the radix finish.  skey(): signed key whose integer order is IEEE comparison order
-// for non-NaN values (-0 and +0 share key 0); used for float64 comparisons so that the
-// per-element loop stays on the integer pipes.
+// the radix finish and, for float64, by every comparison of the passes (integer pipes).
 // ---------------------------------------------------------------------------------
 template <typename T> struct KeyOf;
 template <> struct KeyOf<float> {
@@ -61,26 +59,19 @@ __device__ __forceinline__ uint32_t ukey(float v) {
   uint32_t u = __float_as_uint(v);
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
-__device__ __forceinline__ uint64_t ukey(double v) {
-  uint64_t u = (uint64_t)__double_as_longlong(v);
-  return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+// float64 totalOrder key from the bits: flip everything for a negative value, the sign
+// bit for a positive one (the mask comes from an arithmetic shift of the high word).
+__device__ __forceinline__ uint64_t ukey_bits(uint64_t u) {
+  const uint32_t m = (uint32_t)((int32_t)(uint32_t)(u >> 32) >> 31);
+  return u ^ ((((uint64_t)(m | 0x80000000u)) << 32) | (uint64_t)m);
 }
+__device__ __forceinline__ uint64_t ukey(double v) { return ukey_bits((uint64_t)__double_as_longlong(v)); }
 __device__ __forceinline__ float ukey_value(uint32_t k, float) {
   uint32_t u = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
   return __uint_as_float(u);
 }
 __device__ __forceinline__ double ukey_value(uint64_t k, double) {
   uint64_t u = (k & 0x8000000000000000ull) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
-  return __longlong_as_double((long long)u);
-}
-
-__device__ __forceinline__ int64_t skey_bits(uint64_t u) {
-  int64_t mag = (int64_t)(u & 0x7FFFFFFFFFFFFFFFull);
-  return ((int64_t)u < 0) ? -mag : mag;
-}
-__device__ __forceinline__ int64_t skey(double v) { return skey_bits((uint64_t)__double_as_longlong(v)); }
-__device__ __forceinline__ double skey_value(int64_t s) {
-  uint64_t u = s < 0 ? ((uint64_t)(-s) | 0x8000000000000000ull) : (uint64_t)s;
   return __longlong_as_double((long long)u);
 }
 

@@ -13,8 +13,8 @@ namespace gbs {
 
 // ---------------------------------------------------------------------------------
 // Per-type element operations.  cmp(): the value compared against the iterate
-// (IEEE float for float32, the signed integer key for float64).  img(): float32 image
-// used only for the cost partials.
+// (IEEE float for float32, the unsigned totalOrder key for float64, see CmpOf).  img():
+// float32 image used only for the cost partials.
 // ---------------------------------------------------------------------------------
 template <typename T> struct Ops;
 template <> struct Ops<float> {
@@ -38,10 +38,10 @@ template <> struct Ops<float> {
   }
 };
 template <> struct Ops<double> {
-  using C = long long;
+  using C = unsigned long long;
   using V = double2;
   static constexpr int kVec = 2;
-  static __device__ __forceinline__ C cmp(double x) { return (long long)skey(x); }
+  static __device__ __forceinline__ C cmp(double x) { return ukey(x); }
   static __device__ __forceinline__ float img(double x) {
     return f64_to_f32_trunc((uint64_t)__double_as_longlong(x));
   }
@@ -117,32 +117,52 @@ __device__ __forceinline__ void core(float x, float a, float t, float nsig, floa
       : "+r"(lt), "+r"(le), "+f"(S)
       : "f"(x), "f"(a), "f"(t), "f"(nsig), "f"(tsig));
 }
-// float64: comparisons on signed integer keys, the cost on the truncated float32 image.
-__device__ __forceinline__ void core(double xv, long long sa, long long st, float nsig, float tsig,
-                                     unsigned& lt, unsigned& le, float& S) {
+// float64: comparisons on unsigned totalOrder keys (integer pipes; the thresholds carry
+// the IEEE treatment of zeros, see CmpOf), the cost on the truncated float32 image.
+// ka = CmpOf::le(a), kt_lt = CmpOf::lt(t), kt_le = CmpOf::le(t).
+__device__ __forceinline__ void core(double xv, unsigned long long ka, unsigned long long kt_lt,
+                                     unsigned long long kt_le, float nsig, float tsig, unsigned& lt, unsigned& le,
+                                     float& S) {
   const uint64_t u = (uint64_t)__double_as_longlong(xv);
-  const long long sx = (long long)skey_bits(u);
-  lt += (sx < st);
-  le += (sx <= st);
-  const bool in = (sx > sa) & (sx < st);
+  const unsigned long long kx = ukey_bits(u);
+  lt += (kx < kt_lt);
+  le += (kx <= kt_le);
+  const bool in = (kx > ka) & (kx < kt_lt);
   const float d = fmaf(f64_to_f32_trunc(u), nsig, tsig);
   S += in ? d : 0.f;
+}
+// float32: the IEEE comparisons of the inline-PTX core (both thresholds are t itself).
+__device__ __forceinline__ void core(float x, float a, float t_lt, float, float nsig, float tsig, unsigned& lt,
+                                     unsigned& le, float& S) {
+  core(x, a, t_lt, nsig, tsig, lt, le, S);
 }
 
 template <typename T> __device__ __forceinline__ typename Ops<T>::C cmp_pos_inf();
 template <> __device__ __forceinline__ float cmp_pos_inf<float>() { return INFINITY; }
-template <> __device__ __forceinline__ long long cmp_pos_inf<double>() { return 0x7FF0000000000000ll; }
+template <> __device__ __forceinline__ unsigned long long cmp_pos_inf<double>() { return 0xFFF0000000000000ull; }
+template <typename T> __device__ __forceinline__ typename Ops<T>::C cmp_neg_inf();
+template <> __device__ __forceinline__ float cmp_neg_inf<float>() { return -INFINITY; }
+template <> __device__ __forceinline__ unsigned long long cmp_neg_inf<double>() { return 0x000FFFFFFFFFFFFFull; }
 
 // value of a comparison key
 __device__ __forceinline__ float cmp_value(float c, float) { return c; }
-__device__ __forceinline__ double cmp_value(long long c, double) { return skey_value(c); }
+__device__ __forceinline__ double cmp_value(unsigned long long c, double) { return ukey_value(c, 0.0); }
 
+// Comparison images.  of(x): the image of an element; lt(t) and le(t): thresholds with
+// x < t  <=>  of(x) < lt(t)  and  x <= t  <=>  of(x) <= le(t)  (so x > a <=> of(x) > le(a))
+// for every non-NaN x under IEEE comparison.  float32 compares the values themselves;
+// float64 compares unsigned totalOrder keys, where -0 sorts before +0, so a zero
+// threshold takes the key of -0 for "<" and of +0 for "<=".
 template <typename T> struct CmpOf;
 template <> struct CmpOf<float> {
   static __device__ __forceinline__ float of(float v) { return v; }
+  static __device__ __forceinline__ float lt(float v) { return v; }
+  static __device__ __forceinline__ float le(float v) { return v; }
 };
 template <> struct CmpOf<double> {
-  static __device__ __forceinline__ long long of(double v) { return (long long)skey(v); }
+  static __device__ __forceinline__ unsigned long long of(double v) { return ukey(v); }
+  static __device__ __forceinline__ unsigned long long lt(double v) { return v == 0.0 ? ukey(-0.0) : ukey(v); }
+  static __device__ __forceinline__ unsigned long long le(double v) { return v == 0.0 ? ukey(0.0) : ukey(v); }
 };
 
 // Scalar head and tail of x handled by this thread (the first threads of CTA 0).

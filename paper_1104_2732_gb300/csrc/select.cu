@@ -170,12 +170,27 @@ struct PassAcc {
   float S;
 };
 
+// Comparison thresholds of one pass (CmpOf images): a, t and b as needed by "<" and "<=".
+template <typename T>
+struct Thr {
+  typename Ops<T>::C a_le, t_lt, t_le, b_lt, b_le;
+};
+template <typename T>
+__device__ __forceinline__ Thr<T> thresholds(T a, T t, T b) {
+  Thr<T> h;
+  h.a_le = CmpOf<T>::le(a);
+  h.t_lt = CmpOf<T>::lt(t);
+  h.t_le = CmpOf<T>::le(t);
+  h.b_lt = CmpOf<T>::lt(b);
+  h.b_le = CmpOf<T>::le(b);
+  return h;
+}
+
 // One streaming pass over x at the iterate t (Algorithm 1, step 1.2).  FIRST also counts
 // #(x <= a) and #(x < b); COMPACT also appends the elements of (a, b] to region `zr`.
 // Kept out of line so that its registers are allocated apart from the kernel's control.
 template <typename T, bool FIRST, bool COMPACT>
-__device__ __noinline__ bool cut_pass(const T* __restrict__ x, const Geometry<T>& geo, bool rev,
-                                      typename Ops<T>::C ca, typename Ops<T>::C ct, typename Ops<T>::C cb,
+__device__ __noinline__ bool cut_pass(const T* __restrict__ x, const Geometry<T>& geo, bool rev, Thr<T> h,
                                       float nsig, float tsig, T* __restrict__ zr, unsigned int* s_cnt,
                                       T* wb, PassAcc& acc) {
   using C = typename Ops<T>::C;
@@ -183,15 +198,15 @@ __device__ __noinline__ bool cut_pass(const T* __restrict__ x, const Geometry<T>
   unsigned int lt = 0, le = 0, xa = 0, xb = 0;
   float S = 0.f;
   auto f = [&](T v) {
-    core(v, ca, ct, nsig, tsig, lt, le, S);
+    core(v, h.a_le, h.t_lt, h.t_le, nsig, tsig, lt, le, S);
     if (FIRST) {
       const C cv = CmpOf<T>::of(v);
-      xa += (cv <= ca);
-      xb += (cv < cb);
+      xa += (cv <= h.a_le);
+      xb += (cv < h.b_lt);
     }
   };
   if (COMPACT) {
-    auto keep = [&](T v) { const C cv = CmpOf<T>::of(v); return (cv > ca) & (cv <= cb); };
+    auto keep = [&](T v) { const C cv = CmpOf<T>::of(v); return (cv > h.a_le) & (cv <= h.b_le); };
     if ((long long)blockIdx.x * kThreads + threadIdx.x < geo.head + (geo.n - geo.tail0)) {
       auto fk = [&](T v) {
         f(v);
@@ -222,7 +237,7 @@ __device__ __noinline__ bool stats_pass(const T* __restrict__ x, const Geometry<
                                         float x0s, StatsAcc<T>& out) {
   using C = typename Ops<T>::C;
   using V = typename Ops<T>::V;
-  C mn = cmp_pos_inf<T>(), mx = -cmp_pos_inf<T>();
+  C mn = cmp_pos_inf<T>(), mx = cmp_neg_inf<T>();
   unsigned int nnan = 0, nneg = 0, npos = 0, seen = 0;
   float sum = 0.f;
   auto f = [&](T v) {
@@ -256,11 +271,12 @@ struct ProposalAcc {
 // cost term, and a side that fails its check starts without it.
 template <typename T>
 __device__ __noinline__ bool stats_pass_learned(const T* __restrict__ x, const Geometry<T>& geo, float sig,
-                                                float x0s, typename Ops<T>::C ca, typename Ops<T>::C cb,
+                                                float x0s, typename Ops<T>::C ca,
+                                                typename Ops<T>::C cb_lt, typename Ops<T>::C cb_le,
                                                 float nsab, float bsab, T* __restrict__ zr, unsigned int* s_cnt,
                                                 T* wb, StatsAcc<T>& out, ProposalAcc& pa) {
   using C = typename Ops<T>::C;
-  C mn = cmp_pos_inf<T>(), mx = -cmp_pos_inf<T>();
+  C mn = cmp_pos_inf<T>(), mx = cmp_neg_inf<T>();
   unsigned int nnan = 0, nneg = 0, npos = 0, seen = 0, la = 0, lblt = 0;
   float sab = 0.f;
   auto f = [&](T v) {
@@ -274,13 +290,13 @@ __device__ __noinline__ bool stats_pass_learned(const T* __restrict__ x, const G
       nneg += Ops<T>::is_neginf(v);
       npos += Ops<T>::is_posinf(v);
     }
-    const bool le_a = cv <= ca, lt_b = cv < cb;
+    const bool le_a = cv <= ca, lt_b = cv < cb_lt;
     la += le_a;
     lblt += lt_b;
     const float d = fmaf(Ops<T>::img(v), nsab, bsab);
     sab += (!le_a && lt_b && cv > ca) ? d : 0.f;
   };
-  auto keep = [&](T v) { const C cv = CmpOf<T>::of(v); return (cv > ca) & (cv <= cb); };
+  auto keep = [&](T v) { const C cv = CmpOf<T>::of(v); return (cv > ca) & (cv <= cb_le); };
   if ((long long)blockIdx.x * kThreads + threadIdx.x < geo.head + (geo.n - geo.tail0)) {
     auto fk = [&](T v) {
       f(v);
@@ -347,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
   // the multiplicities of the extremes (array statistics) and the sign of a zero result.
   auto aux_pass = [&](T lo, T hi, unsigned long long* o_le, unsigned long long* o_lt,
                       unsigned long long* o_nz) -> bool {
-    const C cl = CmpOf<T>::of(lo), ch = CmpOf<T>::of(hi);
+    const C cl = CmpOf<T>::le(lo), ch = CmpOf<T>::lt(hi);
     unsigned int a0 = 0, a1 = 0, a2 = 0;
     auto f = [&](T v) {
       const C cv = CmpOf<T>::of(v);
@@ -373,13 +389,13 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
   if (A.mode == kModeEval) {
     // ---------------- one fused pass at (a, t) ----------------
     const T a = Ops<T>::from_double(A.a_eval), t = Ops<T>::from_double(A.t_eval);
-    const C ca = CmpOf<T>::of(a), ct = CmpOf<T>::of(t);
+    const C ca = CmpOf<T>::le(a), ct_lt = CmpOf<T>::lt(t), ct_le = CmpOf<T>::le(t);
     const float sig = cost_scale((double)Ops<T>::img(t) - (double)Ops<T>::img(a), per_thread);
     const float tsig = Ops<T>::img(t) * sig;
     unsigned int lt = 0, le = 0, lea = 0;
     float S = 0.f;
     auto f = [&](T v) {
-      core(v, ca, ct, -sig, tsig, lt, le, S);
+      core(v, ca, ct_lt, ct_le, -sig, tsig, lt, le, S);
       lea += (CmpOf<T>::of(v) <= ca);
     };
     stream_edges(A.x, geo, f);
@@ -434,7 +450,8 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
       sig_ab = cost_scale((double)Ops<T>::img(prop_b) - (double)Ops<T>::img(prop_a), per_thread);
       if (tid == 0) s_zcnt = 0;
       __syncthreads();
-      if (!stats_pass_learned<T>(A.x, geo, sig, x0s, CmpOf<T>::of(prop_a), CmpOf<T>::of(prop_b), -sig_ab,
+      if (!stats_pass_learned<T>(A.x, geo, sig, x0s, CmpOf<T>::le(prop_a), CmpOf<T>::lt(prop_b),
+                                 CmpOf<T>::le(prop_b), -sig_ab,
                                  Ops<T>::img(prop_b) * sig_ab, A.z + region_start(bid, nch, G, Ops<T>::kVec),
                                  &s_zcnt, s_wb, sa, pa))
         return;
@@ -548,7 +565,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
       o.n = n;
       o.n_nan = (long long)st.n_nan; o.n_neginf = nneg; o.n_posinf = npos;
       o.n_negzero = (long long)nz; o.n_finite = (long long)st.n_finite;
-      o.min = any ? st.mn : 0.0; o.max = any ? st.mx : 0.0;
+      o.min = any ? st.mn + 0.0 : 0.0; o.max = any ? st.mx + 0.0 : 0.0;   // + 0.0: a zero extreme as +0
       o.c_le_min = any ? (long long)cle : 0;
       o.c_lt_max = any ? (long long)clt - (long long)st.n_nan : 0;
       o.sum = st.sum;
@@ -654,7 +671,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
       s_br = br;
     }
     __syncthreads();
-    const C ca = CmpOf<T>::of(s_br.a), ct = CmpOf<T>::of(s_br.t), cb = CmpOf<T>::of(s_br.b);
+    const Thr<T> thr = thresholds<T>(s_br.a, s_br.t, s_br.b);
     const float nsig = -s_br.sigma;
     const float tsig = Ops<T>::img(s_br.t) * s_br.sigma;
     const int first = s_br.first, compact = s_br.compact;
@@ -665,11 +682,11 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     T* zr = A.z + region_start(bid, nch, G, Ops<T>::kVec);
     bool ok;
     if (first) {
-      if (compact) ok = cut_pass<T, true, true>(A.x, geo, rev, ca, ct, cb, nsig, tsig, zr, &s_zcnt, s_wb, acc);
-      else ok = cut_pass<T, true, false>(A.x, geo, rev, ca, ct, cb, nsig, tsig, zr, &s_zcnt, s_wb, acc);
+      if (compact) ok = cut_pass<T, true, true>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, acc);
+      else ok = cut_pass<T, true, false>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, acc);
     } else {
-      if (compact) ok = cut_pass<T, false, true>(A.x, geo, rev, ca, ct, cb, nsig, tsig, zr, &s_zcnt, s_wb, acc);
-      else ok = cut_pass<T, false, false>(A.x, geo, rev, ca, ct, cb, nsig, tsig, zr, &s_zcnt, s_wb, acc);
+      if (compact) ok = cut_pass<T, false, true>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, acc);
+      else ok = cut_pass<T, false, false>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, acc);
     }
     if (!ok) return;
     if (bid == 0 && tid == 0 && pass < kMaxIt) s_tstream[pass] = globaltimer();
@@ -797,6 +814,9 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     fpop = (long long)P;
     const unsigned long long lo_i = P * bid / G, hi_i = P * (bid + 1) / G;
     const T fa = fin.a, fb = fin.b;
+    // (a, b] on keys: x > a <=> key(x) > key_le(a), x <= b <=> key(x) <= key_le(b), where a
+    // zero end takes the key of +0 (no NaN reaches the compacted regions)
+    const U k_lo = ukey(fa == T(0) ? T(0) : fa), k_hi = ukey(fb == T(0) ? T(0) : fb);
     const int warp = tid >> 5;
     while (s_known < W) {
       const int known = s_known;
@@ -835,7 +855,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
 #pragma unroll
           for (int j = 0; j < kFinU; ++j) {
             const U key = ukey(v[j]);
-            const bool inb = (v[j] > fa) && (v[j] <= fb);
+            const bool inb = (key > k_lo) && (key <= k_hi);
             const bool match = known == 0 || (U)(key >> (W - known)) == prefix;
             const unsigned int d = (inb && match) ? (unsigned int)(key >> sh) & dmask : kBins;
             const unsigned int act = __ballot_sync(0xffffffffu, d < kBins);

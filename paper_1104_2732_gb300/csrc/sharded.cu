@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) compact_kernel(const T* __restrict__ x, l
                                                       T* __restrict__ z, long long zcap,
                                                       unsigned long long* __restrict__ cnt) {
   using C = typename Ops<T>::C;
-  const C ca = CmpOf<T>::of(a), cb = CmpOf<T>::of(b);
+  const C ca = CmpOf<T>::le(a), cb = CmpOf<T>::le(b);
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
