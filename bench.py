@@ -255,6 +255,18 @@ def bench_segmented(gbs, ctx, torch, np, args):
     same = bool(torch.equal(out.view(torch.int32), outs.view(torch.int32)))
     sizes = np.diff(off)
     big = sizes > ctx.segmented_variant()["smem_cap"]
+    # CPU oracle (as it stands, 1 thread) on every 32nd segment, scaled to the batch
+    from oracle import select as osel
+    sample = range(0, S, 32)
+    t0 = time.perf_counter()
+    elems = 0
+    for s_ in sample:
+        seg = x_host[int(off[s_]):int(off[s_ + 1])]
+        osel.select_kth(seg, (seg.size + 1) // 2)
+        elems += seg.size
+    cpu_s = time.perf_counter() - t0
+    cpu = {"value": len(sample) / cpu_s, "unit": "selections/s", "gelem_s": elems / cpu_s / 1e9, "cores": 1,
+           "kind": "oracle", "sample": f"medians of {len(sample)} of the {S} segments (every 32nd)"}
     return {
         "workload": f"{S} float32 normal arrays, sizes log-uniform [1e3, 1e6], total {total} elements, medians",
         "metric": "selections/s", "value": S / (ms * 1e-3), "gelem_s": total / (ms * 1e-3) / 1e9,
@@ -264,6 +276,7 @@ def bench_segmented(gbs, ctx, torch, np, args):
         "mean_passes_large_segments": float(np.mean(np.array(passes)[big])) if big.any() else None,
         "bytes_read_per_batch": int(sum(p * n * 4 for p, n in zip(passes, sizes))),
         "achieved_gbs": sum(p * n * 4 for p, n in zip(passes, sizes)) / (ms * 1e-3) / 1e9,
+        "cpu_baseline": cpu,
     }
 
 
@@ -309,8 +322,10 @@ def bench_lms(gbs, ctx, torch, np, args):
     rng = np.random.default_rng(8)
     sample = rng.choice(C, 8, replace=False)
     err = {kk: [0.0, 0.0] for kk in forms}
-    for c in sample:
-        wl, wt = oreg.lms_lts(X, y, th[c:c + 1].T, k, h)
+    t0 = time.perf_counter()
+    oracle_vals = [oreg.lms_lts(X, y, th[c:c + 1].T, k, h) for c in sample]
+    cpu_s = time.perf_counter() - t0
+    for c, (wl, wt) in zip(sample, oracle_vals):
         for name, (l, t) in forms.items():
             err[name][0] = max(err[name][0], abs(l[c] / wl[0] - 1))
             err[name][1] = max(err[name][1], abs(t[c] / wt[0] - 1))
@@ -327,6 +342,8 @@ def bench_lms(gbs, ctx, torch, np, args):
         "residual_kernel": {"ms": res_ms, "bytes_written": C * n * 4,
                             "gbs": C * n * 4 / (res_ms * 1e-3) / 1e9,
                             "hbm_frac": C * n * 4 / (res_ms * 1e-3) / 1e9 / hbm, "peak_kind": f"{kind} hbm_gbs"},
+        "cpu_baseline": {"value": len(sample) / cpu_s, "unit": "candidates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"float64 LMS and LTS of {len(sample)} of the {C} candidates"},
         "fused_vs_materialised_max_rel_diff": {
             "lms": float(np.max(np.abs(forms["fused"][0] / forms["materialised"][0] - 1))),
             "lts": float(np.max(np.abs(forms["fused"][1] / forms["materialised"][1] - 1)))},
@@ -344,7 +361,7 @@ def bench_learned(gbs, ctx, torch, np, args, x_big=None):
         return {"unavailable": "no trained model"}
     ctx.load_bracket_model(model)
     flush = torch.empty(1 << 26, dtype=torch.float32, device="cuda")   # 256 MiB > L2
-    count = 200
+    count = 1000
     rng = np.random.default_rng(2 * 10 ** 6)
     buf = torch.empty(1 << 24, device="cuda")
     outs = torch.empty(2, device="cuda")

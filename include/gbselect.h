@@ -67,7 +67,9 @@ typedef struct {
     int32_t maxit;       /* cutting-plane iterations before compaction is forced; 0 = 64 */
     int32_t blocks_per_sm; /* CTAs per SM of the persistent kernel; 0 = 1 below 32 MiB of
                               input, else 2 (at most what fits) */
-    int32_t use_learned; /* 1 = start from the bracket proposed by the loaded model (if any) */
+    int32_t use_learned; /* 1 = start from the bracket proposed by the loaded model (if any);
+                            a proposed bracket that passes its count check and holds at most
+                            max(cap, n/8) elements goes straight to the finish */
     int32_t reserved[7];
 } gbs_config;
 

@@ -629,7 +629,9 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
             br.a = prop_a; br.b = prop_b; br.cle_a = pla; br.clt_b = plb_lt; br.cle_b = plb;
             br.first = 0; br.plain_start = 0;
             br.dF = ((double)(pla - k) + 0.5) * ((double)prop_b - (double)prop_a) + st.s_ab;
-            if (plb - pla <= A.cap)                // already compacted: straight to the finish
+            // already compacted in pass 0: straight to the finish when the bracket holds at
+            // most max(cap, n/8) elements (cheaper than the cutting-plane passes it saves)
+            if (plb - pla <= (A.cap > n / 8 ? A.cap : n / 8))
               br.phase = ((long long)st.c_reg == plb - pla) ? 2 : 4;
           } else if (vb) {                       // (m, b]: a falls back to the minimum
             br.b = prop_b; br.clt_b = plb_lt; br.cle_b = plb; br.plain_start = 0; br.dfv = 0;
