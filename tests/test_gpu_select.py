@@ -106,6 +106,29 @@ def test_cost_pass_parity(ctx, dtype):
         assert abs(e["dphi"] - osel.relative_cost(x, k, a, t)) <= tol + 1e-9 * abs(e["dphi"])
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_cost_pass_zero_thresholds_follow_ieee(ctx, dtype):
+    """Thresholds at -0 and +0 on data full of signed zeros: #(x < t), #(x <= t) and
+    #(x <= a) are the IEEE counts (-0 == +0), whatever the sign of the zero threshold
+    (float64 compares totalOrder keys, whose zero thresholds carry the IEEE rule)."""
+    rng = np.random.default_rng(35)
+    n = 100003
+    vals = np.array([-0.0, 0.0, -1.5, 2.5, -np.inf, np.inf, 1e-300 if dtype == np.float64 else 1e-38,
+                     -(1e-300 if dtype == np.float64 else 1e-38)], dtype=dtype)
+    x = vals[rng.integers(0, vals.size, n)]
+    xt = torch.from_numpy(x).cuda()
+    for a, t in ((-1.0, -0.0), (-1.0, 0.0), (-0.0, 1.0), (0.0, 1.0), (-2.0, 3.0)):
+        a, t = dtype(a), dtype(t)
+        e = ctx.cost_pass(xt, 1, float(a), float(t))
+        assert e["c_lt_t"] == int(np.count_nonzero(x < t)), (a, t)
+        assert e["c_le_t"] == int(np.count_nonzero(x <= t)), (a, t)
+        assert e["c_le_a"] == int(np.count_nonzero(x <= a)), (a, t)
+    for k in (1, n // 3, n // 2, (2 * n) // 3, n):
+        got = ctx.select_kth(xt, k).cpu().numpy()[0]
+        assert np.asarray(got).view(np.uint64 if dtype == np.float64 else np.uint32) == \
+            np.asarray(osel.select_kth(x, k)).view(np.uint64 if dtype == np.float64 else np.uint32)
+
+
 def test_cost_pass_rejects_bad_bracket(ctx, lib):
     x = torch.zeros(10, device="cuda")
     with pytest.raises(lib.GbsError):
