@@ -62,9 +62,11 @@ __device__ __forceinline__ void stream_chunks(const T* __restrict__ x, const Geo
 }
 
 // As stream_chunks, and every element with keep(element) is appended to `zr` (counter
-// *cnt in shared memory).  Per chunk, a warp-wide prefix sum places the warp's kept
-// elements in its shared-memory staging buffer `wb` (room for the warp's whole share of
-// a chunk), from where the warp copies them to `zr` with consecutive, coalesced stores.
+// *cnt in shared memory).  A lane writes its kept elements of a chunk to its own slots of
+// the warp's shared-memory buffer `wb` as soon as they are tested (slot j of lane L at
+// wb[L + 32 j]: no bank conflicts), so the loaded vectors are dead before the warp's
+// prefix sum; the warp then copies them to `zr` with consecutive stores, each output
+// index finding its lane by a binary search over the lanes' inclusive counts.
 template <typename T, typename Fn, typename Keep>
 __device__ __forceinline__ void stream_chunks_compact(const T* __restrict__ x, const Geometry<T>& g, bool rev,
                                                       Fn& f, Keep& keep, T* __restrict__ zr,
@@ -84,15 +86,16 @@ __device__ __forceinline__ void stream_chunks_compact(const T* __restrict__ x, c
 #pragma unroll
     for (int u = 0; u < kVPT; ++u)
       if ((long long)u * kThreads < lim) r[u] = load_stream(p + u * kThreads);
-    unsigned int mask = 0, k = 0;
+    unsigned int k = 0;
 #pragma unroll
     for (int u = 0; u < kVPT; ++u) {
       if ((long long)u * kThreads < lim) {
         Ops<T>::each(r[u], f);
 #pragma unroll
         for (int e = 0; e < kVec; ++e) {
-          const bool kk = keep(Ops<T>::get(r[u], e));
-          mask |= (kk ? 1u : 0u) << (u * kVec + e);
+          const T v = Ops<T>::get(r[u], e);
+          const bool kk = keep(v);
+          if (kk) wb[lane + 32 * k] = v;
           k += kk;
         }
       }
@@ -107,15 +110,19 @@ __device__ __forceinline__ void stream_chunks_compact(const T* __restrict__ x, c
     if (total) {
       unsigned int b0 = 0;
       if (lane == 31) b0 = atomicAdd(cnt, total);
-      unsigned int pos = incl - k;
-#pragma unroll
-      for (int u = 0; u < kVPT; ++u)
-#pragma unroll
-        for (int e = 0; e < kVec; ++e)
-          if (mask & (1u << (u * kVec + e))) wb[pos++] = Ops<T>::get(r[u], e);
       b0 = __shfl_sync(0xffffffffu, b0, 31);
       __syncwarp();
-      for (unsigned int i = lane; i < total; i += 32) zr[b0 + i] = wb[i];
+      for (unsigned int i0 = 0; i0 < total; i0 += 32) {
+        const unsigned int i = i0 + lane;
+        int L = 0;                       // lanes whose inclusive count is <= i
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const unsigned int v = __shfl_sync(0xffffffffu, incl, L + step - 1);
+          if (v <= i) L += step;
+        }
+        const unsigned int exL = __shfl_sync(0xffffffffu, incl, L) - __shfl_sync(0xffffffffu, k, L);
+        if (i < total) zr[b0 + i] = wb[L + 32 * (i - exL)];
+      }
       __syncwarp();
     }
   }
