@@ -269,41 +269,26 @@ __device__ __noinline__ bool stats_pass(const T* __restrict__ x, const Geometry<
 // Per-thread accumulators of the checks of a proposed bracket (a, b] in pass 0.
 struct ProposalAcc {
   unsigned int la, lblt;   // #(x <= a), #(x < b); #(x <= b) = #(x <= a) + #compacted
-  float sab;               // sum over a < x < b of (b - x), scaled
 };
 
-// Pass 0 with a proposed bracket: pass 0's extremes and non-finite counts, the counts at
-// a and b, the cost from a to b, and the elements of (a, b] compacted into this CTA's
-// region.  The sum of x is not formed: with a proposal, Phi(b) - Phi(a) comes from the
-// cost term, and a side that fails its check starts without it.
+// Pass 0 with a proposed bracket, the lean form: the NaN count, #(x <= a), #(x < b) and the
+// elements of (a, b] compacted into this CTA's region.  The extremes, the infinities and
+// the sum are needed only when an end of the proposal fails its check; the plain pass 0
+// then follows.
 template <typename T>
-__device__ __noinline__ bool stats_pass_learned(const T* __restrict__ x, const Geometry<T>& geo, float sig,
-                                                float x0s, typename Ops<T>::C ca,
-                                                typename Ops<T>::C cb_lt, typename Ops<T>::C cb_le,
-                                                float nsab, float bsab, T* __restrict__ zr, unsigned int* s_cnt,
+__device__ __noinline__ bool stats_pass_learned(const T* __restrict__ x, const Geometry<T>& geo,
+                                                typename Ops<T>::C ca, typename Ops<T>::C cb_lt,
+                                                typename Ops<T>::C cb_le, T* __restrict__ zr, unsigned int* s_cnt,
                                                 T* wb, StatsAcc<T>& out, ProposalAcc& pa) {
   using C = typename Ops<T>::C;
-  C mn = cmp_pos_inf<T>(), mx = cmp_neg_inf<T>();
-  unsigned int nnan = 0, nneg = 0, npos = 0, seen = 0, la = 0, lblt = 0;
-  float sab = 0.f;
+  unsigned int nnan = 0, la = 0, lblt = 0;
   auto f = [&](T v) {
-    ++seen;
+    nnan += Ops<T>::is_nan(v);
     const C cv = CmpOf<T>::of(v);
-    if (Ops<T>::is_finite(v)) {
-      mn = cv < mn ? cv : mn;
-      mx = cv > mx ? cv : mx;
-    } else {
-      nnan += Ops<T>::is_nan(v);
-      nneg += Ops<T>::is_neginf(v);
-      npos += Ops<T>::is_posinf(v);
-    }
-    const bool le_a = cv <= ca, lt_b = cv < cb_lt;
-    la += le_a;
-    lblt += lt_b;
-    const float d = fmaf(Ops<T>::img(v), nsab, bsab);
-    sab += (!le_a && lt_b && cv > ca) ? d : 0.f;
+    la += (cv <= ca);
+    lblt += (cv < cb_lt);
   };
-  auto keep = [&](T v) { const C cv = CmpOf<T>::of(v); return (cv > ca) & (cv <= cb_le); };
+  auto keep = [&](T v) { const C cv = CmpOf<T>::of(v); return !Ops<T>::is_nan(v) & (cv > ca) & (cv <= cb_le); };
   if ((long long)blockIdx.x * kThreads + threadIdx.x < geo.head + (geo.n - geo.tail0)) {
     auto fk = [&](T v) {
       f(v);
@@ -312,9 +297,9 @@ __device__ __noinline__ bool stats_pass_learned(const T* __restrict__ x, const G
     stream_edges(x, geo, fk);
   }
   stream_chunks_compact(x, geo, false, f, keep, zr, s_cnt, wb);
-  (void)sig; (void)x0s;
-  out.mn = mn; out.mx = mx; out.nnan = nnan; out.nneg = nneg; out.npos = npos; out.seen = seen; out.sum = 0.f;
-  pa.la = la; pa.lblt = lblt; pa.sab = sab;
+  out.mn = cmp_pos_inf<T>(); out.mx = cmp_neg_inf<T>();
+  out.nnan = nnan; out.nneg = 0; out.npos = 0; out.seen = nnan; out.sum = 0.f;
+  pa.la = la; pa.lblt = lblt;
   return true;
 }
 
@@ -437,128 +422,146 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
   }
 
   // ---------------- pass 0: finite extremes, sum, non-finite counts (Sec. 3, step 0) ----------------
-  {
-    const float sig = A.sigma_stats;
-    float x0 = 0.f;   // per-thread shift of the float32 sum
+  // With a proposed bracket, pass 0 is first the lean check of the proposal; the plain
+  // pass 0 follows only when an end fails its check (the same decision in every CTA).
+  bool lean = prop_ok;
+  __shared__ unsigned long long s_prop[4];   // #(x <= a), #(x < b), #(x <= b), #compacted
+  for (;;) {
     {
-      const long long gtid = (long long)bid * kThreads + tid;
-      const long long i0 = gtid < geo.head ? gtid : geo.head + gtid * Ops<T>::kVec;
-      if (i0 < n) {
-        const T e = A.x[i0];
-        if (Ops<T>::is_finite(e)) x0 = Ops<T>::img(e);
+      const float sig = A.sigma_stats;
+      float x0 = 0.f;   // per-thread shift of the float32 sum
+      {
+        const long long gtid = (long long)bid * kThreads + tid;
+        const long long i0 = gtid < geo.head ? gtid : geo.head + gtid * Ops<T>::kVec;
+        if (i0 < n) {
+          const T e = A.x[i0];
+          if (Ops<T>::is_finite(e)) x0 = Ops<T>::img(e);
+        }
       }
-    }
-    const float x0s = x0 * sig;
-    StatsAcc<T> sa;
-    ProposalAcc pa;
-    pa.la = pa.lblt = 0; pa.sab = 0.f;
-    float sig_ab = 1.f;
-    if (prop_ok) {
-      sig_ab = cost_scale((double)Ops<T>::img(prop_b) - (double)Ops<T>::img(prop_a), per_thread);
-      if (tid == 0) s_zcnt = 0;
-      __syncthreads();
-      if (!stats_pass_learned<T>(A.x, geo, sig, x0s, CmpOf<T>::le(prop_a), CmpOf<T>::lt(prop_b),
-                                 CmpOf<T>::le(prop_b), -sig_ab,
-                                 Ops<T>::img(prop_b) * sig_ab, A.z + region_start(bid, nch, G, Ops<T>::kVec),
-                                 &s_zcnt, s_wb, sa, pa))
-        return;
-    } else {
-      if (!stats_pass<T>(A.x, geo, sig, x0s, sa)) return;
-    }
-    C mn = sa.mn, mx = sa.mx;
-    const unsigned int nnan = sa.nnan, nneg = sa.nneg, npos = sa.npos, seen = sa.seen;
-    const float sum = sa.sum;
-    __shared__ C s_m[kWarps], s_M[kWarps];
+      const float x0s = x0 * sig;
+      StatsAcc<T> sa;
+      ProposalAcc pa;
+      pa.la = pa.lblt = 0;
+      if (lean) {
+        if (tid == 0) s_zcnt = 0;
+        __syncthreads();
+        if (!stats_pass_learned<T>(A.x, geo, CmpOf<T>::le(prop_a), CmpOf<T>::lt(prop_b), CmpOf<T>::le(prop_b),
+                                   A.z + region_start(bid, nch, G, Ops<T>::kVec), &s_zcnt, s_wb, sa, pa))
+          return;
+      } else {
+        if (!stats_pass<T>(A.x, geo, sig, x0s, sa)) return;
+      }
+      C mn = sa.mn, mx = sa.mx;
+      const unsigned int nnan = sa.nnan, nneg = sa.nneg, npos = sa.npos, seen = sa.seen;
+      const float sum = sa.sum;
+      __shared__ C s_m[kWarps], s_M[kWarps];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const C omn = __shfl_xor_sync(0xffffffffu, mn, o);
-      const C omx = __shfl_xor_sync(0xffffffffu, mx, o);
-      mn = omn < mn ? omn : mn;
-      mx = omx > mx ? omx : mx;
-    }
-    if (lane == 0) { s_m[tid >> 5] = mn; s_M[tid >> 5] = mx; }
-    const unsigned int nfin = seen - nnan - nneg - npos;
-    const unsigned long long b_nan = block_sum<unsigned long long>(nnan, s_u64);
-    const unsigned long long b_neg = block_sum<unsigned long long>(nneg, s_u64);
-    const unsigned long long b_pos = block_sum<unsigned long long>(npos, s_u64);
-    const unsigned long long b_fin = block_sum<unsigned long long>(nfin, s_u64);
-    const double own = (double)sum / (double)sig + (double)nfin * (double)x0;
-    const double b_sum = block_sum<double>(own, s_f64);
-    Sum6 p6;
-    p6.u[0] = pa.la; p6.u[1] = pa.lblt; p6.u[2] = 0; p6.u[3] = 0; p6.u[4] = 0; p6.d = (double)pa.sab;
-    if (prop_ok) {
-      __syncthreads();
-      p6.u[3] = tid == 0 ? s_zcnt : 0u;
-    }
-    const Sum6 b6 = prop_ok ? block_sum6(p6, s_sum6) : p6;
-    if (tid == 0) {
-      C bm = s_m[0], bM = s_M[0];
-      for (int w = 1; w < kWarps; ++w) {
-        bm = s_m[w] < bm ? s_m[w] : bm;
-        bM = s_M[w] > bM ? s_M[w] : bM;
+      for (int o = 16; o > 0; o >>= 1) {
+        const C omn = __shfl_xor_sync(0xffffffffu, mn, o);
+        const C omx = __shfl_xor_sync(0xffffffffu, mx, o);
+        mn = omn < mn ? omn : mn;
+        mx = omx > mx ? omx : mx;
       }
-      StatsPartial sp;
-      sp.n_nan = b_nan; sp.n_neginf = b_neg; sp.n_posinf = b_pos; sp.n_negzero = 0; sp.n_finite = b_fin;
-      sp.mn = (double)cmp_value(bm, T()); sp.mx = (double)cmp_value(bM, T());
-      sp.c_mn = 0; sp.c_mx = 0; sp.sum = b_sum;
-      sp.c_le_a = b6.u[0]; sp.c_lt_b = b6.u[1]; sp.c_le_b = b6.u[0] + b6.u[3]; sp.c_reg = b6.u[3];
-      sp.s_ab = b6.d / (double)sig_ab;
-      A.spart[bid] = sp;
+      if (lane == 0) { s_m[tid >> 5] = mn; s_M[tid >> 5] = mx; }
+      const unsigned int nfin = seen - nnan - nneg - npos;
+      const unsigned long long b_nan = block_sum<unsigned long long>(nnan, s_u64);
+      const unsigned long long b_neg = block_sum<unsigned long long>(nneg, s_u64);
+      const unsigned long long b_pos = block_sum<unsigned long long>(npos, s_u64);
+      const unsigned long long b_fin = block_sum<unsigned long long>(nfin, s_u64);
+      const double own = (double)sum / (double)sig + (double)nfin * (double)x0;
+      const double b_sum = block_sum<double>(own, s_f64);
+      Sum6 p6;
+      p6.u[0] = pa.la; p6.u[1] = pa.lblt; p6.u[2] = 0; p6.u[3] = 0; p6.u[4] = 0; p6.d = 0.0;
+      if (lean) {
+        __syncthreads();
+        p6.u[3] = tid == 0 ? s_zcnt : 0u;
+      }
+      const Sum6 b6 = lean ? block_sum6(p6, s_sum6) : p6;
+      if (tid == 0) {
+        C bm = s_m[0], bM = s_M[0];
+        for (int w = 1; w < kWarps; ++w) {
+          bm = s_m[w] < bm ? s_m[w] : bm;
+          bM = s_M[w] > bM ? s_M[w] : bM;
+        }
+        StatsPartial sp;
+        sp.n_nan = b_nan; sp.n_neginf = b_neg; sp.n_posinf = b_pos; sp.n_negzero = 0; sp.n_finite = b_fin;
+        sp.mn = (double)cmp_value(bm, T()); sp.mx = (double)cmp_value(bM, T());
+        sp.c_mn = 0; sp.c_mx = 0; sp.sum = b_sum;
+        sp.c_le_a = b6.u[0]; sp.c_lt_b = b6.u[1]; sp.c_le_b = b6.u[0] + b6.u[3]; sp.c_reg = b6.u[3];
+        sp.s_ab = 0.0;
+        A.spart[bid] = sp;
+      }
     }
-  }
-  if (!grid_sync(A.ctrl, G)) return;
-  stamp();
+    if (!grid_sync(A.ctrl, G)) return;
+    stamp();
 
-  // every CTA: reduce the G pass-0 partials in the same order (thread i takes partials
-  // i, i + kThreads, ...; then a fixed warp / block tree)
-  {
-    Sum6 v;
-    v.u[0] = v.u[1] = v.u[2] = v.u[3] = v.u[4] = 0;
-    v.d = 0.0;
-    double m = INFINITY, M = -INFINITY;
-    for (unsigned int i = tid; i < G; i += kThreads) {
-      const StatsPartial* p = &A.spart[i];
-      v.u[0] += __ldcg(&p->n_nan); v.u[1] += __ldcg(&p->n_neginf);
-      v.u[2] += __ldcg(&p->n_posinf); v.u[3] += __ldcg(&p->n_finite);
-      const double pm = __ldcg(&p->mn), pM = __ldcg(&p->mx);
-      m = pm < m ? pm : m;
-      M = pM > M ? pM : M;
-      v.d += __ldcg(&p->sum);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double om = __shfl_xor_sync(0xffffffffu, m, o), oM = __shfl_xor_sync(0xffffffffu, M, o);
-      m = om < m ? om : m;
-      M = oM > M ? oM : M;
-    }
-    __shared__ double s_mm[kWarps], s_MM[kWarps];
-    if (lane == 0) { s_mm[tid >> 5] = m; s_MM[tid >> 5] = M; }
-    const Sum6 r = block_sum6(v, s_sum6);   // its barriers also publish s_mm / s_MM
-    Sum6 w;
-    w.u[0] = w.u[1] = w.u[2] = w.u[3] = w.u[4] = 0;
-    w.d = 0.0;
-    if (prop_ok) {
+    // every CTA: reduce the G pass-0 partials in the same order (thread i takes partials
+    // i, i + kThreads, ...; then a fixed warp / block tree)
+    {
+      Sum6 v;
+      v.u[0] = v.u[1] = v.u[2] = v.u[3] = v.u[4] = 0;
+      v.d = 0.0;
+      double m = INFINITY, M = -INFINITY;
       for (unsigned int i = tid; i < G; i += kThreads) {
         const StatsPartial* p = &A.spart[i];
-        w.u[0] += __ldcg(&p->c_le_a); w.u[1] += __ldcg(&p->c_lt_b); w.u[2] += __ldcg(&p->c_le_b);
-        w.u[3] += __ldcg(&p->c_reg); w.d += __ldcg(&p->s_ab);
+        v.u[0] += __ldcg(&p->n_nan); v.u[1] += __ldcg(&p->n_neginf);
+        v.u[2] += __ldcg(&p->n_posinf); v.u[3] += __ldcg(&p->n_finite);
+        const double pm = __ldcg(&p->mn), pM = __ldcg(&p->mx);
+        m = pm < m ? pm : m;
+        M = pM > M ? pM : M;
+        v.d += __ldcg(&p->sum);
       }
-      w = block_sum6(w, s_sum6);
-    }
-    if (tid == 0) {
-      StatsPartial t;
-      t.n_nan = r.u[0]; t.n_neginf = r.u[1]; t.n_posinf = r.u[2]; t.n_finite = r.u[3];
-      t.n_negzero = 0; t.c_mn = t.c_mx = 0; t.sum = r.d;
-      t.c_le_a = w.u[0]; t.c_lt_b = w.u[1]; t.c_le_b = w.u[2]; t.c_reg = w.u[3]; t.s_ab = w.d;
-      t.mn = s_mm[0]; t.mx = s_MM[0];
-      for (int w = 1; w < kWarps; ++w) {
-        t.mn = s_mm[w] < t.mn ? s_mm[w] : t.mn;
-        t.mx = s_MM[w] > t.mx ? s_MM[w] : t.mx;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double om = __shfl_xor_sync(0xffffffffu, m, o), oM = __shfl_xor_sync(0xffffffffu, M, o);
+        m = om < m ? om : m;
+        M = oM > M ? oM : M;
       }
-      s_st = t;
+      __shared__ double s_mm[kWarps], s_MM[kWarps];
+      if (lane == 0) { s_mm[tid >> 5] = m; s_MM[tid >> 5] = M; }
+      const Sum6 r = block_sum6(v, s_sum6);   // its barriers also publish s_mm / s_MM
+      Sum6 w;
+      w.u[0] = w.u[1] = w.u[2] = w.u[3] = w.u[4] = 0;
+      w.d = 0.0;
+      if (lean) {
+        for (unsigned int i = tid; i < G; i += kThreads) {
+          const StatsPartial* p = &A.spart[i];
+          w.u[0] += __ldcg(&p->c_le_a); w.u[1] += __ldcg(&p->c_lt_b); w.u[2] += __ldcg(&p->c_le_b);
+          w.u[3] += __ldcg(&p->c_reg);
+        }
+        w = block_sum6(w, s_sum6);
+      }
+      if (tid == 0) {
+        StatsPartial t;
+        t.n_nan = r.u[0]; t.n_neginf = r.u[1]; t.n_posinf = r.u[2]; t.n_finite = r.u[3];
+        t.n_negzero = 0; t.c_mn = t.c_mx = 0; t.sum = r.d;
+        t.c_le_a = w.u[0]; t.c_lt_b = w.u[1]; t.c_le_b = w.u[2]; t.c_reg = w.u[3]; t.s_ab = 0.0;
+        t.mn = s_mm[0]; t.mx = s_MM[0];
+        for (int w = 1; w < kWarps; ++w) {
+          t.mn = s_mm[w] < t.mn ? s_mm[w] : t.mn;
+          t.mx = s_MM[w] > t.mx ? s_MM[w] : t.mx;
+        }
+        if (lean) {
+          s_prop[0] = t.c_le_a; s_prop[1] = t.c_lt_b; s_prop[2] = t.c_le_b; s_prop[3] = t.c_reg;
+        } else if (prop_ok) {   // the plain pass after a failed end: keep the proposal's counts
+          t.c_le_a = s_prop[0]; t.c_lt_b = s_prop[1]; t.c_le_b = s_prop[2]; t.c_reg = s_prop[3];
+        }
+        s_st = t;
+      }
     }
+    __syncthreads();
+    if (lean) {
+      const bool ok_a = (long long)s_st.c_le_a < k, ok_b = k <= (long long)s_st.c_le_b;
+      if (s_st.n_nan == 0 && !(ok_a && ok_b)) {   // an end failed: the plain pass 0
+        lean = false;
+        if (!grid_sync(A.ctrl, G)) return;       // every CTA has read the partials
+        continue;
+      }
+    }
+    break;
   }
-  __syncthreads();
+  // both ends of a proposal checked (the lean pass 0 only): the extremes are not known
+  const bool prop_both = prop_ok && lean && s_st.n_nan == 0;
   const StatsPartial& st = s_st;     // read from shared memory where needed
   const long long nneg = (long long)st.n_neginf, npos = (long long)st.n_posinf;
 
@@ -592,6 +595,20 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     if (st.n_nan > 0) {
       br.phase = 3;
       br.result = T(NAN);
+    } else if (prop_both) {
+      // the proposed bracket (a, b] passed its count check in the lean pass 0
+      const long long pla = (long long)st.c_le_a, plb_lt = (long long)st.c_lt_b, plb = (long long)st.c_le_b;
+      br.learned = 1;
+      if (plb_lt < k) {                        // x_(k) is b itself
+        br.phase = 1; br.result = prop_b; br.how = GBS_HOW_HIT; br.clt_res = plb_lt;
+      } else {
+        br.a = prop_a; br.b = prop_b; br.cle_a = pla; br.clt_b = plb_lt; br.cle_b = plb;
+        br.first = 0; br.plain_start = 0; br.dfv = 0;   // Phi(b) - Phi(a) unknown: bisect first
+        // already compacted in pass 0: straight to the finish when the bracket holds at
+        // most max(cap, n/8) elements (cheaper than the cutting-plane passes it saves)
+        if (plb - pla <= (A.cap > n / 8 ? A.cap : n / 8))
+          br.phase = ((long long)st.c_reg == plb - pla) ? 2 : 4;
+      }
     } else if (k <= nneg) {
       br.phase = 1; br.result = T(-INFINITY); br.how = GBS_HOW_NEGINF;
     } else if (k > n - npos) {
@@ -626,21 +643,12 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
           br.dF = gL * ((double)M - (double)m) + (double)(br.clt_b - br.cle_a) * (double)M - inner;
         }
         if (prop_ok) {
-          // the proposed bracket (a, b] was checked by counts in pass 0
+          // an end of the proposed bracket failed its check in the lean pass 0; the other
+          // end still narrows the start
           const long long pla = (long long)st.c_le_a, plb_lt = (long long)st.c_lt_b, plb = (long long)st.c_le_b;
           const bool va = pla < k, vb = k <= plb;
-          br.learned = (va && vb) ? 1 : 2;
-          if (va && vb && plb_lt < k) {          // x_(k) is b itself
-            br.phase = 1; br.result = prop_b; br.how = GBS_HOW_HIT; br.clt_res = plb_lt;
-          } else if (va && vb) {
-            br.a = prop_a; br.b = prop_b; br.cle_a = pla; br.clt_b = plb_lt; br.cle_b = plb;
-            br.first = 0; br.plain_start = 0;
-            br.dF = ((double)(pla - k) + 0.5) * ((double)prop_b - (double)prop_a) + st.s_ab;
-            // already compacted in pass 0: straight to the finish when the bracket holds at
-            // most max(cap, n/8) elements (cheaper than the cutting-plane passes it saves)
-            if (plb - pla <= (A.cap > n / 8 ? A.cap : n / 8))
-              br.phase = ((long long)st.c_reg == plb - pla) ? 2 : 4;
-          } else if (vb) {                       // (m, b]: a falls back to the minimum
+          br.learned = 2;
+          if (vb) {                              // (m, b]: a falls back to the minimum
             br.b = prop_b; br.clt_b = plb_lt; br.cle_b = plb; br.plain_start = 0; br.dfv = 0;
           } else if (va) {                       // (a, M]: b falls back to the maximum
             br.a = prop_a; br.cle_a = pla; br.plain_start = 0; br.dfv = 0;
