@@ -273,6 +273,66 @@ __device__ __forceinline__ void below_sums(const float* buf, int m, float q, flo
   }
 }
 
+// The streaming passes of a large segment, kept out of line so that their registers are
+// allocated apart from the kernel's control (the whole kernel runs at 64 registers).
+struct SegStatsAcc {
+  float mn, mx, sum;
+  unsigned int nnan, nneg, npos, nnz, seen;
+};
+template <int B>
+__device__ __noinline__ void seg_stats_pass(const float* __restrict__ xs, const Geometry<float>& g, float sig0,
+                                            float x0s, SegStatsAcc& out) {
+  float mn = INFINITY, mx = -INFINITY, sum = 0.f;
+  unsigned int nnan = 0, nneg = 0, npos = 0, nnz = 0, seen = 0;
+  auto f = [&](float v) {
+    ++seen;
+    if (fabsf(v) <= FLT_MAX) {
+      mn = fminf(mn, v);
+      mx = fmaxf(mx, v);
+      sum += fmaf(v, sig0, -x0s);
+      nnz += (__float_as_uint(v) == 0x80000000u);
+    } else {
+      nnan += (v != v);
+      nneg += (v == -INFINITY);
+      npos += (v == INFINITY);
+    }
+  };
+  cta_stream<B>(xs, g, f);
+  out.mn = mn; out.mx = mx; out.sum = sum;
+  out.nnan = nnan; out.nneg = nneg; out.npos = npos; out.nnz = nnz; out.seen = seen;
+}
+
+struct SegPassAcc {
+  unsigned int lt, le, xa, xb;
+  float S, sle;
+};
+// One cutting-plane pass over a segment at t (Algorithm 1, step 1.2); FIRST also counts at
+// the extremes, COMPACT appends (a, b] to zb, SUMLE sums the elements at or below a.
+template <int B, bool FIRST, bool COMPACT, bool SUMLE>
+__device__ __noinline__ void seg_cut_pass(const float* __restrict__ xs, const Geometry<float>& g, float ca, float ct,
+                                          float cb, float nsig, float tsig, float* zb, unsigned int* cnt,
+                                          SegPassAcc& acc) {
+  unsigned int lt = 0, le = 0, xa = 0, xb = 0;
+  float S = 0.f, sle = 0.f;
+  auto f = [&](float v) {
+    core(v, ca, ct, nsig, tsig, lt, le, S);
+    if (FIRST) {
+      xa += (v <= ca);
+      xb += (v < cb);
+    }
+    if (SUMLE) {
+      if (v <= ca) sle += v;
+    }
+  };
+  if (COMPACT) {
+    auto keep = [&](float v) { return (v > ca) & (v <= cb); };
+    cta_stream_compact<B>(xs, g, f, keep, zb, cnt);
+  } else {
+    cta_stream<B>(xs, g, f);
+  }
+  acc.lt = lt; acc.le = le; acc.xa = xa; acc.xb = xb; acc.S = S; acc.sle = sle;
+}
+
 template <int B, int CAP, bool LTS>
 __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
   extern __shared__ __align__(16) float zb[];   // CAP floats
@@ -359,22 +419,11 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
       float x0 = 0.f;
       if (tid < n && Ops<float>::is_finite(xs[tid])) x0 = xs[tid];
       const float x0s = x0 * sig0;
-      float mn = INFINITY, mx = -INFINITY, sum = 0.f;
-      unsigned int nnan = 0, nneg = 0, npos = 0, nnz = 0, seen = 0;
-      auto f = [&](float v) {
-        ++seen;
-        if (fabsf(v) <= FLT_MAX) {
-          mn = fminf(mn, v);
-          mx = fmaxf(mx, v);
-          sum += fmaf(v, sig0, -x0s);
-          nnz += (__float_as_uint(v) == 0x80000000u);
-        } else {
-          nnan += (v != v);
-          nneg += (v == -INFINITY);
-          npos += (v == INFINITY);
-        }
-      };
-      cta_stream<B>(xs, g, f);
+      SegStatsAcc sa;
+      seg_stats_pass<B>(xs, g, sig0, x0s, sa);
+      float mn = sa.mn, mx = sa.mx;
+      const float sum = sa.sum;
+      const unsigned int nnan = sa.nnan, nneg = sa.nneg, npos = sa.npos, nnz = sa.nnz, seen = sa.seen;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
@@ -443,39 +492,24 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
       if (sh.phase != 0) break;
       const float ca = sh.a, ct = sh.t, cb = sh.b, nsig = -sh.sig, tsig = sh.t * sh.sig;
       const int first = sh.first, compact = sh.compact;
-      unsigned int lt = 0, le = 0, xa = 0, xb = 0;
-      float S = 0.f, sle = 0.f;
-      auto fcore = [&](float v) { core(v, ca, ct, nsig, tsig, lt, le, S); };
-      auto ffirst = [&](float v) {
-        core(v, ca, ct, nsig, tsig, lt, le, S);
-        xa += (v <= ca);
-        xb += (v < cb);
-      };
-      // trimmed-sum mode: the compacting pass also sums the elements at or below a
-      auto fcore_s = [&](float v) {
-        core(v, ca, ct, nsig, tsig, lt, le, S);
-        if (v <= ca) sle += v;
-      };
-      auto ffirst_s = [&](float v) {
-        ffirst(v);
-        if (v <= ca) sle += v;
-      };
-      auto keep = [&](float v) { return (v > ca) & (v <= cb); };
+      SegPassAcc pacc;
       if (first) {
         if (compact) {
-          if (LTS) cta_stream_compact<B>(xs, g, ffirst_s, keep, zb, &sh.zcnt);
-          else cta_stream_compact<B>(xs, g, ffirst, keep, zb, &sh.zcnt);
+          if (LTS) seg_cut_pass<B, true, true, true>(xs, g, ca, ct, cb, nsig, tsig, zb, &sh.zcnt, pacc);
+          else seg_cut_pass<B, true, true, false>(xs, g, ca, ct, cb, nsig, tsig, zb, &sh.zcnt, pacc);
         } else {
-          cta_stream<B>(xs, g, ffirst);
+          seg_cut_pass<B, true, false, false>(xs, g, ca, ct, cb, nsig, tsig, zb, &sh.zcnt, pacc);
         }
       } else {
         if (compact) {
-          if (LTS) cta_stream_compact<B>(xs, g, fcore_s, keep, zb, &sh.zcnt);
-          else cta_stream_compact<B>(xs, g, fcore, keep, zb, &sh.zcnt);
+          if (LTS) seg_cut_pass<B, false, true, true>(xs, g, ca, ct, cb, nsig, tsig, zb, &sh.zcnt, pacc);
+          else seg_cut_pass<B, false, true, false>(xs, g, ca, ct, cb, nsig, tsig, zb, &sh.zcnt, pacc);
         } else {
-          cta_stream<B>(xs, g, fcore);
+          seg_cut_pass<B, false, false, false>(xs, g, ca, ct, cb, nsig, tsig, zb, &sh.zcnt, pacc);
         }
       }
+      const unsigned int lt = pacc.lt, le = pacc.le, xa = pacc.xa, xb = pacc.xb;
+      const float S = pacc.S, sle = pacc.sle;
       Sum6 v6;
       v6.u[0] = lt; v6.u[1] = le; v6.u[2] = xa; v6.u[3] = xb; v6.u[4] = 0; v6.d = (double)S;
       const Sum6 r6 = cta_sum6<B>(v6, sh.sum6);   // also orders every append before the reads below
