@@ -34,31 +34,38 @@ __device__ __forceinline__ void stream_edges(const T* __restrict__ x, const Geom
 // with 128-bit streaming loads, all kVPT of them in flight before any is used.
 constexpr int kVPT = (int)(kChunkVecs / kThreads);
 
+// Calls f on this thread's elements of chunk c (vectors threadIdx.x + u*kThreads); only
+// the last chunk of the body (c == last) can be partial.  32-bit chunk indices keep the
+// loop's registers low (no spills in the passes at 64 registers a thread).
+template <typename T, typename Fn>
+__device__ __forceinline__ void stream_chunk(const typename Ops<T>::V* __restrict__ xv, unsigned int c,
+                                             unsigned int last, long long nv, Fn& f) {
+  using V = typename Ops<T>::V;
+  const V* p = xv + (long long)c * kChunkVecs + threadIdx.x;
+  if (c != last) {
+    V r[kVPT];
+#pragma unroll
+    for (int u = 0; u < kVPT; ++u) r[u] = load_stream(p + u * kThreads);
+#pragma unroll
+    for (int u = 0; u < kVPT; ++u) Ops<T>::each(r[u], f);
+  } else {
+    const long long lim = nv - (long long)c * kChunkVecs - threadIdx.x;   // vectors left from p on
+    for (int u = 0; u < kVPT; ++u)
+      if ((long long)u * kThreads < lim) {
+        const V r = load_stream(p + u * kThreads);
+        Ops<T>::each(r, f);
+      }
+  }
+}
+
 template <typename T, typename Fn>
 __device__ __forceinline__ void stream_chunks(const T* __restrict__ x, const Geometry<T>& g, bool rev, Fn& f) {
   using V = typename Ops<T>::V;
   const V* xv = reinterpret_cast<const V*>(x + g.head);
-  const long long G = gridDim.x, bid = blockIdx.x;
-  const long long nch = chunk_count(g.nv);
-  const long long my = bid < nch ? (nch - 1 - bid) / G + 1 : 0;
-  for (long long j = 0; j < my; ++j) {
-    const long long c = bid + (rev ? my - 1 - j : j) * G;
-    const V* p = xv + c * kChunkVecs + threadIdx.x;
-    const long long lim = g.nv - c * kChunkVecs - threadIdx.x;   // vectors left from p on
-    if (lim > (long long)(kVPT - 1) * kThreads) {
-      V r[kVPT];
-#pragma unroll
-      for (int u = 0; u < kVPT; ++u) r[u] = load_stream(p + u * kThreads);
-#pragma unroll
-      for (int u = 0; u < kVPT; ++u) Ops<T>::each(r[u], f);
-    } else {
-      for (int u = 0; u < kVPT; ++u)
-        if ((long long)u * kThreads < lim) {
-          const V r = load_stream(p + u * kThreads);
-          Ops<T>::each(r, f);
-        }
-    }
-  }
+  const unsigned int G = gridDim.x, bid = blockIdx.x;
+  const unsigned int nch = (unsigned int)chunk_count(g.nv);
+  const unsigned int my = bid < nch ? (nch - 1 - bid) / G + 1 : 0;
+  for (unsigned int j = 0; j < my; ++j) stream_chunk<T>(xv, bid + (rev ? my - 1 - j : j) * G, nch - 1, g.nv, f);
 }
 
 // As stream_chunks, and every element with keep(element) is appended to `zr` (counter
@@ -75,13 +82,13 @@ __device__ __forceinline__ void stream_chunks_compact(const T* __restrict__ x, c
   constexpr int kVec = Ops<T>::kVec;
   const int lane = threadIdx.x & 31;
   const V* xv = reinterpret_cast<const V*>(x + g.head);
-  const long long G = gridDim.x, bid = blockIdx.x;
-  const long long nch = chunk_count(g.nv);
-  const long long my = bid < nch ? (nch - 1 - bid) / G + 1 : 0;
-  for (long long j = 0; j < my; ++j) {
-    const long long c = bid + (rev ? my - 1 - j : j) * G;
-    const V* p = xv + c * kChunkVecs + threadIdx.x;
-    const long long lim = g.nv - c * kChunkVecs - threadIdx.x;
+  const unsigned int G = gridDim.x, bid = blockIdx.x;
+  const unsigned int nch = (unsigned int)chunk_count(g.nv);
+  const unsigned int my = bid < nch ? (nch - 1 - bid) / G + 1 : 0;
+  for (unsigned int j = 0; j < my; ++j) {
+    const unsigned int c = bid + (rev ? my - 1 - j : j) * G;
+    const V* p = xv + (long long)c * kChunkVecs + threadIdx.x;
+    const long long lim = g.nv - (long long)c * kChunkVecs - threadIdx.x;
     V r[kVPT];
 #pragma unroll
     for (int u = 0; u < kVPT; ++u)
