@@ -291,11 +291,11 @@ gbs_status gbs_lms_lts_f32(gbs_ctx* c, const float* X, const float* y, int64_t n
   if (st != GBS_OK) return st;
   if (batched) {
     // trimmed-sum mode for rank h (LTS and q), the LMS rank k from the same bracket
-    st = gbs_internal_ensure(c, (size_t)C * 2 * sizeof(int));
-    if (st != GBS_OK) return st;
     gbs::SegLaunch L;
+    st = gbs::seg_attach_workspace(c, C, &L);
+    if (st != GBS_OK) return st;
     L.x = S; L.off = off; L.S = C; L.kk = nullptr; L.out = q;
-    L.order = static_cast<int*>(c->z); L.seg_passes = static_cast<int*>(c->z) + C; L.ctrl = c->ctrl;
+    L.ctrl = c->ctrl;
     L.mask = nullptr; L.kk2 = nullptr; L.out2 = lms_out; L.outsum = lts_out; L.flags = flags;
     L.k_const = h_lts; L.k2_const = k_lms;
     st = gbs::seg_launch(c, L, c->seg_variant, strm);

@@ -727,7 +727,7 @@ extern "C" gbs_status gbs_lms_lts_fused_f32(gbs_ctx* c, const float* X, const fl
     c->fused_buf = ptr;
     c->fused_bytes = bytes;
   }
-  gbs_status st = gbs_internal_ensure(c, (size_t)C * 2 * sizeof(int));
+  gbs_status st = gbs_internal_ensure(c, seg_workspace_bytes(C));
   if (st != GBS_OK) return st;
   char* b = static_cast<char*>(c->fused_buf);
   FusedArgs A;
@@ -819,8 +819,9 @@ extern "C" gbs_status gbs_lms_lts_fused_f32(gbs_ctx* c, const float* X, const fl
   fused_gather_kernel<<<C, 256, 0, strm>>>(A.zbuf, off, C, zcat);
   if ((st = check()) != GBS_OK) return st;
   SegLaunch L;
+  if ((st = seg_attach_workspace(c, C, &L)) != GBS_OK) return st;   // already large enough: no reallocation
   L.x = zcat; L.off = off; L.S = C; L.kk = P.kk; L.out = qbuf;
-  L.order = static_cast<int*>(c->z); L.seg_passes = static_cast<int*>(c->z) + C; L.ctrl = c->ctrl;
+  L.ctrl = c->ctrl;
   L.mask = P.mask; L.kk2 = P.kk2; L.out2 = lms_out; L.outsum = lts_out; L.flags = flags;
   L.k_const = 0; L.k2_const = 0;
   if ((st = seg_launch(c, L, kFVariant, strm)) != GBS_OK) return st;

@@ -6,8 +6,10 @@
 // is loaded once and radix-selected there.  A larger one runs the cutting plane of
 // Algorithm 1 (Sec. 3) with CTA-wide reductions: pass 0 (extremes, sum), then one fused
 // cost + count pass per iterate; the pass that sees a bracket small enough for shared
-// memory compacts it there and the answer is radix-selected inside it (the hybrid of
-// Sec. 3).  No CTA waits on another, so the launch needs no grid-wide barrier and the
+// memory compacts it there, or one of at most n/16 elements into the CTA's own
+// device-memory region, and the answer is radix-selected inside it (the hybrid of
+// Sec. 3; from device memory the rounds move to shared memory once the chosen digit's
+// elements fit there).  No CTA waits on another, so the launch needs no grid-wide barrier and the
 // whole call (schedule + kernel) can be captured in a CUDA graph.
 #include <algorithm>
 #include <cfloat>
@@ -24,6 +26,7 @@ namespace gbs {
 namespace {
 
 constexpr int kSchedBuckets = 64;
+constexpr long long kSegGlobalDiv = 16;   // device-memory compaction once pop <= n / 16
 
 // Buckets segment ids by floor(log2(size)), largest bucket first; also checks offsets.
 __global__ void seg_schedule_kernel(const long long* __restrict__ off, int S, int* __restrict__ order,
@@ -105,21 +108,29 @@ __device__ __forceinline__ void cta_stream(const float* __restrict__ xs, const G
   }
 }
 
-// As cta_stream, and appends every element with keep(element) to zb (shared memory,
-// counter *cnt).  Warp-uniform loop for the per-warp prefix sum.
+// As cta_stream, and appends every element with keep(element) to zb (shared memory or
+// this CTA's device-memory region, counter *cnt; appends past zcap are counted, not
+// written, so the caller's count check catches them).  Warp-uniform loop for the
+// per-warp prefix sum.
 template <int B, typename Fn, typename Keep>
 __device__ __forceinline__ void cta_stream_compact(const float* __restrict__ xs, const Geometry<float>& g, Fn& f,
-                                                   Keep& keep, float* zb, unsigned int* cnt) {
+                                                   Keep& keep, float* zb, unsigned int zcap, unsigned int* cnt) {
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid < g.head) {
     const float e = xs[tid];
     f(e);
-    if (keep(e)) zb[atomicAdd(cnt, 1u)] = e;
+    if (keep(e)) {
+      const unsigned int q = atomicAdd(cnt, 1u);
+      if (q < zcap) zb[q] = e;
+    }
   }
   if (tid < g.n - g.tail0) {
     const float e = xs[g.tail0 + tid];
     f(e);
-    if (keep(e)) zb[atomicAdd(cnt, 1u)] = e;
+    if (keep(e)) {
+      const unsigned int q = atomicAdd(cnt, 1u);
+      if (q < zcap) zb[q] = e;
+    }
   }
   const float4* xv = reinterpret_cast<const float4*>(xs + g.head);
   for (long long wb = tid - lane; wb < g.nv; wb += 4 * B) {
@@ -155,19 +166,95 @@ __device__ __forceinline__ void cta_stream_compact(const float* __restrict__ xs,
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-          if (mask & (1u << (u * 4 + e))) zb[pos++] = Ops<float>::get(r[u], e);
+          if (mask & (1u << (u * 4 + e))) {
+            if (pos < zcap) zb[pos] = Ops<float>::get(r[u], e);
+            ++pos;
+          }
     }
   }
 }
 
-// Radix select in shared memory: the rank-th (1-based) smallest, in totalOrder, of the
-// elements of zb[0, m) that lie in (a, b] (all of them when !filter).  Returns the
-// element's key.  8-bit digits from the highest bit where the bracket's keys differ;
-// equal digits within a warp are merged before the shared-memory atomic.
+// State of an in-CTA radix select (shared memory).
+struct RadixState {
+  unsigned int hist[256];
+  uint32_t prefix;          // the key's known leading bits
+  int known;                // how many
+  unsigned long long rank;  // rank among the elements with that prefix (0 flags an inconsistency)
+  unsigned int bucket;      // elements in the digit chosen last
+  unsigned int cnt;         // append counter of the gather
+};
+
+constexpr int kRadixU = 4;   // loads in flight per thread in the radix sweeps
+
+// Whether element i of buf[0, m) (value v) takes part in a round: in (a, b] when filtering,
+// and its key starts with the known prefix.
+__device__ __forceinline__ bool radix_takes(int i, int m, float v, uint32_t key, bool filter, float a, float b,
+                                            int known, uint32_t prefix) {
+  return i < m && (!filter || ((v > a) && (v <= b))) && (known == 0 || (key >> (32 - known)) == prefix);
+}
+
+// Histogram of the next digit (bits [sh, sh + 8) of the key) over the elements of buf that
+// take part; a warp's lanes with equal digits add once.
 template <int B>
-__device__ uint32_t smem_radix_select(const float* zb, int m, unsigned long long rank, bool filter, float a,
-                                      float b, unsigned int* hist /* [256] */, uint32_t* s_prefix,
-                                      int* s_known, unsigned long long* s_rank) {
+__device__ __forceinline__ void radix_hist(const float* buf, int m, bool filter, float a, float b, int known,
+                                           uint32_t prefix, int sh, unsigned int dmask, unsigned int* hist) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int base = warp * 32; base < m; base += B * kRadixU) {
+    float v[kRadixU];
+#pragma unroll
+    for (int u = 0; u < kRadixU; ++u) {
+      const int i = base + u * B + lane;
+      v[u] = i < m ? buf[i] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kRadixU; ++u) {
+      const int i = base + u * B + lane;
+      const uint32_t key = ukey(v[u]);
+      const unsigned int d =
+          radix_takes(i, m, v[u], key, filter, a, b, known, prefix) ? (key >> sh) & dmask : 256u;
+      const unsigned int same = __match_any_sync(0xffffffffu, d);
+      if (d < 256 && lane == __ffs(same) - 1) atomicAdd(&hist[d], (unsigned int)__popc(same));
+    }
+  }
+}
+
+// Appends the elements of buf that take part to zs (counter *cnt; any order; at most cap
+// are written).
+template <int B>
+__device__ __forceinline__ void radix_gather(const float* buf, int m, bool filter, float a, float b, int known,
+                                             uint32_t prefix, float* zs, unsigned int cap, unsigned int* cnt) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int base = warp * 32; base < m; base += B * kRadixU) {
+    float v[kRadixU];
+#pragma unroll
+    for (int u = 0; u < kRadixU; ++u) {
+      const int i = base + u * B + lane;
+      v[u] = i < m ? buf[i] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kRadixU; ++u) {
+      const int i = base + u * B + lane;
+      const bool t = radix_takes(i, m, v[u], ukey(v[u]), filter, a, b, known, prefix);
+      const unsigned int bal = __ballot_sync(0xffffffffu, t);
+      if (bal) {
+        unsigned int b0 = 0;
+        if (lane == 0) b0 = atomicAdd(cnt, (unsigned int)__popc(bal));
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+        const unsigned int pos = b0 + __popc(bal & ((1u << lane) - 1u));
+        if (t && pos < cap) zs[pos] = v[u];
+      }
+    }
+  }
+}
+
+// Radix select inside the CTA: the rank-th (1-based) smallest, in totalOrder, of the
+// elements of buf[0, m) that lie in (a, b] (all of them when !filter).  Returns the
+// element's key.  8-bit digits from the highest bit where the bracket's keys differ.  When
+// buf is in device memory, zs (shared memory, cap elements, else nullptr) takes the
+// elements of the chosen digit once they fit, and the later rounds run there.
+template <int B>
+__device__ uint32_t radix_select(const float* buf, int m, unsigned long long rank, bool filter, float a, float b,
+                                 float* zs, int cap, RadixState& st) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     int known = 0;
@@ -178,39 +265,29 @@ __device__ uint32_t smem_radix_select(const float* zb, int m, unsigned long long
       known = diff == 0 ? 32 : __clz(diff);
       prefix = known == 0 ? 0u : (known == 32 ? hi : (hi >> (32 - known)));
     }
-    *s_known = known;
-    *s_prefix = prefix;
-    *s_rank = rank;
+    st.known = known;
+    st.prefix = prefix;
+    st.rank = rank;
   }
   __syncthreads();
-  while (*s_known < 32) {
-    const int known = *s_known;
-    const uint32_t prefix = *s_prefix;
+  const float* cur = buf;
+  int mc = m;
+  while (st.known < 32) {
+    const int known = st.known;
+    const uint32_t prefix = st.prefix;
     const int nbits = (32 - known) < 8 ? (32 - known) : 8;
     const int sh = 32 - known - nbits;
     const unsigned int dmask = (1u << nbits) - 1u;
-    for (int i = tid; i < 256; i += B) hist[i] = 0;
+    for (int i = tid; i < 256; i += B) st.hist[i] = 0;
     __syncthreads();
-    for (int base = warp * 32; base < m; base += B) {
-      const int i = base + lane;
-      unsigned int d = 256;
-      if (i < m) {
-        const float v = zb[i];
-        const uint32_t key = ukey(v);
-        const bool inb = !filter || ((v > a) && (v <= b));
-        const bool match = known == 0 || (key >> (32 - known)) == prefix;
-        if (inb && match) d = (key >> sh) & dmask;
-      }
-      const unsigned int same = __match_any_sync(0xffffffffu, d);
-      if (d < 256 && lane == __ffs(same) - 1) atomicAdd(&hist[d], (unsigned int)__popc(same));
-    }
+    radix_hist<B>(cur, mc, filter, a, b, known, prefix, sh, dmask, st.hist);
     __syncthreads();
     if (warp == 0) {
       unsigned int h[8];
       unsigned int local = 0;
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        h[j] = hist[lane * 8 + j];
+        h[j] = st.hist[lane * 8 + j];
         local += h[j];
       }
       unsigned long long incl = local;
@@ -219,40 +296,47 @@ __device__ uint32_t smem_radix_select(const float* zb, int m, unsigned long long
         const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
       }
-      const unsigned long long want = *s_rank;
+      const unsigned long long want = st.rank;
       const unsigned long long excl = incl - local;
       const bool mine = excl < want && want <= incl;
       const unsigned int who = __ballot_sync(0xffffffffu, mine);
       if (mine) {
         unsigned long long c = excl;
         int d = 0;
+        unsigned int bk = 0;
         for (int j = 0; j < 8; ++j) {
-          if (c + h[j] >= want) { d = lane * 8 + j; break; }
+          if (c + h[j] >= want) { d = lane * 8 + j; bk = h[j]; break; }
           c += h[j];
         }
-        *s_rank = want - c;
-        *s_prefix = (prefix << nbits) | (uint32_t)d;
-        *s_known = known + nbits;
+        st.rank = want - c;
+        st.prefix = (prefix << nbits) | (uint32_t)d;
+        st.known = known + nbits;
+        st.bucket = bk;
+        st.cnt = 0;
       }
       if (who == 0 && lane == 0) {
-        *s_known = 32;
-        *s_prefix = 0;
-        *s_rank = 0;   // flags an inconsistency to the caller
+        st.known = 32;
+        st.prefix = 0;
+        st.rank = 0;   // flags an inconsistency to the caller
+        st.bucket = 0xffffffffu;
       }
     }
     __syncthreads();
+    if (zs != nullptr && cur == buf && st.known < 32 && st.bucket <= (unsigned int)cap) {
+      radix_gather<B>(buf, m, filter, a, b, st.known, st.prefix, zs, (unsigned int)cap, &st.cnt);
+      __syncthreads();
+      cur = zs;
+      mc = (int)min(st.cnt, (unsigned int)cap);   // equal to the bucket's count
+    }
   }
-  return *s_prefix;
+  return st.prefix;
 }
 
 struct SegShared {
   Sum6 sum6[33];
   float mn[32], mx[32];
-  unsigned int hist[256];
+  RadixState rx;
   unsigned int zcnt;
-  uint32_t prefix;
-  int known;
-  unsigned long long rank;
   int seg;
   // bracket state (thread 0 writes, all read)
   float a, b, t, m, M, sig, result;
@@ -261,13 +345,23 @@ struct SegShared {
   float a0, b0;       // that bracket
   double dF, sum;
   int it, use_bisect, stalled, compact, first, phase, how, passes;
+  int zglob;          // 1: the compacted bracket is in this CTA's device-memory region
 };
 
 // Sum of the elements below q and their number, over this thread's share of buf[0, m)
 // (the whole CTA: reduced into sh.sum6 by the caller).
 template <int B>
 __device__ __forceinline__ void below_sums(const float* buf, int m, float q, float& sum, unsigned int& cnt) {
-  for (int i = threadIdx.x; i < m; i += B) {
+  int i = threadIdx.x;
+  for (; i + (kRadixU - 1) * B < m; i += kRadixU * B) {
+    float v[kRadixU];
+#pragma unroll
+    for (int u = 0; u < kRadixU; ++u) v[u] = buf[i + u * B];
+#pragma unroll
+    for (int u = 0; u < kRadixU; ++u)
+      if (v[u] < q) { sum += v[u]; ++cnt; }
+  }
+  for (; i < m; i += B) {
     const float v = buf[i];
     if (v < q) { sum += v; ++cnt; }
   }
@@ -307,10 +401,12 @@ struct SegPassAcc {
   float S, sle;
 };
 // One cutting-plane pass over a segment at t (Algorithm 1, step 1.2); FIRST also counts at
-// the extremes, COMPACT appends (a, b] to zb, SUMLE sums the elements at or below a.
+// the extremes, COMPACT appends (a, b] to zb (capacity zcap), SUMLE sums the elements at or
+// below a.
 template <int B, bool FIRST, bool COMPACT, bool SUMLE>
 __device__ __noinline__ void seg_cut_pass(const float* __restrict__ xs, const Geometry<float>& g, float ca, float ct,
-                                          float cb, float nsig, float tsig, float* zb, unsigned int* cnt,
+                                          float cb, float nsig, float tsig, float* zb, unsigned int zcap,
+                                          unsigned int* cnt,
                                           SegPassAcc& acc) {
   unsigned int lt = 0, le = 0, xa = 0, xb = 0;
   float S = 0.f, sle = 0.f;
@@ -326,7 +422,7 @@ __device__ __noinline__ void seg_cut_pass(const float* __restrict__ xs, const Ge
   };
   if (COMPACT) {
     auto keep = [&](float v) { return (v > ca) & (v <= cb); };
-    cta_stream_compact<B>(xs, g, f, keep, zb, cnt);
+    cta_stream_compact<B>(xs, g, f, keep, zb, zcap, cnt);
   } else {
     cta_stream<B>(xs, g, f);
   }
@@ -385,11 +481,10 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
         __syncthreads();
         continue;
       }
-      const uint32_t key = smem_radix_select<B>(zb, (int)n, (unsigned long long)k, false, 0.f, 0.f, sh.hist,
-                                                &sh.prefix, &sh.known, &sh.rank);
+      const uint32_t key = radix_select<B>(zb, (int)n, (unsigned long long)k, false, 0.f, 0.f, nullptr, 0, sh.rx);
       const float q = ukey_value(key, 0.f);
       if (tid == 0) {
-        if (sh.rank == 0) atomicCAS(&A.ctrl->status, 0, (int)GBS_EINTERNAL);
+        if (sh.rx.rank == 0) atomicCAS(&A.ctrl->status, 0, (int)GBS_EINTERNAL);
         A.out[s] = q;
         if (A.seg_passes) A.seg_passes[s] = 1;
       }
@@ -401,8 +496,7 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
         Sum6 w6;
         w6.u[0] = bc; w6.u[1] = w6.u[2] = w6.u[3] = w6.u[4] = 0; w6.d = (double)bs;
         const Sum6 t6 = cta_sum6<B>(w6, sh.sum6);
-        const uint32_t key2 = smem_radix_select<B>(zb, (int)n, (unsigned long long)k2, false, 0.f, 0.f, sh.hist,
-                                                   &sh.prefix, &sh.known, &sh.rank);
+        const uint32_t key2 = radix_select<B>(zb, (int)n, (unsigned long long)k2, false, 0.f, 0.f, nullptr, 0, sh.rx);
         if (tid == 0) {
           A.outsum[s] = t6.d + (double)(k - (long long)t6.u[0]) * (double)q;
           A.out2[s] = ukey_value(key2, 0.f);
@@ -466,8 +560,11 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
     const long long per_thread = ((g.nv + B - 1) / B) * 4 + 8;
     while (sh.phase == 0) {
       if (tid == 0) {   // step 1.1 (with the key-midpoint safeguard)
+        // compaction of (a, b] in this pass: into shared memory when it fits there, else into
+        // the CTA's device-memory region once the bracket holds at most n / 16 elements
         const long long pop = sh.cle_b - sh.cle_a;
-        sh.compact = pop <= CAP;   // the compacted bracket must fit in shared memory
+        sh.compact = pop <= CAP ? 1
+                     : (A.zg != nullptr && pop <= (long long)A.zg_cap && pop * kSegGlobalDiv <= n) ? 2 : 0;
         const uint32_t ka = ukey(sh.a), kb = ukey(sh.b);
         float t;
         if (kb - ka <= 1u) {
@@ -492,20 +589,22 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
       if (sh.phase != 0) break;
       const float ca = sh.a, ct = sh.t, cb = sh.b, nsig = -sh.sig, tsig = sh.t * sh.sig;
       const int first = sh.first, compact = sh.compact;
+      float* const zdst = compact == 2 ? A.zg + (long long)blockIdx.x * A.zg_cap : zb;
+      const unsigned int zcap = compact == 2 ? (unsigned int)A.zg_cap : (unsigned int)CAP;
       SegPassAcc pacc;
       if (first) {
         if (compact) {
-          if (LTS) seg_cut_pass<B, true, true, true>(xs, g, ca, ct, cb, nsig, tsig, zb, &sh.zcnt, pacc);
-          else seg_cut_pass<B, true, true, false>(xs, g, ca, ct, cb, nsig, tsig, zb, &sh.zcnt, pacc);
+          if (LTS) seg_cut_pass<B, true, true, true>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
+          else seg_cut_pass<B, true, true, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
         } else {
-          seg_cut_pass<B, true, false, false>(xs, g, ca, ct, cb, nsig, tsig, zb, &sh.zcnt, pacc);
+          seg_cut_pass<B, true, false, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
         }
       } else {
         if (compact) {
-          if (LTS) seg_cut_pass<B, false, true, true>(xs, g, ca, ct, cb, nsig, tsig, zb, &sh.zcnt, pacc);
-          else seg_cut_pass<B, false, true, false>(xs, g, ca, ct, cb, nsig, tsig, zb, &sh.zcnt, pacc);
+          if (LTS) seg_cut_pass<B, false, true, true>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
+          else seg_cut_pass<B, false, true, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
         } else {
-          seg_cut_pass<B, false, false, false>(xs, g, ca, ct, cb, nsig, tsig, zb, &sh.zcnt, pacc);
+          seg_cut_pass<B, false, false, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
         }
       }
       const unsigned int lt = pacc.lt, le = pacc.le, xa = pacc.xa, xb = pacc.xb;
@@ -541,7 +640,7 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
         if (!resolved) {
           const long long pop = sh.cle_b - sh.cle_a;
           if (compact) {   // the bracket just compacted and the sum below it
-            sh.cle_a0 = sh.cle_a; sh.a0 = sh.a; sh.b0 = sh.b; sh.sum = sle_tot;
+            sh.cle_a0 = sh.cle_a; sh.a0 = sh.a; sh.b0 = sh.b; sh.sum = sle_tot; sh.zglob = compact == 2;
           }
           if (clt < k && k <= cle) {
             sh.phase = 1; sh.result = sh.t; sh.clt_res = clt; sh.cle_res = cle;
@@ -568,14 +667,16 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
     if (sh.phase == 2) {
       // the compacted bracket (a0, b0] holds ranks cle_a0 + 1 .. cle_a0 + zcnt
       const int m = (int)sh.zcnt;
-      const uint32_t key = smem_radix_select<B>(zb, m, (unsigned long long)(k - sh.cle_a0), true, sh.a0, sh.b0,
-                                                sh.hist, &sh.prefix, &sh.known, &sh.rank);
-      if (tid == 0 && sh.rank == 0) atomicCAS(&A.ctrl->status, 0, (int)GBS_EINTERNAL);
+      const float* zf = sh.zglob ? A.zg + (long long)blockIdx.x * A.zg_cap : zb;
+      float* const zs = sh.zglob ? zb : nullptr;   // gathers the last digits into shared memory
+      const uint32_t key = radix_select<B>(zf, m, (unsigned long long)(k - sh.cle_a0), true, sh.a0, sh.b0, zs, CAP,
+                                           sh.rx);
+      if (tid == 0 && sh.rx.rank == 0) atomicCAS(&A.ctrl->status, 0, (int)GBS_EINTERNAL);
       result = ukey_value(key, 0.f);
       if (LTS) {
         float bs = 0.f;
         unsigned int bc = 0;
-        below_sums<B>(zb, m, result, bs, bc);
+        below_sums<B>(zf, m, result, bs, bc);
         Sum6 w6;
         w6.u[0] = bc; w6.u[1] = w6.u[2] = w6.u[3] = w6.u[4] = 0; w6.d = (double)bs;
         const Sum6 t6 = cta_sum6<B>(w6, sh.sum6);
@@ -583,8 +684,8 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
         const bool inside2 = sh.cle_a0 < k2 && k2 <= sh.cle_a0 + m;
         float r2 = NAN;
         if (inside2) {
-          const uint32_t key2 = smem_radix_select<B>(zb, m, (unsigned long long)(k2 - sh.cle_a0), true, sh.a0,
-                                                     sh.b0, sh.hist, &sh.prefix, &sh.known, &sh.rank);
+          const uint32_t key2 = radix_select<B>(zf, m, (unsigned long long)(k2 - sh.cle_a0), true, sh.a0, sh.b0,
+                                                zs, CAP, sh.rx);
           r2 = ukey_value(key2, 0.f);
         }
         if (tid == 0) {
@@ -672,6 +773,16 @@ gbs_status seg_launch(gbs_ctx* c, const SegLaunch& L, int variant, cudaStream_t 
   SegArgs A;
   A.x = L.x; A.off = L.off; A.S = L.S; A.kk = L.kk; A.out = L.out; A.order = L.order; A.ctrl = L.ctrl;
   A.maxit = 48;
+  // the compaction area shared out among the CTAs (multiples of 32 elements each)
+  A.zg = nullptr;
+  A.zg_cap = 0;
+  if (L.zg != nullptr) {
+    const long long per = (L.zg_elems / grid) / 32 * 32;
+    if (per >= 32) {
+      A.zg = L.zg;
+      A.zg_cap = (int)std::min<long long>(per, 1ll << 30);
+    }
+  }
   A.seg_passes = L.seg_passes;
   A.k_const = L.k_const; A.k2_const = L.k2_const;
   A.kk2 = L.kk2; A.out2 = L.out2; A.outsum = L.outsum; A.flags = L.flags;
@@ -684,6 +795,25 @@ gbs_status seg_launch(gbs_ctx* c, const SegLaunch& L, int variant, cudaStream_t 
 }
 
 int seg_variant_threads(int v) { return (v >= 0 && v < kNumVariants) ? kVariants[v].threads : 0; }
+
+// Device-memory compaction area of a segmented launch, shared out among its CTAs (64 MiB:
+// about 55,000 elements a CTA at two CTAs on each of 152 SMs).
+constexpr size_t kSegZgBytes = size_t(64) << 20;
+
+size_t seg_workspace_bytes(int S) {
+  const size_t head = ((size_t)S * 2 * sizeof(int) + 255) / 256 * 256;
+  return head + kSegZgBytes;
+}
+
+gbs_status seg_attach_workspace(gbs_ctx* c, int S, SegLaunch* L) {
+  const gbs_status st = gbs_internal_ensure(c, seg_workspace_bytes(S));
+  if (st != GBS_OK) return st;
+  L->order = static_cast<int*>(c->z);
+  L->seg_passes = static_cast<int*>(c->z) + S;
+  L->zg = reinterpret_cast<float*>(static_cast<char*>(c->z) + ((size_t)S * 2 * sizeof(int) + 255) / 256 * 256);
+  L->zg_elems = (long long)(kSegZgBytes / sizeof(float));
+  return GBS_OK;
+}
 int seg_variant_cap(int v) { return (v >= 0 && v < kNumVariants) ? kVariants[v].cap : 0; }
 
 }  // namespace gbs
@@ -695,12 +825,10 @@ namespace {
 gbs_status seg_prepare(gbs_ctx* c, const float* x, const int64_t* off, int32_t S, float* out,
                        gbs::SegLaunch* L, const int64_t* k) {
   if (!c || !x || !off || !out || S < 1) return GBS_EINVAL;
-  gbs_status st = gbs_internal_ensure(c, (size_t)S * 2 * sizeof(int));
+  gbs_status st = gbs::seg_attach_workspace(c, S, L);
   if (st != GBS_OK) return st;
   L->x = x; L->off = reinterpret_cast<const long long*>(off); L->S = S;
   L->kk = reinterpret_cast<const long long*>(k); L->out = out;
-  L->order = static_cast<int*>(c->z);
-  L->seg_passes = static_cast<int*>(c->z) + S;
   L->ctrl = c->ctrl;
   L->mask = nullptr; L->kk2 = nullptr; L->out2 = nullptr; L->outsum = nullptr; L->flags = nullptr;
   L->k_const = 0; L->k2_const = 0;

@@ -26,6 +26,10 @@ struct SegArgs {
   double* outsum;
   int* flags;
   long long k_const, k2_const;   // ranks used for every segment when kk / kk2 are null (0: median)
+  // per-CTA compaction regions in device memory (CTA g owns zg[g * zg_cap, (g + 1) * zg_cap)) for
+  // brackets too large for shared memory; nullptr: shared memory only
+  float* zg;
+  int zg_cap;
 };
 
 struct SegLaunch {
@@ -43,7 +47,15 @@ struct SegLaunch {
   double* outsum;
   int* flags;
   long long k_const, k2_const;
+  float* zg = nullptr;            // compaction area shared out among the CTAs (see SegArgs)
+  long long zg_elems = 0;
 };
+
+// Bytes of the segmented workspace for S segments: the processing order, the pass
+// counts and the compaction area.
+size_t seg_workspace_bytes(int S);
+// Ensures the workspace for S segments and points L.order, L.seg_passes and L.zg into it.
+gbs_status seg_attach_workspace(gbs_ctx* c, int S, SegLaunch* L);
 
 int seg_num_variants();
 int seg_variant_threads(int v);

@@ -109,6 +109,31 @@ def test_segmented_heavy_tailed_segments(ctx):
         assert np.array_equal(bits(got), bits(expect(x, off, k))), frac
 
 
+def test_segmented_brackets_compacted_in_device_memory(ctx):
+    """Segments of 2e5 to 9e5 elements reach a bracket of at most n/16 elements while it is
+    still larger than shared memory: it is compacted into the CTA's device-memory region
+    and the finish gathers the chosen digit into shared memory.  Few distinct values (a
+    digit bucket larger than shared memory), signed zeros and a normal sample."""
+    def gen(i, n, rng):
+        kind = i % 3
+        if kind == 0:   # 3000 distinct values, each repeated
+            return rng.choice(rng.standard_normal(3000).astype(np.float32), n)
+        if kind == 1:   # zeros of both signs among a narrow normal sample
+            v = (rng.standard_normal(n) * 1e-3).astype(np.float32)
+            v[rng.random(n) < 0.2] = 0.0
+            v[rng.random(n) < 0.2] = -0.0
+            return v
+        return (rng.standard_normal(n) * 50.0 + 7.0).astype(np.float32)
+    sizes = [200_003, 450_000, 900_001, 333_333, 600_000, 250_000]
+    x, off = make_batch(sizes, seed=81, gen=gen)
+    for frac in (0.001, 0.3, 0.5, 0.97):
+        k = np.array([max(1, int(frac * n)) for n in sizes], dtype=np.int64)
+        got = run(ctx, x, off, k)
+        assert np.array_equal(bits(got), bits(expect(x, off, k))), frac
+    passes = ctx.segmented_passes(len(sizes))
+    assert all(2 <= p <= 40 for p in passes), passes
+
+
 def test_segmented_invalid_segments_are_flagged(ctx, lib):
     x, off = make_batch([10, 0, 10], seed=75)
     got = run(ctx, x, off)
