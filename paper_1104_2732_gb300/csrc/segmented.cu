@@ -6,7 +6,7 @@
 // is loaded once and radix-selected there.  A larger one runs the cutting plane of
 // Algorithm 1 (Sec. 3) with CTA-wide reductions: pass 0 (extremes, sum), then one fused
 // cost + count pass per iterate; the pass that sees a bracket small enough for shared
-// memory compacts it there, or one of at most n/16 elements into the CTA's own
+// memory compacts it there, or one of at most n/4 elements into the CTA's own
 // device-memory region, and the answer is radix-selected inside it (the hybrid of
 // Sec. 3; from device memory the rounds move to shared memory once the chosen digit's
 // elements fit there).  No CTA waits on another, so the launch needs no grid-wide barrier and the
@@ -26,7 +26,7 @@ namespace gbs {
 namespace {
 
 constexpr int kSchedBuckets = 64;
-constexpr long long kSegGlobalDiv = 16;   // device-memory compaction once pop <= n / 16
+constexpr long long kSegGlobalDiv = 4;   // device-memory compaction once pop <= n / 4
 
 // Buckets segment ids by floor(log2(size)), largest bucket first; also checks offsets.
 __global__ void seg_schedule_kernel(const long long* __restrict__ off, int S, int* __restrict__ order,
@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
     while (sh.phase == 0) {
       if (tid == 0) {   // step 1.1 (with the key-midpoint safeguard)
         // compaction of (a, b] in this pass: into shared memory when it fits there, else into
-        // the CTA's device-memory region once the bracket holds at most n / 16 elements
+        // the CTA's device-memory region once the bracket holds at most n / 4 elements
         const long long pop = sh.cle_b - sh.cle_a;
         sh.compact = pop <= CAP ? 1
                      : (A.zg != nullptr && pop <= (long long)A.zg_cap && pop * kSegGlobalDiv <= n) ? 2 : 0;
@@ -796,9 +796,9 @@ gbs_status seg_launch(gbs_ctx* c, const SegLaunch& L, int variant, cudaStream_t 
 
 int seg_variant_threads(int v) { return (v >= 0 && v < kNumVariants) ? kVariants[v].threads : 0; }
 
-// Device-memory compaction area of a segmented launch, shared out among its CTAs (64 MiB:
-// about 55,000 elements a CTA at two CTAs on each of 152 SMs).
-constexpr size_t kSegZgBytes = size_t(64) << 20;
+// Device-memory compaction area of a segmented launch, shared out among its CTAs (256 MiB:
+// about 220,000 elements a CTA at two CTAs on each of 152 SMs).
+constexpr size_t kSegZgBytes = size_t(256) << 20;
 
 size_t seg_workspace_bytes(int S) {
   const size_t head = ((size_t)S * 2 * sizeof(int) + 255) / 256 * 256;

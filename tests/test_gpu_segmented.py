@@ -110,7 +110,7 @@ def test_segmented_heavy_tailed_segments(ctx):
 
 
 def test_segmented_brackets_compacted_in_device_memory(ctx):
-    """Segments of 2e5 to 9e5 elements reach a bracket of at most n/16 elements while it is
+    """Segments of 2e5 to 9e5 elements reach a bracket of at most n/4 elements while it is
     still larger than shared memory: it is compacted into the CTA's device-memory region
     and the finish gathers the chosen digit into shared memory.  Few distinct values (a
     digit bucket larger than shared memory), signed zeros and a normal sample."""
