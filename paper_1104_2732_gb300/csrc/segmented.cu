@@ -139,8 +139,12 @@ __device__ __forceinline__ void cta_stream_compact(const float* __restrict__ xs,
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const long long i = wb + lane + (long long)u * B;
+      if (i < g.nv) r[u] = __ldcs(xv + i);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long i = wb + lane + (long long)u * B;
       if (i < g.nv) {
-        r[u] = __ldcs(xv + i);
         Ops<float>::each(r[u], f);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -184,38 +188,72 @@ struct RadixState {
   unsigned int cnt;         // append counter of the gather
 };
 
-constexpr int kRadixU = 4;   // loads in flight per thread in the radix sweeps
+constexpr int kRadixV = 2;   // 16-byte loads in flight per thread in the radix sweeps
 
-// Whether element i of buf[0, m) (value v) takes part in a round: in (a, b] when filtering,
-// and its key starts with the known prefix.
-__device__ __forceinline__ bool radix_takes(int i, int m, float v, uint32_t key, bool filter, float a, float b,
-                                            int known, uint32_t prefix) {
-  return i < m && (!filter || ((v > a) && (v <= b))) && (known == 0 || (key >> (32 - known)) == prefix);
+// Whether an element (value v, key) takes part in a round: in (a, b] when filtering, and
+// its key starts with the known prefix.
+__device__ __forceinline__ bool radix_takes(float v, uint32_t key, bool filter, float a, float b, int known,
+                                            uint32_t prefix) {
+  return (!filter || ((v > a) && (v <= b))) && (known == 0 || (key >> (32 - known)) == prefix);
+}
+
+// Adds digit d (256: none) of every lane of the warp to the histogram: once for the warp
+// when its active lanes share the digit (runs of equal values), else once per lane.
+__device__ __forceinline__ void radix_hist_add(unsigned int d, int lane, unsigned int* hist) {
+  const unsigned int act = __ballot_sync(0xffffffffu, d < 256u);
+  if (act) {
+    const int l0 = __ffs(act) - 1;
+    const unsigned int d0 = __shfl_sync(0xffffffffu, d, l0);
+    if (__all_sync(0xffffffffu, d == 256u || d == d0)) {
+      if (lane == l0) atomicAdd(&hist[d0], (unsigned int)__popc(act));
+    } else if (d < 256u) {
+      atomicAdd(&hist[d], 1u);
+    }
+  }
+}
+
+// Calls fn(valid, value) on every element of buf[0, m) (16-byte aligned) for this warp's
+// share, kRadixV 16-byte loads in flight per lane; the warp loop is uniform (fn may use
+// warp collectives), and the last m mod 4 elements go to warp 0.
+template <int B, typename Fn>
+__device__ __forceinline__ void radix_sweep(const float* buf, int m, Fn& fn) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float4* b4 = reinterpret_cast<const float4*>(buf);
+  const int m4 = m >> 2;
+  for (int base = warp * 32; base < m4; base += B * kRadixV) {
+    float4 v[kRadixV];
+#pragma unroll
+    for (int u = 0; u < kRadixV; ++u) {
+      const int i = base + u * B + lane;
+      v[u] = i < m4 ? b4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kRadixV; ++u) {
+      const bool ok = base + u * B + lane < m4;
+      fn(ok, v[u].x);
+      fn(ok, v[u].y);
+      fn(ok, v[u].z);
+      fn(ok, v[u].w);
+    }
+  }
+  if (warp == 0 && (m & 3)) {
+    const bool ok = lane < (m & 3);
+    fn(ok, ok ? buf[4 * m4 + lane] : 0.f);
+  }
 }
 
 // Histogram of the next digit (bits [sh, sh + 8) of the key) over the elements of buf that
-// take part; a warp's lanes with equal digits add once.
+// take part.
 template <int B>
 __device__ __forceinline__ void radix_hist(const float* buf, int m, bool filter, float a, float b, int known,
                                            uint32_t prefix, int sh, unsigned int dmask, unsigned int* hist) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int base = warp * 32; base < m; base += B * kRadixU) {
-    float v[kRadixU];
-#pragma unroll
-    for (int u = 0; u < kRadixU; ++u) {
-      const int i = base + u * B + lane;
-      v[u] = i < m ? buf[i] : 0.f;
-    }
-#pragma unroll
-    for (int u = 0; u < kRadixU; ++u) {
-      const int i = base + u * B + lane;
-      const uint32_t key = ukey(v[u]);
-      const unsigned int d =
-          radix_takes(i, m, v[u], key, filter, a, b, known, prefix) ? (key >> sh) & dmask : 256u;
-      const unsigned int same = __match_any_sync(0xffffffffu, d);
-      if (d < 256 && lane == __ffs(same) - 1) atomicAdd(&hist[d], (unsigned int)__popc(same));
-    }
-  }
+  const int lane = threadIdx.x & 31;
+  auto fn = [&](bool ok, float v) {
+    const uint32_t key = ukey(v);
+    radix_hist_add(ok && radix_takes(v, key, filter, a, b, known, prefix) ? (key >> sh) & dmask : 256u, lane,
+                   hist);
+  };
+  radix_sweep<B>(buf, m, fn);
 }
 
 // Appends the elements of buf that take part to zs (counter *cnt; any order; at most cap
@@ -223,28 +261,19 @@ __device__ __forceinline__ void radix_hist(const float* buf, int m, bool filter,
 template <int B>
 __device__ __forceinline__ void radix_gather(const float* buf, int m, bool filter, float a, float b, int known,
                                              uint32_t prefix, float* zs, unsigned int cap, unsigned int* cnt) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int base = warp * 32; base < m; base += B * kRadixU) {
-    float v[kRadixU];
-#pragma unroll
-    for (int u = 0; u < kRadixU; ++u) {
-      const int i = base + u * B + lane;
-      v[u] = i < m ? buf[i] : 0.f;
+  const int lane = threadIdx.x & 31;
+  auto fn = [&](bool ok, float v) {
+    const bool t = ok && radix_takes(v, ukey(v), filter, a, b, known, prefix);
+    const unsigned int bal = __ballot_sync(0xffffffffu, t);
+    if (bal) {
+      unsigned int b0 = 0;
+      if (lane == 0) b0 = atomicAdd(cnt, (unsigned int)__popc(bal));
+      b0 = __shfl_sync(0xffffffffu, b0, 0);
+      const unsigned int pos = b0 + __popc(bal & ((1u << lane) - 1u));
+      if (t && pos < cap) zs[pos] = v;
     }
-#pragma unroll
-    for (int u = 0; u < kRadixU; ++u) {
-      const int i = base + u * B + lane;
-      const bool t = radix_takes(i, m, v[u], ukey(v[u]), filter, a, b, known, prefix);
-      const unsigned int bal = __ballot_sync(0xffffffffu, t);
-      if (bal) {
-        unsigned int b0 = 0;
-        if (lane == 0) b0 = atomicAdd(cnt, (unsigned int)__popc(bal));
-        b0 = __shfl_sync(0xffffffffu, b0, 0);
-        const unsigned int pos = b0 + __popc(bal & ((1u << lane) - 1u));
-        if (t && pos < cap) zs[pos] = v[u];
-      }
-    }
-  }
+  };
+  radix_sweep<B>(buf, m, fn);
 }
 
 // Radix select inside the CTA: the rank-th (1-based) smallest, in totalOrder, of the
@@ -253,8 +282,8 @@ __device__ __forceinline__ void radix_gather(const float* buf, int m, bool filte
 // buf is in device memory, zs (shared memory, cap elements, else nullptr) takes the
 // elements of the chosen digit once they fit, and the later rounds run there.
 template <int B>
-__device__ uint32_t radix_select(const float* buf, int m, unsigned long long rank, bool filter, float a, float b,
-                                 float* zs, int cap, RadixState& st) {
+__device__ __noinline__ uint32_t radix_select(const float* buf, int m, unsigned long long rank, bool filter, float a,
+                                              float b, float* zs, int cap, RadixState& st) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     int known = 0;
@@ -348,23 +377,92 @@ struct SegShared {
   int zglob;          // 1: the compacted bracket is in this CTA's device-memory region
 };
 
+// As cta_stream_compact for a destination in device memory: a lane writes the kept
+// elements of an iteration to its own slots of the warp's shared-memory staging buffer
+// (slot j of lane L at stage[warp * 512 + L + 32 j]: no bank conflicts), and the warp
+// copies them to zb with consecutive stores, each output index finding its lane by a
+// binary search over the lanes' inclusive counts.
+template <int B, typename Fn, typename Keep>
+__device__ __forceinline__ void cta_stream_compact_staged(const float* __restrict__ xs, const Geometry<float>& g,
+                                                          Fn& f, Keep& keep, float* __restrict__ zb,
+                                                          unsigned int zcap, unsigned int* cnt, float* stage) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  float* wbuf = stage + (tid >> 5) * 512;
+  if (tid < g.head) {
+    const float e = xs[tid];
+    f(e);
+    if (keep(e)) {
+      const unsigned int q = atomicAdd(cnt, 1u);
+      if (q < zcap) zb[q] = e;
+    }
+  }
+  if (tid < g.n - g.tail0) {
+    const float e = xs[g.tail0 + tid];
+    f(e);
+    if (keep(e)) {
+      const unsigned int q = atomicAdd(cnt, 1u);
+      if (q < zcap) zb[q] = e;
+    }
+  }
+  const float4* xv = reinterpret_cast<const float4*>(xs + g.head);
+  for (long long w0 = tid - lane; w0 < g.nv; w0 += 4 * B) {
+    float4 r[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long i = w0 + lane + (long long)u * B;
+      if (i < g.nv) r[u] = __ldcs(xv + i);
+    }
+    unsigned int k = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long i = w0 + lane + (long long)u * B;
+      if (i < g.nv) {
+        Ops<float>::each(r[u], f);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float v = Ops<float>::get(r[u], e);
+          const bool kk = keep(v);
+          if (kk) wbuf[lane + 32 * k] = v;
+          k += kk;
+        }
+      }
+    }
+    unsigned int incl = k;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total) {
+      unsigned int b0 = 0;
+      if (lane == 31) b0 = atomicAdd(cnt, total);
+      b0 = __shfl_sync(0xffffffffu, b0, 31);
+      __syncwarp();
+      for (unsigned int i0 = 0; i0 < total; i0 += 32) {
+        const unsigned int i = i0 + lane;
+        int L = 0;   // lanes whose inclusive count is <= i
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const unsigned int v = __shfl_sync(0xffffffffu, incl, L + step - 1);
+          if (v <= i) L += step;
+        }
+        const unsigned int exL = __shfl_sync(0xffffffffu, incl, L) - __shfl_sync(0xffffffffu, k, L);
+        if (i < total && b0 + i < zcap) zb[b0 + i] = wbuf[L + 32 * (i - exL)];
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // Sum of the elements below q and their number, over this thread's share of buf[0, m)
-// (the whole CTA: reduced into sh.sum6 by the caller).
+// (16-byte aligned; the whole CTA: reduced into sh.sum6 by the caller).
 template <int B>
-__device__ __forceinline__ void below_sums(const float* buf, int m, float q, float& sum, unsigned int& cnt) {
-  int i = threadIdx.x;
-  for (; i + (kRadixU - 1) * B < m; i += kRadixU * B) {
-    float v[kRadixU];
-#pragma unroll
-    for (int u = 0; u < kRadixU; ++u) v[u] = buf[i + u * B];
-#pragma unroll
-    for (int u = 0; u < kRadixU; ++u)
-      if (v[u] < q) { sum += v[u]; ++cnt; }
-  }
-  for (; i < m; i += B) {
-    const float v = buf[i];
-    if (v < q) { sum += v; ++cnt; }
-  }
+__device__ __noinline__ void below_sums(const float* buf, int m, float q, float& sum, unsigned int& cnt) {
+  auto fn = [&](bool ok, float v) {
+    if (ok && v < q) { sum += v; ++cnt; }
+  };
+  radix_sweep<B>(buf, m, fn);
 }
 
 // The streaming passes of a large segment, kept out of line so that their registers are
@@ -401,13 +499,13 @@ struct SegPassAcc {
   float S, sle;
 };
 // One cutting-plane pass over a segment at t (Algorithm 1, step 1.2); FIRST also counts at
-// the extremes, COMPACT appends (a, b] to zb (capacity zcap), SUMLE sums the elements at or
-// below a.
+// the extremes, COMPACT appends (a, b] to zb (capacity zcap; staged through `stage`, the
+// warps' shared-memory buffers, when zb is in device memory), SUMLE sums the elements at
+// or below a.
 template <int B, bool FIRST, bool COMPACT, bool SUMLE>
 __device__ __noinline__ void seg_cut_pass(const float* __restrict__ xs, const Geometry<float>& g, float ca, float ct,
                                           float cb, float nsig, float tsig, float* zb, unsigned int zcap,
-                                          unsigned int* cnt,
-                                          SegPassAcc& acc) {
+                                          unsigned int* cnt, float* stage, SegPassAcc& acc) {
   unsigned int lt = 0, le = 0, xa = 0, xb = 0;
   float S = 0.f, sle = 0.f;
   auto f = [&](float v) {
@@ -422,7 +520,8 @@ __device__ __noinline__ void seg_cut_pass(const float* __restrict__ xs, const Ge
   };
   if (COMPACT) {
     auto keep = [&](float v) { return (v > ca) & (v <= cb); };
-    cta_stream_compact<B>(xs, g, f, keep, zb, zcap, cnt);
+    if (stage != nullptr) cta_stream_compact_staged<B>(xs, g, f, keep, zb, zcap, cnt, stage);
+    else cta_stream_compact<B>(xs, g, f, keep, zb, zcap, cnt);
   } else {
     cta_stream<B>(xs, g, f);
   }
@@ -431,6 +530,7 @@ __device__ __noinline__ void seg_cut_pass(const float* __restrict__ xs, const Ge
 
 template <int B, int CAP, bool LTS>
 __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
+  static_assert(CAP >= 16 * B, "the warps' compaction staging (512 floats each) lives in the CAP buffer");
   extern __shared__ __align__(16) float zb[];   // CAP floats
   __shared__ SegShared sh;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -591,20 +691,21 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
       const int first = sh.first, compact = sh.compact;
       float* const zdst = compact == 2 ? A.zg + (long long)blockIdx.x * A.zg_cap : zb;
       const unsigned int zcap = compact == 2 ? (unsigned int)A.zg_cap : (unsigned int)CAP;
+      float* const zstage = compact == 2 ? zb : nullptr;   // shared memory is free for staging then
       SegPassAcc pacc;
       if (first) {
         if (compact) {
-          if (LTS) seg_cut_pass<B, true, true, true>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
-          else seg_cut_pass<B, true, true, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
+          if (LTS) seg_cut_pass<B, true, true, true>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, zstage, pacc);
+          else seg_cut_pass<B, true, true, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, zstage, pacc);
         } else {
-          seg_cut_pass<B, true, false, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
+          seg_cut_pass<B, true, false, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, zstage, pacc);
         }
       } else {
         if (compact) {
-          if (LTS) seg_cut_pass<B, false, true, true>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
-          else seg_cut_pass<B, false, true, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
+          if (LTS) seg_cut_pass<B, false, true, true>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, zstage, pacc);
+          else seg_cut_pass<B, false, true, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, zstage, pacc);
         } else {
-          seg_cut_pass<B, false, false, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
+          seg_cut_pass<B, false, false, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, zstage, pacc);
         }
       }
       const unsigned int lt = pacc.lt, le = pacc.le, xa = pacc.xa, xb = pacc.xb;
