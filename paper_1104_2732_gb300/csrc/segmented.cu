@@ -110,8 +110,9 @@ __device__ __forceinline__ void cta_stream(const float* __restrict__ xs, const G
 
 // As cta_stream, and appends every element with keep(element) to zb (shared memory or
 // this CTA's device-memory region, counter *cnt; appends past zcap are counted, not
-// written, so the caller's count check catches them).  Warp-uniform loop for the
-// per-warp prefix sum.
+// written, so the caller's count check catches them).  Per warp iteration (16 elements a
+// lane) one atomic reserves the warp's kept elements; then, slot by slot, a ballot gives
+// every keeping lane its position, so each store covers consecutive addresses.
 template <int B, typename Fn, typename Keep>
 __device__ __forceinline__ void cta_stream_compact(const float* __restrict__ xs, const Geometry<float>& g, Fn& f,
                                                    Keep& keep, float* zb, unsigned int zcap, unsigned int* cnt) {
@@ -132,48 +133,40 @@ __device__ __forceinline__ void cta_stream_compact(const float* __restrict__ xs,
       if (q < zcap) zb[q] = e;
     }
   }
+  const unsigned int lt_mask = (1u << lane) - 1u;
   const float4* xv = reinterpret_cast<const float4*>(xs + g.head);
-  for (long long wb = tid - lane; wb < g.nv; wb += 4 * B) {
+  for (long long w0 = tid - lane; w0 < g.nv; w0 += 4 * B) {
     float4 r[4];
-    unsigned int mask = 0, c = 0;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const long long i = wb + lane + (long long)u * B;
+      const long long i = w0 + lane + (long long)u * B;
       if (i < g.nv) r[u] = __ldcs(xv + i);
     }
+    unsigned int kmask = 0;   // bit 4u + e: this lane keeps element e of vector u
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const long long i = wb + lane + (long long)u * B;
+      const long long i = w0 + lane + (long long)u * B;
       if (i < g.nv) {
         Ops<float>::each(r[u], f);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const bool kk = keep(Ops<float>::get(r[u], e));
-          mask |= (kk ? 1u : 0u) << (u * 4 + e);
-          c += kk;
-        }
+        for (int e = 0; e < 4; ++e) kmask |= (keep(Ops<float>::get(r[u], e)) ? 1u : 0u) << (u * 4 + e);
       }
     }
-    unsigned int incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+    const unsigned int total = __reduce_add_sync(0xffffffffu, (unsigned int)__popc(kmask));
     if (total) {
-      unsigned int b0 = 0;
-      if (lane == 31) b0 = atomicAdd(cnt, total);
-      b0 = __shfl_sync(0xffffffffu, b0, 31);
-      unsigned int pos = b0 + incl - c;
+      unsigned int pos = 0;
+      if (lane == 0) pos = atomicAdd(cnt, total);
+      pos = __shfl_sync(0xffffffffu, pos, 0);
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (mask & (1u << (u * 4 + e))) {
-            if (pos < zcap) zb[pos] = Ops<float>::get(r[u], e);
-            ++pos;
-          }
+        for (int e = 0; e < 4; ++e) {
+          const bool kk = (kmask >> (u * 4 + e)) & 1u;
+          const unsigned int bal = __ballot_sync(0xffffffffu, kk);
+          const unsigned int q = pos + __popc(bal & lt_mask);
+          if (kk && q < zcap) zb[q] = Ops<float>::get(r[u], e);
+          pos += __popc(bal);
+        }
     }
   }
 }
@@ -377,84 +370,6 @@ struct SegShared {
   int zglob;          // 1: the compacted bracket is in this CTA's device-memory region
 };
 
-// As cta_stream_compact for a destination in device memory: a lane writes the kept
-// elements of an iteration to its own slots of the warp's shared-memory staging buffer
-// (slot j of lane L at stage[warp * 512 + L + 32 j]: no bank conflicts), and the warp
-// copies them to zb with consecutive stores, each output index finding its lane by a
-// binary search over the lanes' inclusive counts.
-template <int B, typename Fn, typename Keep>
-__device__ __forceinline__ void cta_stream_compact_staged(const float* __restrict__ xs, const Geometry<float>& g,
-                                                          Fn& f, Keep& keep, float* __restrict__ zb,
-                                                          unsigned int zcap, unsigned int* cnt, float* stage) {
-  const int tid = threadIdx.x, lane = tid & 31;
-  float* wbuf = stage + (tid >> 5) * 512;
-  if (tid < g.head) {
-    const float e = xs[tid];
-    f(e);
-    if (keep(e)) {
-      const unsigned int q = atomicAdd(cnt, 1u);
-      if (q < zcap) zb[q] = e;
-    }
-  }
-  if (tid < g.n - g.tail0) {
-    const float e = xs[g.tail0 + tid];
-    f(e);
-    if (keep(e)) {
-      const unsigned int q = atomicAdd(cnt, 1u);
-      if (q < zcap) zb[q] = e;
-    }
-  }
-  const float4* xv = reinterpret_cast<const float4*>(xs + g.head);
-  for (long long w0 = tid - lane; w0 < g.nv; w0 += 4 * B) {
-    float4 r[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const long long i = w0 + lane + (long long)u * B;
-      if (i < g.nv) r[u] = __ldcs(xv + i);
-    }
-    unsigned int k = 0;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const long long i = w0 + lane + (long long)u * B;
-      if (i < g.nv) {
-        Ops<float>::each(r[u], f);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float v = Ops<float>::get(r[u], e);
-          const bool kk = keep(v);
-          if (kk) wbuf[lane + 32 * k] = v;
-          k += kk;
-        }
-      }
-    }
-    unsigned int incl = k;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
-    if (total) {
-      unsigned int b0 = 0;
-      if (lane == 31) b0 = atomicAdd(cnt, total);
-      b0 = __shfl_sync(0xffffffffu, b0, 31);
-      __syncwarp();
-      for (unsigned int i0 = 0; i0 < total; i0 += 32) {
-        const unsigned int i = i0 + lane;
-        int L = 0;   // lanes whose inclusive count is <= i
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const unsigned int v = __shfl_sync(0xffffffffu, incl, L + step - 1);
-          if (v <= i) L += step;
-        }
-        const unsigned int exL = __shfl_sync(0xffffffffu, incl, L) - __shfl_sync(0xffffffffu, k, L);
-        if (i < total && b0 + i < zcap) zb[b0 + i] = wbuf[L + 32 * (i - exL)];
-      }
-      __syncwarp();
-    }
-  }
-}
-
 // Sum of the elements below q and their number, over this thread's share of buf[0, m)
 // (16-byte aligned; the whole CTA: reduced into sh.sum6 by the caller).
 template <int B>
@@ -499,13 +414,12 @@ struct SegPassAcc {
   float S, sle;
 };
 // One cutting-plane pass over a segment at t (Algorithm 1, step 1.2); FIRST also counts at
-// the extremes, COMPACT appends (a, b] to zb (capacity zcap; staged through `stage`, the
-// warps' shared-memory buffers, when zb is in device memory), SUMLE sums the elements at
+// the extremes, COMPACT appends (a, b] to zb (capacity zcap), SUMLE sums the elements at
 // or below a.
 template <int B, bool FIRST, bool COMPACT, bool SUMLE>
 __device__ __noinline__ void seg_cut_pass(const float* __restrict__ xs, const Geometry<float>& g, float ca, float ct,
                                           float cb, float nsig, float tsig, float* zb, unsigned int zcap,
-                                          unsigned int* cnt, float* stage, SegPassAcc& acc) {
+                                          unsigned int* cnt, SegPassAcc& acc) {
   unsigned int lt = 0, le = 0, xa = 0, xb = 0;
   float S = 0.f, sle = 0.f;
   auto f = [&](float v) {
@@ -520,8 +434,7 @@ __device__ __noinline__ void seg_cut_pass(const float* __restrict__ xs, const Ge
   };
   if (COMPACT) {
     auto keep = [&](float v) { return (v > ca) & (v <= cb); };
-    if (stage != nullptr) cta_stream_compact_staged<B>(xs, g, f, keep, zb, zcap, cnt, stage);
-    else cta_stream_compact<B>(xs, g, f, keep, zb, zcap, cnt);
+    cta_stream_compact<B>(xs, g, f, keep, zb, zcap, cnt);
   } else {
     cta_stream<B>(xs, g, f);
   }
@@ -530,7 +443,6 @@ __device__ __noinline__ void seg_cut_pass(const float* __restrict__ xs, const Ge
 
 template <int B, int CAP, bool LTS>
 __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
-  static_assert(CAP >= 16 * B, "the warps' compaction staging (512 floats each) lives in the CAP buffer");
   extern __shared__ __align__(16) float zb[];   // CAP floats
   __shared__ SegShared sh;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -691,21 +603,20 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
       const int first = sh.first, compact = sh.compact;
       float* const zdst = compact == 2 ? A.zg + (long long)blockIdx.x * A.zg_cap : zb;
       const unsigned int zcap = compact == 2 ? (unsigned int)A.zg_cap : (unsigned int)CAP;
-      float* const zstage = compact == 2 ? zb : nullptr;   // shared memory is free for staging then
       SegPassAcc pacc;
       if (first) {
         if (compact) {
-          if (LTS) seg_cut_pass<B, true, true, true>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, zstage, pacc);
-          else seg_cut_pass<B, true, true, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, zstage, pacc);
+          if (LTS) seg_cut_pass<B, true, true, true>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
+          else seg_cut_pass<B, true, true, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
         } else {
-          seg_cut_pass<B, true, false, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, zstage, pacc);
+          seg_cut_pass<B, true, false, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
         }
       } else {
         if (compact) {
-          if (LTS) seg_cut_pass<B, false, true, true>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, zstage, pacc);
-          else seg_cut_pass<B, false, true, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, zstage, pacc);
+          if (LTS) seg_cut_pass<B, false, true, true>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
+          else seg_cut_pass<B, false, true, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
         } else {
-          seg_cut_pass<B, false, false, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, zstage, pacc);
+          seg_cut_pass<B, false, false, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
         }
       }
       const unsigned int lt = pacc.lt, le = pacc.le, xa = pacc.xa, xb = pacc.xb;
