@@ -255,6 +255,34 @@ def bench_segmented(gbs, ctx, torch, np, args):
     same = bool(torch.equal(out.view(torch.int32), outs.view(torch.int32)))
     sizes = np.diff(off)
     big = sizes > ctx.segmented_variant()["smem_cap"]
+    # the same batch with learned starting brackets for the medians (shipped model)
+    learned = None
+    model = os.path.join(ROOT, "paper_1104_2732_gb300", "bracket_model.bin")
+    if os.path.exists(model):
+        ctx.load_bracket_model(model)
+        ctx.set_config(use_learned=1)
+        outl = torch.empty(S, device="cuda")
+        with torch.cuda.stream(stream):
+            ctx.select_segmented(x, ot, None, outl, stream=stream)
+        stream.synchronize()
+        lpasses = np.array(ctx.segmented_passes(S))
+        gl = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gl, stream=stream):
+            ctx.select_segmented(x, ot, None, outl, stream=stream)
+        for _ in range(3):
+            gl.replay()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            gl.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        lms_ = e0.elapsed_time(e1) / reps
+        ctx.set_config(use_learned=0)
+        learned = {"ms_per_batch": lms_, "value": S / (lms_ * 1e-3), "gelem_s": total / (lms_ * 1e-3) / 1e9,
+                   "mean_passes_large_segments": float(lpasses[big].mean()) if big.any() else None,
+                   "identical_to_plain_start": bool(torch.equal(out.view(torch.int32), outl.view(torch.int32))),
+                   "speedup_vs_plain_start": ms / lms_}
     # CPU oracle (as it stands, 1 thread) on every 32nd segment, scaled to the batch
     from oracle import select as osel
     sample = range(0, S, 32)
@@ -277,6 +305,7 @@ def bench_segmented(gbs, ctx, torch, np, args):
         "bytes_read_per_batch": int(sum(p * n * 4 for p, n in zip(passes, sizes))),
         "achieved_gbs": sum(p * n * 4 for p, n in zip(passes, sizes)) / (ms * 1e-3) / 1e9,
         "cpu_baseline": cpu,
+        "learned_start": learned,
     }
 
 

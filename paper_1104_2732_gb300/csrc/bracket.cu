@@ -92,7 +92,6 @@ __global__ void gen_train_kernel(float* __restrict__ x, long long n, int family,
   }
 }
 
-__device__ __forceinline__ float gelu(float u) { return 0.5f * u * (1.0f + erff(u * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float u) {
   return 0.5f * (1.0f + erff(u * 0.70710678118654752f)) + u * 0.39894228040143268f * expf(-0.5f * u * u);
 }
@@ -131,38 +130,7 @@ __device__ bool sketch(const T* __restrict__ x, long long n, double* sv, float* 
   }
   sv[tid] = (double)ukey_value(key, T());
   __syncthreads();
-  if (tid < 32) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    for (int i = 0; i < kSample / 32; i += 4) {
-      s0 += sv[(i + 0) * 32 + lane];
-      s1 += sv[(i + 1) * 32 + lane];
-      s2 += sv[(i + 2) * 32 + lane];
-      s3 += sv[(i + 3) * 32 + lane];
-    }
-    double s = (s0 + s1) + (s2 + s3);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    const double m = s / kSample;
-    double q0 = 0.0, q1 = 0.0;
-    for (int i = 0; i < kSample / 32; i += 2) {
-      const double d0 = sv[i * 32 + lane] - m, d1 = sv[(i + 1) * 32 + lane] - m;
-      q0 = fma(d0, d0, q0);
-      q1 = fma(d1, d1, q1);
-    }
-    double q = q0 + q1;
-    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-    double d = sqrt(q / kSample);
-    d = d > 0.0 ? d : 1.0;
-    f[lane] = (float)((sv[16 + 32 * lane] - m) / d);           // 32 quantiles (kQuant == 32)
-    if (lane < 3) {
-      const double z = lane == 0 ? (sv[0] - m) / d : lane == 1 ? (sv[kSample - 1] - m) / d : m / d;
-      f[32 + lane] = asinhf((float)z);
-    }
-    if (lane == 3) f[35] = logf((float)d) * (1.0f / 16.0f);
-    if (lane == 0) {
-      *mu = m;
-      *sd = d;
-    }
-  }
+  if (tid < 32) sketch_features_warp(sv, f, mu, sd);
   __syncthreads();
   return true;
 }
@@ -216,13 +184,6 @@ struct WarpRows {
   }
 };
 
-__device__ __forceinline__ float warp_dot(float a0, float a1, const float* v, int len) {
-  const int lane = threadIdx.x & 31;
-  float u = a0 * v[lane];
-  if (lane + 32 < len) u = fmaf(a1, v[lane + 32], u);
-  for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
-  return u;
-}
 
 __device__ void mlp_forward_warps(const WarpRows& R, const float* f, float* h1, float* h2, float* o) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -261,11 +222,8 @@ __global__ void __launch_bounds__(1024) propose_kernel(const T* __restrict__ x, 
   }
   mlp_forward_warps(R, f, h1, h2, o);
   if (threadIdx.x == 0) {
-    const double c = o[0];
-    const double om = fmin(fmax((double)o[1], -30.0), 30.0);
-    const double w = exp(om);
-    const double a = mu + sd * (c - w), b = mu + sd * (c + w);
-    const bool valid = isfinite(a) && isfinite(b) && a < b;
+    double a, b;
+    const bool valid = proposal_from_outputs(o, mu, sd, &a, &b);
     prop[0] = a;
     prop[1] = b;
     prop[2] = valid ? 1.0 : 0.0;

@@ -17,6 +17,7 @@
 #include <cstdint>
 
 #include "api_internal.h"
+#include "bracket.cuh"
 #include "common.cuh"
 #include "elem.cuh"
 #include "segmented.cuh"
@@ -282,7 +283,9 @@ __device__ __noinline__ uint32_t radix_select(const float* buf, int m, unsigned 
     int known = 0;
     uint32_t prefix = 0;
     if (filter) {
-      const uint32_t lo = ukey(a) + 1, hi = ukey(b);
+      // (a, b] under IEEE comparison on keys: a zero end takes the key of +0 (x > -0 and
+      // x > +0 both exclude the zeros, x <= -0 and x <= +0 both include them)
+      const uint32_t lo = ukey(a == 0.f ? 0.f : a) + 1, hi = ukey(b == 0.f ? 0.f : b);
       const uint32_t diff = lo ^ hi;
       known = diff == 0 ? 32 : __clz(diff);
       prefix = known == 0 ? 0u : (known == 32 ? hi : (hi >> (32 - known)));
@@ -368,6 +371,8 @@ struct SegShared {
   double dF, sum;
   int it, use_bisect, stalled, compact, first, phase, how, passes;
   int zglob;          // 1: the compacted bracket is in this CTA's device-memory region
+  int lean;           // 1: a learned start ran its lean pass on this segment
+  float pa, pb;       // its proposed bracket
 };
 
 // Sum of the elements below q and their number, over this thread's share of buf[0, m)
@@ -439,6 +444,79 @@ __device__ __noinline__ void seg_cut_pass(const float* __restrict__ xs, const Ge
     cta_stream<B>(xs, g, f);
   }
   acc.lt = lt; acc.le = le; acc.xa = xa; acc.xb = xb; acc.S = S; acc.sle = sle;
+}
+
+// Learned starting bracket for the median of a large segment (the proposal of the
+// single-array select, computed by this CTA): 1024 strided samples sorted on their keys by
+// a shared-memory bitonic network, the sketch features, the network forward, and the
+// bracket (*pa, *pb].  `scratch` is shared memory of at least 3.5 * kSample floats.
+// Returns false (in every thread) when a sample is not finite or the bracket is not a
+// finite a < b.
+template <int B>
+__device__ __noinline__ bool seg_propose(const float* __restrict__ xs, long long n, const float* __restrict__ W,
+                                         float* scratch, float* pa, float* pb) {
+  __shared__ double s_mu, s_sd;
+  __shared__ int s_ok;
+  uint32_t* kb = reinterpret_cast<uint32_t*>(scratch);
+  double* sv = reinterpret_cast<double*>(scratch + kSample);
+  float* f = scratch + 3 * kSample;
+  float* h1 = f + 64;
+  float* h2 = h1 + kHid;
+  float* o = h2 + kHid;
+  const long long stride = n / kSample;
+  bool bad = false;
+  for (int i = threadIdx.x; i < kSample; i += B) {
+    const float v = xs[i * stride];
+    bad |= !(fabsf(v) <= FLT_MAX);
+    kb[i] = ukey(v);
+  }
+  if (__syncthreads_or(bad)) return false;
+  for (int k = 2; k <= kSample; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int q = threadIdx.x; q < kSample / 2; q += B) {
+        const int i = 2 * q - (q & (j - 1));   // the pair (i, i + j), bit j of i clear
+        const uint32_t u = kb[i], v = kb[i + j];
+        if ((u > v) == ((i & k) == 0)) {
+          kb[i] = v;
+          kb[i + j] = u;
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < kSample; i += B) sv[i] = (double)ukey_value(kb[i], 0.f);
+  __syncthreads();
+  if (threadIdx.x < 32) sketch_features_warp(sv, f, &s_mu, &s_sd);
+  __syncthreads();
+  mlp_forward_rows<B / 32>(W, f, h1, h2, o);
+  if (threadIdx.x == 0) {
+    double a, b;
+    const bool valid = proposal_from_outputs(o, s_mu, s_sd, &a, &b);
+    const float fa = (float)a, fb = (float)b;
+    s_ok = valid && fa < fb && fabsf(fa) <= FLT_MAX && fabsf(fb) <= FLT_MAX;
+    *pa = fa;
+    *pb = fb;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The lean first pass of a learned start: NaN count, #(x <= a), and (a, b] compacted into
+// zb (capacity zcap, counter *cnt, which also gives #(a < x <= b)).
+struct SegLeanAcc {
+  unsigned int nnan, le_a;
+};
+template <int B>
+__device__ __noinline__ void seg_lean_pass(const float* __restrict__ xs, const Geometry<float>& g, float a, float b,
+                                           float* zb, unsigned int zcap, unsigned int* cnt, SegLeanAcc& acc) {
+  unsigned int nnan = 0, le_a = 0;
+  auto f = [&](float v) {
+    nnan += (v != v);
+    le_a += (v <= a);
+  };
+  auto keep = [&](float v) { return (v > a) & (v <= b); };
+  cta_stream_compact<B>(xs, g, f, keep, zb, zcap, cnt);
+  acc.nnan = nnan;
+  acc.le_a = le_a;
 }
 
 template <int B, int CAP, bool LTS>
@@ -519,8 +597,36 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
       continue;
     }
 
+    // ---- large segment, learned start (medians, with a model): proposal and lean pass ----
+    if (tid == 0) { sh.phase = 0; sh.lean = 0; sh.zcnt = 0; }
+    __syncthreads();
+    if (!LTS && A.W != nullptr && A.zg != nullptr && n >= kLearnMinN && k == (n + 1) / 2 &&
+        seg_propose<B>(xs, n, A.W, zb, &sh.pa, &sh.pb)) {
+      SegLeanAcc la;
+      seg_lean_pass<B>(xs, g, sh.pa, sh.pb, A.zg + (long long)blockIdx.x * A.zg_cap, (unsigned int)A.zg_cap,
+                       &sh.zcnt, la);
+      Sum6 v6;
+      v6.u[0] = la.nnan; v6.u[1] = la.le_a; v6.u[2] = v6.u[3] = v6.u[4] = 0; v6.d = 0.0;
+      const Sum6 r6 = cta_sum6<B>(v6, sh.sum6);   // also orders the appends before the finish
+      if (tid == 0) {
+        const long long le_a = (long long)r6.u[1], zc = (long long)sh.zcnt;
+        sh.lean = 1;
+        sh.passes = 1;
+        sh.how = GBS_HOW_NONE;
+        if (r6.u[0] > 0) {
+          sh.phase = 3;
+          sh.result = NAN;
+        } else if (le_a < k && k <= le_a + zc && zc <= (long long)A.zg_cap) {
+          // the proposal holds the median and all of (a, b] is compacted: the finish
+          sh.phase = 2;
+          sh.a0 = sh.pa; sh.b0 = sh.pb; sh.cle_a0 = le_a; sh.zglob = 1; sh.sum = 0.0;
+        }
+      }
+      __syncthreads();
+    }
+
     // ---- large segment: pass 0 (extremes, sum, non-finite and -0 counts) ----
-    {
+    if (sh.phase == 0) {
       const float sig0 = A.sigma_stats;
       float x0 = 0.f;
       if (tid < n && Ops<float>::is_finite(xs[tid])) x0 = xs[tid];
@@ -547,7 +653,7 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
         sh.m = bm; sh.M = bM;
         sh.n_nan = (long long)r6.u[0]; sh.nneg = (long long)r6.u[1]; sh.npos = (long long)r6.u[2];
         sh.nnz = (long long)r6.u[3]; sh.sum = r6.d;
-        sh.passes = 1; sh.it = 0; sh.use_bisect = 0; sh.stalled = 0; sh.first = 0; sh.phase = 0;
+        sh.passes = 1 + sh.lean; sh.it = 0; sh.use_bisect = 0; sh.stalled = 0; sh.first = 0; sh.phase = 0;
         sh.how = GBS_HOW_NONE; sh.clt_res = -1; sh.cle_res = -1; sh.result = 0.f;
         if (sh.n_nan > 0) {
           sh.phase = 3; sh.result = NAN;
@@ -798,6 +904,8 @@ gbs_status seg_launch(gbs_ctx* c, const SegLaunch& L, int variant, cudaStream_t 
   A.seg_passes = L.seg_passes;
   A.k_const = L.k_const; A.k2_const = L.k2_const;
   A.kk2 = L.kk2; A.out2 = L.out2; A.outsum = L.outsum; A.flags = L.flags;
+  // learned starting brackets for the medians (gbs_config.use_learned with a model loaded)
+  A.W = (!lts && c->cfg.use_learned && c->model_loaded) ? c->model : nullptr;
   // pass-0 sums: a thread adds at most ceil(1e6 / threads) * ... terms of a segment; the
   // scale keeps any float32 partial finite for segments up to 2^31 elements
   A.sigma_stats = std::ldexp(1.0f, -24);

@@ -30,6 +30,8 @@ struct SegArgs {
   // brackets too large for shared memory; nullptr: shared memory only
   float* zg;
   int zg_cap;
+  // bracket-proposal network (float32 parameters) for learned starts of the medians, or nullptr
+  const float* W;
 };
 
 struct SegLaunch {

@@ -3,6 +3,8 @@
 Every segment's result must be bit-identical to oracle.select.select_kth on that
 segment.  Calls go through the C-ABI (ctypes binding).
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -132,6 +134,50 @@ def test_segmented_brackets_compacted_in_device_memory(ctx):
         assert np.array_equal(bits(got), bits(expect(x, off, k))), frac
     passes = ctx.segmented_passes(len(sizes))
     assert all(2 <= p <= 40 for p in passes), passes
+
+
+MODEL = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1104_2732_gb300",
+                     "bracket_model.bin")
+
+
+@pytest.mark.skipif(not os.path.exists(MODEL), reason="no trained model in the package")
+def test_segmented_learned_medians(lib):
+    """Medians with learned starting brackets (proposal in the CTA, lean first pass,
+    straight to the finish when the check holds): identical to the oracle, fewer passes on
+    the large segments than the plain start, and a NaN in a large segment still reported."""
+    def gen(i, n, rng):
+        fam = synth.HEAVY_FAMILIES[i % 4]
+        return synth.heavy_mixture(fam, n, seed=int(rng.integers(1 << 30))) * np.float32(10 ** rng.uniform(-2, 2))
+    sizes = [70_000, 300_000, 1_000_000, 5_000, 131_072, 65_536, 800_001, 40_000, 450_000]
+    x, off = make_batch(sizes, seed=82, gen=gen)
+    plain = lib.Context()
+    learned = lib.Context()
+    learned.load_bracket_model(MODEL)
+    learned.set_config(use_learned=1)
+    try:
+        want = expect(x, off)
+        got_p = run(plain, x, off)
+        got_l = run(learned, x, off)
+        assert np.array_equal(bits(got_l), bits(want))
+        assert np.array_equal(bits(got_p), bits(want))
+        big = np.array(sizes) >= 65_536
+        pp = np.array(plain.segmented_passes(len(sizes)))[big]
+        pl = np.array(learned.segmented_passes(len(sizes)))[big]
+        assert pl.mean() < pp.mean(), (pl, pp)
+        # explicit ranks other than the median take the plain start
+        k = np.array([max(1, n // 3) for n in sizes], dtype=np.int64)
+        assert np.array_equal(bits(run(learned, x, off, k)), bits(expect(x, off, k)))
+        y = x.copy()
+        y[off[2] + 12345] = np.nan
+        got = run(learned, y, off)
+        with pytest.raises(lib.GbsError) as ei:
+            learned.last_stats()
+        assert ei.value.status == lib.GBS_ENAN
+        assert np.isnan(got[2])
+        assert np.array_equal(bits(np.delete(got, 2)), bits(np.delete(want, 2)))
+    finally:
+        plain.close()
+        learned.close()
 
 
 def test_segmented_invalid_segments_are_flagged(ctx, lib):
