@@ -7,6 +7,7 @@ Cases (inputs from ``synth``; every case holds at most a few GB on the device):
   select64   the same for the 2^26 float64 mixture
   learned    median of the 2^27 mixture starting from the shipped bracket model
   segmented  the 4096-array batch (seed 5), medians, R batched calls
+  segmented_learned  the same batch with learned starting brackets (shipped model)
   lms        LMS/LTS objectives, n = 1e6, p = 8, 512 candidates (seeds 6, 7), TF32x3 + batched
   lms_fused  the same objectives for 2048 candidates with the residuals recomputed per pass
   propose    the bracket-proposal kernel on a 2^24 array, R calls
@@ -25,7 +26,8 @@ sys.path.insert(0, os.path.dirname(HERE))
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["select", "select64", "learned", "segmented", "lms", "lms_fused", "propose"])
+    ap.add_argument("case", choices=["select", "select64", "learned", "segmented", "segmented_learned", "lms",
+                                     "lms_fused", "propose"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
     args = ap.parse_args()
@@ -54,11 +56,15 @@ def main():
         def rep():
             for k in ks:
                 ctx.select_kth(x, k, out=out)
-    elif case == "segmented":
+    elif case in ("segmented", "segmented_learned"):
         xh, off = synth.segmented(4096, seed=5)
         x = torch.from_numpy(xh).cuda()
         offs = torch.from_numpy(off).cuda()
         out = torch.empty(4096, device="cuda")
+        ctx.set_segmented_variant(0)
+        if case == "segmented_learned":
+            ctx.load_bracket_model(os.path.join(HERE, "bracket_model.bin"))
+            ctx.set_config(use_learned=1)
 
         def rep():
             ctx.select_segmented(x, offs, out=out)
