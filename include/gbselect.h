@@ -63,7 +63,7 @@ enum {
 typedef struct {
     int64_t cap;         /* the pass that sees a bracket of <= cap elements compacts it and
                             the cutting plane stops (Sec. 3: "the algorithm stops when the
-                            cost of its iteration outweighs the benefit"); 0 = max(n/16, 4096) */
+                            cost of its iteration outweighs the benefit"); 0 = max(n/8, 4096) */
     int32_t maxit;       /* cutting-plane iterations before compaction is forced; 0 = 64 */
     int32_t blocks_per_sm; /* CTAs per SM of the persistent kernel; 0 = 1 below 32 MiB of
                               input, else 2 (at most what fits) */

@@ -1034,7 +1034,7 @@ gbs_status launch_select(gbs_ctx* c, const T* x, long long n, long long k, T* ou
   A.x = x; A.n = n; A.k = k; A.out = out; A.mode = mode;
   A.maxit = c->cfg.maxit > 0 ? c->cfg.maxit : 64;
   if (A.maxit > kMaxIt) A.maxit = kMaxIt;
-  A.cap = c->cfg.cap > 0 ? c->cfg.cap : std::max<long long>(n / 16, 4096);
+  A.cap = c->cfg.cap > 0 ? c->cfg.cap : std::max<long long>(n / 8, 4096);
   A.a_eval = a; A.t_eval = t;
   A.sigma_stats = stats_sigma<T>(n, grid);
   A.ctrl = c->ctrl; A.part = c->part; A.spart = c->spart; A.ghist = c->ghist;
