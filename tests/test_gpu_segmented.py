@@ -180,6 +180,47 @@ def test_segmented_learned_medians(lib):
         learned.close()
 
 
+def _altered_model(path, centre_shift=0.0, log_width_shift=0.0):
+    """A copy of the shipped model with the output biases moved (file layout: 8-byte
+    magic, 5 u32 header words, u64 Adam step, then the parameters; the last two are the
+    biases of the centre c and of the log half-width omega)."""
+    raw = bytearray(open(MODEL, "rb").read())
+    n_params = int(np.frombuffer(bytes(raw[8:28]), dtype=np.uint32)[4])
+    params = np.frombuffer(bytes(raw[36:36 + 4 * n_params]), dtype=np.float32).copy()
+    params[-2] += np.float32(centre_shift)
+    params[-1] += np.float32(log_width_shift)
+    raw[36:36 + 4 * n_params] = params.tobytes()
+    with open(path, "wb") as fh:
+        fh.write(bytes(raw))
+    return path
+
+
+@pytest.mark.skipif(not os.path.exists(MODEL), reason="no trained model in the package")
+@pytest.mark.parametrize("shift", [(20.0, 0.0), (0.0, 12.0)], ids=["missed", "too-wide"])
+def test_segmented_learned_fallbacks(lib, tmp_path, shift):
+    """Proposals that miss the median (centre moved 20 sigma) take the plain path after the
+    lean pass; proposals holding the whole segment finish from a device-memory bracket
+    when it fits the CTA's share and otherwise take the plain path.  Results identical to
+    the oracle either way."""
+    def gen(i, n, rng):
+        return (rng.standard_normal(n) * 3.0 + rng.uniform(-5, 5)).astype(np.float32)
+    sizes = [20_000, 150_000, 600_000, 13_000, 260_000]
+    x, off = make_batch(sizes, seed=83, gen=gen)
+    c = lib.Context()
+    try:
+        c.load_bracket_model(_altered_model(str(tmp_path / "m.bin"), *shift))
+        c.set_config(use_learned=1)
+        got = run(c, x, off)
+        assert np.array_equal(bits(got), bits(expect(x, off)))
+        passes = np.array(c.segmented_passes(len(sizes)))
+        large = np.array(sizes) > c.segmented_variant()["smem_cap"]   # the others stay in shared memory
+        assert large.sum() >= 3
+        if shift[0] != 0.0:
+            assert (passes[large] >= 3).all(), passes   # lean pass + pass 0 + at least one cut
+    finally:
+        c.close()
+
+
 def test_segmented_invalid_segments_are_flagged(ctx, lib):
     x, off = make_batch([10, 0, 10], seed=75)
     got = run(ctx, x, off)
