@@ -70,7 +70,12 @@ typedef struct {
     int32_t use_learned; /* 1 = start from the bracket proposed by the loaded model (if any);
                             a proposed bracket that passes its count check and holds at most
                             max(cap, n/8) elements goes straight to the finish */
-    int32_t reserved[7];
+    int32_t lms_start;   /* fused LMS/LTS objectives (n >= 65536): 0 = each candidate starts from
+                            a bracket proposed by order statistics of its squared residuals on
+                            8192 sampled rows and checked by counts in the first pass (a
+                            candidate whose check fails goes to the materialising form);
+                            1 = start from the extremes (Algorithm 1, step 0) */
+    int32_t reserved[6];
 } gbs_config;
 
 /* Per-call record of the last selection on a context (host copy). */

@@ -33,7 +33,7 @@ class GbsError(RuntimeError):
 # ------------------------------------------------------------------ structures
 class gbs_config(C.Structure):
     _fields_ = [("cap", C.c_int64), ("maxit", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("use_learned", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("use_learned", C.c_int32), ("lms_start", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class gbs_run_stats(C.Structure):
@@ -204,7 +204,7 @@ class Context:
         cfg = gbs_config()
         _check(gbs_get_config(self._h, C.byref(cfg)), "gbs_get_config")
         return {"cap": cfg.cap, "maxit": cfg.maxit, "blocks_per_sm": cfg.blocks_per_sm,
-                "use_learned": cfg.use_learned}
+                "use_learned": cfg.use_learned, "lms_start": cfg.lms_start}
 
     def reserve(self, n, elem_bytes=4):
         _check(gbs_reserve(self._h, int(n), int(elem_bytes)), "gbs_reserve")

@@ -49,8 +49,10 @@ constexpr long long kFCap = 49152;     // compaction buffer per candidate (eleme
 constexpr int kFVariant = 2;           // segmented variant of the finish (1024 threads, 49152 in smem)
 constexpr int kRing = 16;              // cost passes whose per-lane counts are kept
 
-enum { kFStats = 0, kFCost = 1, kFWrite = 3 };
-enum { kPhIter = 0, kPhDone = 1, kPhCompact = 2, kPhFallback = 3, kPhFinish = 4 };
+enum { kFStats = 0, kFCost = 1, kFCheck = 2, kFWrite = 3 };
+enum { kPhIter = 0, kPhDone = 1, kPhCompact = 2, kPhFallback = 3, kPhFinish = 4, kPhCheck = 5 };
+constexpr int kSampleRows = 8192;           // rows of the sampled start
+constexpr long long kSampleMinN = 65536;    // smaller problems start from the extremes
 
 struct FusedCand {
   float a, b, t;        // bracket (a, b] and the point of the next cost pass
@@ -184,6 +186,7 @@ __device__ __forceinline__ void fused_item(const FusedArgs& A, long long item, f
       const FusedCand& fc = A.cand[c];
       if (MODE == kFStats) act = true;
       if (MODE == kFCost) act = fc.phase == kPhIter;
+      if (MODE == kFCheck) act = fc.phase == kPhCheck;
       if (MODE == kFWrite) act = fc.phase == kPhCompact;
       pa[j] = fc.a; pt[j] = fc.t; pb[j] = fc.b;
       nsig[j] = -fc.sigma; tsig[j] = fc.t * fc.sigma; fx[j] = fc.fx;
@@ -281,6 +284,11 @@ __device__ __forceinline__ void fused_item(const FusedArgs& A, long long item, f
             nf[j] += (valid && !ok) ? 1u : 0u;
           } else if (MODE == kFCost) {
             core_le(s, pa[j], pt[j], nsig[j], tsig[j], le[j], S[j]);
+          } else if (MODE == kFCheck) {   // #(s <= a), #(s <= b) of a proposed bracket
+            const bool valid = full || (r0 + lr + (e & 1)) < r_end;
+            nf[j] += (valid && !(s <= FLT_MAX)) ? 1u : 0u;
+            le[j] += (s <= pa[j]) ? 1u : 0u;
+            lea[j] += (s <= pb[j]) ? 1u : 0u;
           } else {
             // below the bracket: the stage's partial sum; inside: the lane's next slot
             const bool below = s <= pa[j];
@@ -305,12 +313,15 @@ __device__ __forceinline__ void fused_item(const FusedArgs& A, long long item, f
     __syncthreads();
   }
 
-  if (MODE == kFCost) {           // each lane's own #(s <= t), for the compaction offsets
+  if (MODE == kFCost || MODE == kFCheck) {   // each lane's own counts, for the compaction offsets
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int c = j ? c1 : c0;
-      if (c < A.C && (j ? act1 : act0))
+      if (c < A.C && (j ? act1 : act0)) {
         A.lring[(((long long)A.ring_slot * A.C + c) * A.nrc + rc) * 4 + q] = le[j];
+        if (MODE == kFCheck)   // #(s <= b) in the next slot
+          A.lring[(((long long)(A.ring_slot + 1) * A.C + c) * A.nrc + rc) * 4 + q] = lea[j];
+      }
     }
   }
   double dsum[2];
@@ -349,6 +360,10 @@ __device__ __forceinline__ void fused_item(const FusedArgs& A, long long item, f
         if (le[j]) atomicAdd(&T.le, (unsigned long long)le[j]);
         const unsigned long long sf = __double2ull_rn(ldexp((double)S[j], fx[j]));
         if (sf) atomicAdd(&T.sfix, sf);
+      } else if (MODE == kFCheck) {
+        if (nf[j]) atomicAdd(&T.nonfinite, (unsigned long long)nf[j]);
+        if (le[j]) atomicAdd(&T.le, (unsigned long long)le[j]);
+        if (lea[j]) atomicAdd(&T.kept, (unsigned long long)lea[j]);
       } else {
         if (lea[j]) atomicAdd(&T.le_a, (unsigned long long)lea[j]);
         if (kept[j]) atomicAdd(&T.kept, (unsigned long long)kept[j]);
@@ -467,6 +482,22 @@ __global__ void fused_step_kernel(StepArgs P) {
         const int prev = s.use_bisect;
         s.use_bisect = (!prev) && ((double)npop > 0.75 * (double)pop);
         s.stalled = ((double)npop > 0.875 * (double)pop) ? s.stalled + 1 : 0;
+        fused_next(s, P);
+      }
+    }
+  } else if (MODE == kFCheck) {
+    // a proposed bracket holds both ranks when #(s <= a) < k_lo and k_hi <= #(s <= b);
+    // then it is the starting bracket (Phi(b) - Phi(a) unknown: the first step bisects)
+    if (s.phase == kPhCheck) {
+      const long long la = (long long)T.le, lb = (long long)T.kept;
+      if (T.nonfinite > 0 || !(la < P.k_lo && P.k_hi <= lb)) {
+        s.phase = kPhFallback;   // counted by the step after the write pass
+      } else {
+        s.phase = kPhIter;
+        s.it = 0; s.use_bisect = 0; s.stalled = 0; s.dfv = 0; s.dF = 0.0;
+        s.cle_a = la; s.cle_b = lb; s.clt_b = lb;   // #(s <= b) stands for #(s < b)
+        s.pa_pass = P.pass; s.pb_pass = P.pass + 1;
+        s.mn = 0.f;
         fused_next(s, P);
       }
     }
@@ -648,7 +679,46 @@ template <int KS>
 gbs_status launch_pass(int mode, const FusedArgs& A, int num_sms, cudaStream_t s) {
   if (mode == kFStats) return launch_mode<KS, kFStats>(A, num_sms, s);
   if (mode == kFCost) return launch_mode<KS, kFCost>(A, num_sms, s);
+  if (mode == kFCheck) return launch_mode<KS, kFCheck>(A, num_sms, s);
   return launch_mode<KS, kFWrite>(A, num_sms, s);
+}
+
+// Squared residuals of every candidate on kSampleRows rows spread evenly over X (row
+// (j * n) / ns), candidate-major; a non-finite square is stored as +inf.  float32 FMAs:
+// the sample only proposes brackets, which the check pass then counts on the fused pass's
+// own residuals.
+__global__ void lms_sample_kernel(const float* __restrict__ X, const float* __restrict__ y, long long n, int p,
+                                  const float* __restrict__ theta, int C, int ns, float* __restrict__ out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)C * ns) return;
+  const int c = (int)(idx / ns), j = (int)(idx - (long long)c * ns);
+  const long long i = (long long)j * n / ns;
+  float d = 0.f;
+  for (int q = 0; q < p; ++q) d = fmaf(X[i * p + q], theta[(long long)c * p + q], d);
+  const float r = y[i] - d;
+  const float sq = r * r;
+  out[idx] = sq <= FLT_MAX ? sq : INFINITY;
+}
+
+__global__ void lms_sample_offsets_kernel(long long* off, int C, int ns) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c <= C) off[c] = (long long)c * ns;
+}
+
+// The proposed brackets (lo[c], hi[c]] from the sample's order statistics (a rank below
+// the sample: -1, below every square; above it: FLT_MAX); a bracket that is not a finite
+// a < b sends its candidate to the fallback.
+__global__ void lms_propose_kernel(FusedCand* cand, int C, const float* lo, const float* hi, int lo_in, int hi_in) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  FusedCand s;
+  s.a = lo_in ? lo[c] : -1.f;
+  s.b = hi_in ? hi[c] : FLT_MAX;
+  s.t = 0.f; s.sigma = 1.f; s.fx = kSFixBits;
+  s.it = 0; s.use_bisect = 0; s.stalled = 0; s.dfv = 0;
+  s.cle_a = s.clt_b = s.cle_b = 0; s.dF = 0.0; s.mn = 0.f; s.pa_pass = s.pb_pass = -1;
+  s.phase = (s.a < s.b && s.b <= FLT_MAX) ? kPhCheck : kPhFallback;
+  cand[c] = s;
 }
 
 size_t up256f(size_t v) { return (v + 255) / 256 * 256; }
@@ -695,6 +765,8 @@ extern "C" gbs_status gbs_lms_lts_fused_f32(gbs_ctx* c, const float* X, const fl
   const size_t o_list = o; o = up256f(o + sizeof(int) * (size_t)C);
   const size_t o_q = o; o = up256f(o + sizeof(float) * (size_t)C);
   const size_t o_flags = o; o = up256f(o + sizeof(int) * (size_t)C);
+  const size_t o_plo = o; o = up256f(o + sizeof(float) * (size_t)C);   // sampled start: proposed ends
+  const size_t o_phi = o; o = up256f(o + sizeof(float) * (size_t)C);
   const size_t o_z = o; o = up256f(o + sizeof(float) * (size_t)C * kFCap);
   const size_t o_zc = o; o = up256f(o + sizeof(float) * (size_t)C * kFCap);
   const size_t o_y = o; o = up256f(o + sizeof(float) * (size_t)n);
@@ -789,11 +861,51 @@ extern "C" gbs_status gbs_lms_lts_fused_f32(gbs_ctx* c, const float* X, const fl
     return KS == 1 ? launch_pass<1>(mode, A, c->num_sms, strm) : launch_pass<2>(mode, A, c->num_sms, strm);
   };
   int npass = 0;
-  // statistics pass and the starting brackets
-  if ((st = pass(kFStats)) != GBS_OK) return st;
-  ++npass;
-  fused_step_kernel<kFStats><<<sgrid, 256, 0, strm>>>(P);
-  if ((st = check()) != GBS_OK) return st;
+  int first_cost = 0;   // index of the first cost pass (ring slot: index % kRing)
+  if (c->cfg.lms_start == 0 && n >= kSampleMinN) {
+    // sampled start: order statistics of the candidates' squares on kSampleRows rows
+    // propose (a, b] around both ranks (3.5 binomial standard deviations and 2 ranks of
+    // margin on each side: at the medians of 1e6 rows the bracket holds about 3.9 % of
+    // them, inside the compaction buffer, and a side misses with probability ~2e-4); the
+    // check pass counts #(s <= a) and #(s <= b) exactly
+    const int ns = kSampleRows;
+    const double pl = (double)P.k_lo / (double)n, ph = (double)P.k_hi / (double)n;
+    const long long jl = (long long)std::floor(ns * pl - 3.5 * std::sqrt(ns * pl * (1.0 - pl))) - 2;
+    const long long jh = (long long)std::ceil(ns * ph + 3.5 * std::sqrt(ns * ph * (1.0 - ph))) + 2;
+    const int lo_in = jl >= 1, hi_in = jh <= ns;
+    float* plo = reinterpret_cast<float*>(b + o_plo);
+    float* phi = reinterpret_cast<float*>(b + o_phi);
+    float* rs = zcat;   // C x ns squares (the finish's buffer, free until the gather)
+    lms_sample_kernel<<<(unsigned int)(((long long)C * ns + 255) / 256), 256, 0, strm>>>(X, y, n, p, theta, C, ns,
+                                                                                       rs);
+    lms_sample_offsets_kernel<<<(unsigned int)((C + 1 + 255) / 256), 256, 0, strm>>>(off, C, ns);
+    if ((st = check()) != GBS_OK) return st;
+    // both order statistics from one load of each candidate's sample: the segmented
+    // select's two-rank mode (its trimmed sums and flags land in buffers the finish fills
+    // later)
+    SegLaunch L;
+    if ((st = seg_attach_workspace(c, C, &L)) != GBS_OK) return st;
+    L.x = rs; L.off = off; L.S = C; L.kk = nullptr; L.ctrl = c->ctrl; L.mask = nullptr; L.kk2 = nullptr;
+    L.k_const = std::max<long long>(jl, 1); L.out = plo;
+    L.k2_const = std::min<long long>(jh, ns); L.out2 = phi;
+    L.outsum = P.below; L.flags = flags;
+    if ((st = seg_launch(c, L, 0, strm)) != GBS_OK) return st;
+    lms_propose_kernel<<<sgrid, 256, 0, strm>>>(A.cand, C, plo, phi, lo_in, hi_in);
+    // check pass: ring slots 0 (#(s <= a)) and 1 (#(s <= b))
+    A.ring_slot = 0;
+    P.pass = 0;
+    if ((st = pass(kFCheck)) != GBS_OK) return st;
+    ++npass;
+    fused_step_kernel<kFCheck><<<sgrid, 256, 0, strm>>>(P);
+    if ((st = check()) != GBS_OK) return st;
+    first_cost = 2;
+  } else {
+    // statistics pass and the starting brackets
+    if ((st = pass(kFStats)) != GBS_OK) return st;
+    ++npass;
+    fused_step_kernel<kFStats><<<sgrid, 256, 0, strm>>>(P);
+    if ((st = check()) != GBS_OK) return st;
+  }
   // cutting-plane passes until every candidate is ready to compact
   unsigned int h_cnt[2] = {0u, 0u};
   for (int it = 0; it <= P.maxit + 1; ++it) {
@@ -802,8 +914,8 @@ extern "C" gbs_status gbs_lms_lts_fused_f32(gbs_ctx* c, const float* X, const fl
       return GBS_ECUDA;
     if (h_cnt[0] == 0) break;
     if (cudaMemsetAsync(P.counters, 0, sizeof(unsigned int), strm) != cudaSuccess) return GBS_ECUDA;
-    A.ring_slot = it % kRing;
-    P.pass = it;
+    A.ring_slot = (first_cost + it) % kRing;
+    P.pass = first_cost + it;
     if ((st = pass(kFCost)) != GBS_OK) return st;
     ++npass;
     fused_step_kernel<kFCost><<<sgrid, 256, 0, strm>>>(P);

@@ -562,11 +562,34 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
 
     if (n <= CAP) {
       // ---- small segment: load once, radix select in shared memory ----
+      // load: the scalar head and tail, and the 16-byte body four vectors per thread in flight
       unsigned int nan_here = 0;
-      for (long long i = tid; i < n; i += B) {
-        const float v = xs[i];
+      if (tid < g.head) {
+        const float v = xs[tid];
         nan_here += (v != v);
-        zb[i] = v;
+        zb[tid] = v;
+      }
+      if (tid < n - g.tail0) {
+        const float v = xs[g.tail0 + tid];
+        nan_here += (v != v);
+        zb[g.tail0 + tid] = v;
+      }
+      {
+        const float4* xv = reinterpret_cast<const float4*>(xs + g.head);
+        float* zh = zb + g.head;
+        auto put = [&](long long q, const float4 r) {
+          nan_here += (r.x != r.x) + (r.y != r.y) + (r.z != r.z) + (r.w != r.w);
+          zh[4 * q] = r.x; zh[4 * q + 1] = r.y; zh[4 * q + 2] = r.z; zh[4 * q + 3] = r.w;
+        };
+        long long q = tid;
+        for (; q + 3 * B < g.nv; q += 4 * B) {
+          float4 r[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) r[u] = __ldcs(xv + q + u * B);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) put(q + u * B, r[u]);
+        }
+        for (; q < g.nv; q += B) put(q, __ldcs(xv + q));
       }
       Sum6 v6;
       v6.u[0] = nan_here; v6.u[1] = v6.u[2] = v6.u[3] = v6.u[4] = 0; v6.d = 0.0;

@@ -212,6 +212,29 @@ def test_fused_ranks_far_apart_use_the_batched_form(ctx):
     check_against_oracle(lms.cpu().numpy(), lts.cpu().numpy(), X, y, th, k, h)
 
 
+def test_fused_sampled_start_matches_plain_start(ctx):
+    """Brackets proposed by the candidates' order statistics on 8192 sampled rows (checked
+    by counts in the first pass) against the start from the extremes: the same LMS values
+    bit for bit (both select from the same recomputed residuals), LTS within rounding of
+    the sum below the bracket, fewer passes, and both within the oracle's bound."""
+    n, p, C = 300_000, 8, 256
+    X, y, th = problem(n, p, C, seed=96)
+    Xt, yt, tt = to_dev(X, y, th)
+    k, h = (n + 1) // 2, (n + p + 1) // 2
+    try:
+        ctx.set_config(lms_start=1)
+        lp, tp, pp = ctx.lms_lts_fused(Xt, yt, tt, k=k, h=h)
+        ctx.set_config(lms_start=0)
+        ls, ts, ps = ctx.lms_lts_fused(Xt, yt, tt, k=k, h=h)
+    finally:
+        ctx.set_config(lms_start=0)
+    lp, tp, ls, ts = (a.cpu().numpy() for a in (lp, tp, ls, ts))
+    assert np.array_equal(lp.view(np.uint32), ls.view(np.uint32))
+    assert np.all(np.abs(ts - tp) <= 1e-6 * np.abs(tp))
+    assert ps < pp, (ps, pp)
+    check_against_oracle(ls, ts, X, y, th, k, h, [0, 17, 255])
+
+
 def test_fused_nan_row_matches_batched_form(ctx):
     n, p, C = 5000, 8, 6
     X, y, th = problem(n, p, C, seed=99)
