@@ -312,7 +312,8 @@ def bench_segmented(gbs, ctx, torch, np, args):
 def bench_lms(gbs, ctx, torch, np, args):
     """LMS / LTS of 2048 elemental candidates on n = 1e6, p = 8 (30% contaminated rows), in
     three forms: fused (TF32 x 3 tensor-core residuals recomputed in every cutting-plane
-    pass, never written), materialised (TF32 x 3 residual matrix + batched trimmed-sum
+    pass, never written; brackets proposed from 8192 sampled rows, and for reference the
+    start from the extremes), materialised (TF32 x 3 residual matrix + batched trimmed-sum
     select) and plain (float32 CUDA-core residuals + one single-array select per
     candidate and rank).  The chosen form is the faster of the first two; relative errors
     of sampled candidates against the float64 oracle for every form."""
@@ -337,6 +338,12 @@ def bench_lms(gbs, ctx, torch, np, args):
 
     reps = max(3, min(20, args.steps // 5))
     fused_ms, (lms_f, lts_f, fused_passes) = timed(lambda: ctx.lms_lts_fused(Xt, yt, tt, k=k, h=h), reps)
+    # the same fused form started from the extremes (Algorithm 1, step 0) instead of the
+    # sampled brackets
+    ctx.set_config(lms_start=1)
+    fx_ms, (lms_x, _, fx_passes) = timed(lambda: ctx.lms_lts_fused(Xt, yt, tt, k=k, h=h), reps)
+    ctx.set_config(lms_start=0)
+    fx_same = bool(torch.equal(lms_x.view(torch.int32), lms_f.view(torch.int32)))
     mat_ms, (lms_m, lts_m) = timed(lambda: ctx.lms_lts(Xt, yt, tt, k=k, h=h, precision=1, batched=True), reps)
     plain_ms, (lms_p, lts_p) = timed(lambda: ctx.lms_lts(Xt, yt, tt, k=k, h=h, precision=0, batched=False), 1)
     # the residual kernel alone (materialised form): bytes written against HBM
@@ -363,7 +370,9 @@ def bench_lms(gbs, ctx, torch, np, args):
     return {
         "workload": "LMS/LTS, n=1e6, p=8, 30% contaminated rows, 2048 elemental candidates, k=(n+1)/2, h=(n+p+1)/2",
         "metric": "candidates/s", "value": C / (chosen_ms * 1e-3), "ms": chosen_ms, "chosen_form": chosen,
-        "fused_ms": fused_ms, "fused_passes": fused_passes, "materialised_ms": mat_ms,
+        "fused_ms": fused_ms, "fused_passes": fused_passes,
+        "fused_extremes_start": {"ms": fx_ms, "passes": fx_passes, "lms_identical": fx_same},
+        "materialised_ms": mat_ms,
         "plain_value": C / (plain_ms * 1e-3), "plain_ms": plain_ms, "speedup_vs_plain": plain_ms / chosen_ms,
         "max_rel_err_vs_float64": {**{f"lms_{kk}": v[0] for kk, v in err.items()},
                                    **{f"lts_{kk}": v[1] for kk, v in err.items()},
