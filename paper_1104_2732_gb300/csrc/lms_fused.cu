@@ -683,19 +683,28 @@ gbs_status launch_pass(int mode, const FusedArgs& A, int num_sms, cudaStream_t s
   return launch_mode<KS, kFWrite>(A, num_sms, s);
 }
 
-// Squared residuals of every candidate on kSampleRows rows spread evenly over X (row
-// (j * n) / ns), candidate-major; a non-finite square is stored as +inf.  float32 FMAs:
-// the sample only proposes brackets, which the check pass then counts on the fused pass's
-// own residuals.
-__global__ void lms_sample_kernel(const float* __restrict__ X, const float* __restrict__ y, long long n, int p,
+// The ns sampled rows (row (j * n) / ns of X and y), gathered into xs [ns][p] and ys [ns].
+__global__ void lms_sample_rows_kernel(const float* __restrict__ X, const float* __restrict__ y, long long n, int p,
+                                       int ns, float* __restrict__ xs, float* __restrict__ ys) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)ns * (p + 1)) return;
+  const int j = (int)(idx / (p + 1)), q = (int)(idx - (long long)j * (p + 1));
+  const long long i = (long long)j * n / ns;
+  if (q < p) xs[(long long)j * p + q] = X[i * p + q];
+  else ys[j] = y[i];
+}
+
+// Squared residuals of every candidate on the sampled rows, candidate-major; a non-finite
+// square is stored as +inf.  float32 FMAs: the sample only proposes brackets, which the
+// check pass then counts on the fused pass's own residuals.
+__global__ void lms_sample_kernel(const float* __restrict__ xs, const float* __restrict__ ys, int p,
                                   const float* __restrict__ theta, int C, int ns, float* __restrict__ out) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)C * ns) return;
   const int c = (int)(idx / ns), j = (int)(idx - (long long)c * ns);
-  const long long i = (long long)j * n / ns;
   float d = 0.f;
-  for (int q = 0; q < p; ++q) d = fmaf(X[i * p + q], theta[(long long)c * p + q], d);
-  const float r = y[i] - d;
+  for (int q = 0; q < p; ++q) d = fmaf(xs[(long long)j * p + q], theta[(long long)c * p + q], d);
+  const float r = ys[j] - d;
   const float sq = r * r;
   out[idx] = sq <= FLT_MAX ? sq : INFINITY;
 }
@@ -767,6 +776,7 @@ extern "C" gbs_status gbs_lms_lts_fused_f32(gbs_ctx* c, const float* X, const fl
   const size_t o_flags = o; o = up256f(o + sizeof(int) * (size_t)C);
   const size_t o_plo = o; o = up256f(o + sizeof(float) * (size_t)C);   // sampled start: proposed ends
   const size_t o_phi = o; o = up256f(o + sizeof(float) * (size_t)C);
+  const size_t o_srow = o; o = up256f(o + sizeof(float) * (size_t)kSampleRows * (p + 1));   // sampled rows
   const size_t o_z = o; o = up256f(o + sizeof(float) * (size_t)C * kFCap);
   const size_t o_zc = o; o = up256f(o + sizeof(float) * (size_t)C * kFCap);
   const size_t o_y = o; o = up256f(o + sizeof(float) * (size_t)n);
@@ -876,8 +886,11 @@ extern "C" gbs_status gbs_lms_lts_fused_f32(gbs_ctx* c, const float* X, const fl
     float* plo = reinterpret_cast<float*>(b + o_plo);
     float* phi = reinterpret_cast<float*>(b + o_phi);
     float* rs = zcat;   // C x ns squares (the finish's buffer, free until the gather)
-    lms_sample_kernel<<<(unsigned int)(((long long)C * ns + 255) / 256), 256, 0, strm>>>(X, y, n, p, theta, C, ns,
-                                                                                       rs);
+    float* sx = reinterpret_cast<float*>(b + o_srow);
+    float* sy = sx + (size_t)ns * p;
+    lms_sample_rows_kernel<<<(unsigned int)(((long long)ns * (p + 1) + 255) / 256), 256, 0, strm>>>(X, y, n, p, ns,
+                                                                                                  sx, sy);
+    lms_sample_kernel<<<(unsigned int)(((long long)C * ns + 255) / 256), 256, 0, strm>>>(sx, sy, p, theta, C, ns, rs);
     lms_sample_offsets_kernel<<<(unsigned int)((C + 1 + 255) / 256), 256, 0, strm>>>(off, C, ns);
     if ((st = check()) != GBS_OK) return st;
     // both order statistics from one load of each candidate's sample: the segmented

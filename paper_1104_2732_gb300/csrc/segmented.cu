@@ -190,6 +190,11 @@ struct RadixState {
   unsigned long long rank;  // rank among the elements with that prefix (0 flags an inconsistency)
   unsigned int bucket;      // elements in the digit chosen last
   unsigned int cnt;         // append counter of the gather
+  // a second rank selected with the same histograms while both share a prefix
+  uint32_t prefix2;
+  unsigned long long rank2;
+  unsigned int bucket2;
+  int split;                // 1: the two ranks' digits differed in the last round
 };
 
 constexpr int kRadixV = 2;   // 16-byte loads in flight per thread in the radix sweeps
@@ -280,33 +285,53 @@ __device__ __forceinline__ void radix_gather(const float* buf, int m, bool filte
   radix_sweep<B>(buf, m, fn);
 }
 
-// Radix select inside the CTA: the rank-th (1-based) smallest, in totalOrder, of the
-// elements of buf[0, m) that lie in (a, b] (all of them when !filter).  Returns the
-// element's key.  8-bit digits from the highest bit where the bracket's keys differ.  When
-// buf is in device memory, zs (shared memory, cap elements, else nullptr) takes the
-// elements of the chosen digit once they fit, and the later rounds run there.
-template <int B>
-__device__ __noinline__ uint32_t radix_select(const float* buf, int m, unsigned long long rank, bool filter, float a,
-                                              float b, float* zs, int cap, RadixState& st) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) {
-    int known = 0;
-    uint32_t prefix = 0;
-    if (filter) {
-      // (a, b] under IEEE comparison on keys: a zero end takes the key of +0 (x > -0 and
-      // x > +0 both exclude the zeros, x <= -0 and x <= +0 both include them)
-      const uint32_t lo = ukey(a == 0.f ? 0.f : a) + 1, hi = ukey(b == 0.f ? 0.f : b);
-      const uint32_t diff = lo ^ hi;
-      known = diff == 0 ? 32 : __clz(diff);
-      prefix = known == 0 ? 0u : (known == 32 ? hi : (hi >> (32 - known)));
-    }
-    st.known = known;
-    st.prefix = prefix;
-    st.rank = rank;
+// Known leading key bits of (a, b] (all 32 when a single key lies in it); none without a
+// filter.  (a, b] under IEEE comparison on keys: a zero end takes the key of +0 (x > -0 and
+// x > +0 both exclude the zeros, x <= -0 and x <= +0 both include them).
+__device__ __forceinline__ void radix_known(bool filter, float a, float b, int* known, uint32_t* prefix) {
+  *known = 0;
+  *prefix = 0;
+  if (filter) {
+    const uint32_t lo = ukey(a == 0.f ? 0.f : a) + 1, hi = ukey(b == 0.f ? 0.f : b);
+    const uint32_t diff = lo ^ hi;
+    *known = diff == 0 ? 32 : __clz(diff);
+    *prefix = *known == 0 ? 0u : (*known == 32 ? hi : (hi >> (32 - *known)));
   }
-  __syncthreads();
-  const float* cur = buf;
-  int mc = m;
+}
+
+// One round's digit for a rank by warp 0 from the histogram h[] (lane L holds bins
+// 8L..8L+7 and the inclusive count incl of bins up to its last): the lane holding the
+// rank writes the new prefix, the rank within the digit and the digit's count.
+__device__ __forceinline__ void radix_pick(const unsigned int (&h)[8], unsigned long long incl, unsigned int local,
+                                           unsigned long long want, uint32_t prefix, int nbits, uint32_t* o_prefix,
+                                           unsigned long long* o_rank, unsigned int* o_bucket, bool* found) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long excl = incl - local;
+  const bool mine = excl < want && want <= incl;
+  *found = __ballot_sync(0xffffffffu, mine) != 0;
+  if (mine) {
+    unsigned long long c = excl;
+    int d = 0;
+    unsigned int bk = 0;
+    for (int j = 0; j < 8; ++j) {
+      if (c + h[j] >= want) { d = lane * 8 + j; bk = h[j]; break; }
+      c += h[j];
+    }
+    *o_rank = want - c;
+    *o_prefix = (prefix << nbits) | (uint32_t)d;
+    *o_bucket = bk;
+  }
+}
+
+// The radix rounds from the state in st (known bits, prefix, rank) over cur[0, mc), which is
+// buf[0, m) or, once gathered, zs: 8-bit digits of the elements that lie in (a, b] (all when
+// !filter) and start with the prefix.  When cur is buf in device memory, zs (shared memory,
+// cap elements, else nullptr) takes the elements of the chosen digit once they fit, and
+// the later rounds run there.  The selected key ends in st.prefix.
+template <int B>
+__device__ void radix_rounds(const float* buf, int m, const float* cur, int mc, bool filter, float a, float b,
+                             float* zs, int cap, RadixState& st) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   while (st.known < 32) {
     const int known = st.known;
     const uint32_t prefix = st.prefix;
@@ -331,29 +356,17 @@ __device__ __noinline__ uint32_t radix_select(const float* buf, int m, unsigned 
         const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
       }
-      const unsigned long long want = st.rank;
-      const unsigned long long excl = incl - local;
-      const bool mine = excl < want && want <= incl;
-      const unsigned int who = __ballot_sync(0xffffffffu, mine);
-      if (mine) {
-        unsigned long long c = excl;
-        int d = 0;
-        unsigned int bk = 0;
-        for (int j = 0; j < 8; ++j) {
-          if (c + h[j] >= want) { d = lane * 8 + j; bk = h[j]; break; }
-          c += h[j];
-        }
-        st.rank = want - c;
-        st.prefix = (prefix << nbits) | (uint32_t)d;
+      bool found;
+      radix_pick(h, incl, local, st.rank, prefix, nbits, &st.prefix, &st.rank, &st.bucket, &found);
+      if (lane == 0) {
         st.known = known + nbits;
-        st.bucket = bk;
         st.cnt = 0;
-      }
-      if (who == 0 && lane == 0) {
-        st.known = 32;
-        st.prefix = 0;
-        st.rank = 0;   // flags an inconsistency to the caller
-        st.bucket = 0xffffffffu;
+        if (!found) {   // no bin holds the rank: inconsistent counts, flagged by rank 0
+          st.known = 32;
+          st.prefix = 0;
+          st.rank = 0;
+          st.bucket = 0xffffffffu;
+        }
       }
     }
     __syncthreads();
@@ -364,13 +377,128 @@ __device__ __noinline__ uint32_t radix_select(const float* buf, int m, unsigned 
       mc = (int)min(st.cnt, (unsigned int)cap);   // equal to the bucket's count
     }
   }
+}
+
+// Radix select inside the CTA: the rank-th (1-based) smallest, in totalOrder, of the
+// elements of buf[0, m) that lie in (a, b] (all of them when !filter).  Returns the
+// element's key (st.rank == 0 afterwards flags inconsistent counts).  8-bit digits from
+// the highest bit where the bracket's keys differ; zs and cap as for radix_rounds.
+template <int B>
+__device__ __noinline__ uint32_t radix_select(const float* buf, int m, unsigned long long rank, bool filter, float a,
+                                              float b, float* zs, int cap, RadixState& st) {
+  if (threadIdx.x == 0) {
+    radix_known(filter, a, b, &st.known, &st.prefix);
+    st.rank = rank;
+  }
+  __syncthreads();
+  radix_rounds<B>(buf, m, buf, m, filter, a, b, zs, cap, st);
   return st.prefix;
+}
+
+// Two ranks at once (as radix_select for each): the rounds share their histograms while
+// both ranks fall in the same digit, then each continues alone from where they parted.
+// The keys land in *key1 and *key2 (shared memory); st.rank == 0 afterwards flags
+// inconsistent counts for either.
+template <int B>
+__device__ __noinline__ void radix_select2(const float* buf, int m, unsigned long long rank1,
+                                           unsigned long long rank2, bool filter, float a, float b, float* zs,
+                                           int cap, RadixState& st, uint32_t* key1, uint32_t* key2) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    radix_known(filter, a, b, &st.known, &st.prefix);
+    st.prefix2 = st.prefix;
+    st.rank = rank1;
+    st.rank2 = rank2;
+    st.split = 0;
+  }
+  __syncthreads();
+  const float* cur = buf;
+  int mc = m;
+  while (st.known < 32 && !st.split) {
+    const int known = st.known;
+    const uint32_t prefix = st.prefix;
+    const int nbits = (32 - known) < 8 ? (32 - known) : 8;
+    const int sh = 32 - known - nbits;
+    const unsigned int dmask = (1u << nbits) - 1u;
+    for (int i = tid; i < 256; i += B) st.hist[i] = 0;
+    __syncthreads();
+    radix_hist<B>(cur, mc, filter, a, b, known, prefix, sh, dmask, st.hist);
+    __syncthreads();
+    if (warp == 0) {
+      unsigned int h[8];
+      unsigned int local = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        h[j] = st.hist[lane * 8 + j];
+        local += h[j];
+      }
+      unsigned long long incl = local;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const unsigned long long w1 = st.rank, w2 = st.rank2;
+      bool f1, f2;
+      radix_pick(h, incl, local, w1, prefix, nbits, &st.prefix, &st.rank, &st.bucket, &f1);
+      radix_pick(h, incl, local, w2, prefix, nbits, &st.prefix2, &st.rank2, &st.bucket2, &f2);
+      __syncwarp();
+      if (lane == 0) {
+        st.known = known + nbits;
+        st.cnt = 0;
+        st.split = st.prefix != st.prefix2;
+        if (!f1 || !f2) {
+          st.known = 32;
+          st.prefix = st.prefix2 = 0;
+          st.rank = 0;
+          st.split = 0;
+        }
+      }
+    }
+    __syncthreads();
+    if (!st.split && zs != nullptr && cur == buf && st.known < 32 && st.bucket <= (unsigned int)cap) {
+      radix_gather<B>(buf, m, filter, a, b, st.known, st.prefix, zs, (unsigned int)cap, &st.cnt);
+      __syncthreads();
+      cur = zs;
+      mc = (int)min(st.cnt, (unsigned int)cap);
+    }
+  }
+  if (!st.split) {
+    if (tid == 0) { *key1 = st.prefix; *key2 = st.prefix; }
+    __syncthreads();
+    return;
+  }
+  // parted: the first rank's rounds, then the second's from the same point
+  const int known_at = st.known;
+  const uint32_t p2 = st.prefix2;
+  const unsigned long long r2 = st.rank2;
+  radix_rounds<B>(buf, m, cur, mc, filter, a, b, zs, cap, st);
+  const uint32_t k1 = st.prefix;
+  const bool bad1 = st.rank == 0;
+  __syncthreads();
+  if (tid == 0) {
+    *key1 = k1;
+    st.known = known_at;
+    st.prefix = p2;
+    st.rank = r2;
+    st.cnt = 0;
+  }
+  __syncthreads();
+  // when cur was gathered into zs before the split it still holds both ranks' elements
+  // (the first rank's rounds read it without gathering again)
+  radix_rounds<B>(buf, m, cur, mc, filter, a, b, zs, cap, st);
+  if (tid == 0) {
+    *key2 = st.prefix;
+    if (bad1) st.rank = 0;
+  }
+  __syncthreads();
 }
 
 struct SegShared {
   Sum6 sum6[33];
   float mn[32], mx[32];
   RadixState rx;
+  uint32_t key1, key2;   // keys of a two-rank select
   unsigned int zcnt;
   int seg;
   // bracket state (thread 0 writes, all read)
@@ -604,7 +732,11 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
         __syncthreads();
         continue;
       }
-      const uint32_t key = radix_select<B>(zb, (int)n, (unsigned long long)k, false, 0.f, 0.f, nullptr, 0, sh.rx);
+      // trimmed-sum mode: both ranks from shared rounds
+      if (LTS) radix_select2<B>(zb, (int)n, (unsigned long long)k, (unsigned long long)k2, false, 0.f, 0.f, nullptr, 0,
+                                sh.rx, &sh.key1, &sh.key2);
+      const uint32_t key =
+          LTS ? sh.key1 : radix_select<B>(zb, (int)n, (unsigned long long)k, false, 0.f, 0.f, nullptr, 0, sh.rx);
       const float q = ukey_value(key, 0.f);
       if (tid == 0) {
         if (sh.rx.rank == 0) atomicCAS(&A.ctrl->status, 0, (int)GBS_EINTERNAL);
@@ -619,7 +751,7 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
         Sum6 w6;
         w6.u[0] = bc; w6.u[1] = w6.u[2] = w6.u[3] = w6.u[4] = 0; w6.d = (double)bs;
         const Sum6 t6 = cta_sum6<B>(w6, sh.sum6);
-        const uint32_t key2 = radix_select<B>(zb, (int)n, (unsigned long long)k2, false, 0.f, 0.f, nullptr, 0, sh.rx);
+        const uint32_t key2 = sh.key2;
         if (tid == 0) {
           A.outsum[s] = t6.d + (double)(k - (long long)t6.u[0]) * (double)q;
           A.out2[s] = ukey_value(key2, 0.f);
@@ -820,8 +952,16 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
       const int m = (int)sh.zcnt;
       const float* zf = sh.zglob ? A.zg + (long long)blockIdx.x * A.zg_cap : zb;
       float* const zs = sh.zglob ? zb : nullptr;   // gathers the last digits into shared memory
-      const uint32_t key = radix_select<B>(zf, m, (unsigned long long)(k - sh.cle_a0), true, sh.a0, sh.b0, zs, CAP,
-                                           sh.rx);
+      // trimmed-sum mode with the second rank inside the bracket: both from shared rounds
+      const bool inside2 = LTS && sh.cle_a0 < k2 && k2 <= sh.cle_a0 + m;
+      uint32_t key;
+      if (inside2) {
+        radix_select2<B>(zf, m, (unsigned long long)(k - sh.cle_a0), (unsigned long long)(k2 - sh.cle_a0), true,
+                         sh.a0, sh.b0, zs, CAP, sh.rx, &sh.key1, &sh.key2);
+        key = sh.key1;
+      } else {
+        key = radix_select<B>(zf, m, (unsigned long long)(k - sh.cle_a0), true, sh.a0, sh.b0, zs, CAP, sh.rx);
+      }
       if (tid == 0 && sh.rx.rank == 0) atomicCAS(&A.ctrl->status, 0, (int)GBS_EINTERNAL);
       result = ukey_value(key, 0.f);
       if (LTS) {
@@ -832,13 +972,7 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
         w6.u[0] = bc; w6.u[1] = w6.u[2] = w6.u[3] = w6.u[4] = 0; w6.d = (double)bs;
         const Sum6 t6 = cta_sum6<B>(w6, sh.sum6);
         const long long below = sh.cle_a0 + (long long)t6.u[0];
-        const bool inside2 = sh.cle_a0 < k2 && k2 <= sh.cle_a0 + m;
-        float r2 = NAN;
-        if (inside2) {
-          const uint32_t key2 = radix_select<B>(zf, m, (unsigned long long)(k2 - sh.cle_a0), true, sh.a0, sh.b0,
-                                                zs, CAP, sh.rx);
-          r2 = ukey_value(key2, 0.f);
-        }
+        const float r2 = inside2 ? ukey_value(sh.key2, 0.f) : NAN;
         if (tid == 0) {
           A.outsum[s] = sh.sum + t6.d + (double)(k - below) * (double)result;
           A.out2[s] = r2;
