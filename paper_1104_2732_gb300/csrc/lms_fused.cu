@@ -26,6 +26,15 @@
 // compacted sets; LTS adds the sum below the bracket.  A candidate whose residuals are not
 // all finite, whose bracket outgrows its compaction buffer or whose counts disagree is
 // recomputed by the materialising batched form.
+//
+// Sampled start (the default for n >= 65536): each candidate's squares on 8192 evenly
+// spread rows give order statistics around both ranks, and the proposed bracket (a, b] is
+// compacted straight away in one pass: every lane gets a region of the candidate's buffer
+// sized from the sample's share of (a, b] (1.3 times it plus 6 standard deviations), and
+// the pass counts #(s <= a), the kept elements and the non-finite squares exactly.  When
+// the bracket holds both ranks and no lane outgrew its region, the lanes' shares are
+// gathered in lane order (each lane's count is kept in the ring) and finished; otherwise
+// the candidate goes to the materialising form.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -49,8 +58,8 @@ constexpr long long kFCap = 49152;     // compaction buffer per candidate (eleme
 constexpr int kFVariant = 2;           // segmented variant of the finish (1024 threads, 49152 in smem)
 constexpr int kRing = 16;              // cost passes whose per-lane counts are kept
 
-enum { kFStats = 0, kFCost = 1, kFCheck = 2, kFWrite = 3 };
-enum { kPhIter = 0, kPhDone = 1, kPhCompact = 2, kPhFallback = 3, kPhFinish = 4, kPhCheck = 5 };
+enum { kFStats = 0, kFCost = 1, kFWrite = 3 };
+enum { kPhIter = 0, kPhDone = 1, kPhCompact = 2, kPhFallback = 3, kPhFinish = 4, kPhDirect = 6 };
 constexpr int kSampleRows = 8192;           // rows of the sampled start
 constexpr long long kSampleMinN = 65536;    // smaller problems start from the extremes
 
@@ -69,7 +78,8 @@ struct FusedCand {
 struct FusedTot {
   unsigned long long le, sfix;       // cost pass
   unsigned long long kept, le_a;     // compaction pass: #(a < s <= b), #(s <= a)
-  unsigned long long nonfinite;      // statistics pass
+  unsigned long long nonfinite;      // statistics pass; direct compaction pass
+  unsigned long long overflow;       // direct compaction pass: lanes whose share outgrew their region
   unsigned int mn, mx;               // statistics pass: bits of min / max (s >= 0)
   double sum;                        // statistics: sum of s; compaction: sum of s <= a
 };
@@ -84,7 +94,9 @@ struct FusedArgs {
   long long rows_per_item;
   FusedCand* cand;
   FusedTot* tot;
-  float* zbuf;        // [C][kFCap]
+  float* zbuf;        // [C][zstride]
+  long long zstride;   // elements of a candidate's compaction buffer
+  unsigned int lane_room; // direct compaction: capacity of each lane's region (its offset in loff)
   unsigned int* lring; // [kRing][C][nrc][4]: each lane's #(s <= t) of the last kRing cost passes
   int ring_slot;       // slot this cost pass writes
   unsigned int* loff;  // [C][nrc][4]: where each lane writes its share of (a, b]
@@ -186,14 +198,13 @@ __device__ __forceinline__ void fused_item(const FusedArgs& A, long long item, f
       const FusedCand& fc = A.cand[c];
       if (MODE == kFStats) act = true;
       if (MODE == kFCost) act = fc.phase == kPhIter;
-      if (MODE == kFCheck) act = fc.phase == kPhCheck;
-      if (MODE == kFWrite) act = fc.phase == kPhCompact;
+      if (MODE == kFWrite) act = fc.phase == kPhCompact || fc.phase == kPhDirect;
       pa[j] = fc.a; pt[j] = fc.t; pb[j] = fc.b;
       nsig[j] = -fc.sigma; tsig[j] = fc.t * fc.sigma; fx[j] = fc.fx;
       if (MODE == kFWrite && act) {
         const unsigned int base = A.loff[((long long)c * A.nrc + rc) * 4 + q];
-        zp[j] = A.zbuf + (long long)c * kFCap + base;
-        room[j] = (unsigned int)kFCap - base;
+        zp[j] = A.zbuf + (long long)c * A.zstride + base;
+        room[j] = fc.phase == kPhDirect ? A.lane_room : (unsigned int)(A.zstride - base);
       }
     }
     if (j) act1 = act; else act0 = act;
@@ -284,13 +295,10 @@ __device__ __forceinline__ void fused_item(const FusedArgs& A, long long item, f
             nf[j] += (valid && !ok) ? 1u : 0u;
           } else if (MODE == kFCost) {
             core_le(s, pa[j], pt[j], nsig[j], tsig[j], le[j], S[j]);
-          } else if (MODE == kFCheck) {   // #(s <= a), #(s <= b) of a proposed bracket
-            const bool valid = full || (r0 + lr + (e & 1)) < r_end;
-            nf[j] += (valid && !(s <= FLT_MAX)) ? 1u : 0u;
-            le[j] += (s <= pa[j]) ? 1u : 0u;
-            lea[j] += (s <= pb[j]) ? 1u : 0u;
           } else {
             // below the bracket: the stage's partial sum; inside: the lane's next slot
+            const bool valid = full || (r0 + lr + (e & 1)) < r_end;
+            nf[j] += (valid && !(s <= FLT_MAX)) ? 1u : 0u;
             const bool below = s <= pa[j];
             const bool keep = (s > pa[j]) & (s <= pb[j]);
             stage_sum[j] += below ? s : 0.f;
@@ -313,15 +321,23 @@ __device__ __forceinline__ void fused_item(const FusedArgs& A, long long item, f
     __syncthreads();
   }
 
-  if (MODE == kFCost || MODE == kFCheck) {   // each lane's own counts, for the compaction offsets
+  unsigned int ovf = 0;
+  if (MODE == kFWrite) {   // each lane's share of (a, b] (the direct route gathers by it)
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int c = j ? c1 : c0;
       if (c < A.C && (j ? act1 : act0)) {
-        A.lring[(((long long)A.ring_slot * A.C + c) * A.nrc + rc) * 4 + q] = le[j];
-        if (MODE == kFCheck)   // #(s <= b) in the next slot
-          A.lring[(((long long)(A.ring_slot + 1) * A.C + c) * A.nrc + rc) * 4 + q] = lea[j];
+        A.lring[(((long long)A.ring_slot * A.C + c) * A.nrc + rc) * 4 + q] = kept[j];
+        ovf |= (kept[j] > room[j] ? 1u : 0u) << j;
       }
+    }
+  }
+  if (MODE == kFCost) {           // each lane's own #(s <= t), for the compaction offsets
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int c = j ? c1 : c0;
+      if (c < A.C && (j ? act1 : act0))
+        A.lring[(((long long)A.ring_slot * A.C + c) * A.nrc + rc) * 4 + q] = le[j];
     }
   }
   double dsum[2];
@@ -336,6 +352,7 @@ __device__ __forceinline__ void fused_item(const FusedArgs& A, long long item, f
       lea[j] += __shfl_xor_sync(0xffffffffu, lea[j], o);
       kept[j] += __shfl_xor_sync(0xffffffffu, kept[j], o);
       nf[j] += __shfl_xor_sync(0xffffffffu, nf[j], o);
+      if (MODE == kFWrite && j == 0) ovf |= __shfl_xor_sync(0xffffffffu, ovf, o);
       S[j] += __shfl_xor_sync(0xffffffffu, S[j], o);
       mn[j] = fminf(mn[j], __shfl_xor_sync(0xffffffffu, mn[j], o));
       mx[j] = fmaxf(mx[j], __shfl_xor_sync(0xffffffffu, mx[j], o));
@@ -360,13 +377,11 @@ __device__ __forceinline__ void fused_item(const FusedArgs& A, long long item, f
         if (le[j]) atomicAdd(&T.le, (unsigned long long)le[j]);
         const unsigned long long sf = __double2ull_rn(ldexp((double)S[j], fx[j]));
         if (sf) atomicAdd(&T.sfix, sf);
-      } else if (MODE == kFCheck) {
-        if (nf[j]) atomicAdd(&T.nonfinite, (unsigned long long)nf[j]);
-        if (le[j]) atomicAdd(&T.le, (unsigned long long)le[j]);
-        if (lea[j]) atomicAdd(&T.kept, (unsigned long long)lea[j]);
       } else {
         if (lea[j]) atomicAdd(&T.le_a, (unsigned long long)lea[j]);
         if (kept[j]) atomicAdd(&T.kept, (unsigned long long)kept[j]);
+        if (nf[j]) atomicAdd(&T.nonfinite, (unsigned long long)nf[j]);
+        if ((ovf >> j) & 1u) atomicAdd(&T.overflow, 1ull);
         atomicAdd(&T.sum, dsum[j]);
       }
     }
@@ -485,25 +500,26 @@ __global__ void fused_step_kernel(StepArgs P) {
         fused_next(s, P);
       }
     }
-  } else if (MODE == kFCheck) {
-    // a proposed bracket holds both ranks when #(s <= a) < k_lo and k_hi <= #(s <= b);
-    // then it is the starting bracket (Phi(b) - Phi(a) unknown: the first step bisects)
-    if (s.phase == kPhCheck) {
-      const long long la = (long long)T.le, lb = (long long)T.kept;
-      if (T.nonfinite > 0 || !(la < P.k_lo && P.k_hi <= lb)) {
-        s.phase = kPhFallback;   // counted by the step after the write pass
-      } else {
-        s.phase = kPhIter;
-        s.it = 0; s.use_bisect = 0; s.stalled = 0; s.dfv = 0; s.dF = 0.0;
-        s.cle_a = la; s.cle_b = lb; s.clt_b = lb;   // #(s <= b) stands for #(s < b)
-        s.pa_pass = P.pass; s.pb_pass = P.pass + 1;
-        s.mn = 0.f;
-        fused_next(s, P);
-      }
-    }
   } else {   // after the write pass: check, and prepare the segmented finish
     int fin = 0;
-    if (s.phase == kPhCompact) {
+    if (s.phase == kPhDirect) {
+      // one pass counted #(s <= a), compacted (a, b] into the lanes' regions and summed
+      // s <= a: the bracket holds both ranks, no square is non-finite, no lane's share
+      // outgrew its region and the set fits the finish's shared memory (kFCap, as for the
+      // start from the extremes), or the candidate goes to the fallback
+      const long long la = (long long)T.le_a, kept = (long long)T.kept;
+      if (T.nonfinite == 0 && T.overflow == 0 && la < P.k_lo && P.k_hi <= la + kept && kept <= kFCap) {
+        s.phase = kPhFinish;
+        s.cle_a = la; s.cle_b = la + kept; s.clt_b = s.cle_b;
+        fin = 1;
+        P.seg_len[c] = kept;
+        P.kk[c] = P.h_lts - la;
+        P.kk2[c] = P.k_lms - la;
+        P.below[c] = T.sum;
+      } else {
+        s.phase = kPhFallback;
+      }
+    } else if (s.phase == kPhCompact) {
       const long long kept = (long long)T.kept;
       if ((long long)T.le_a != s.cle_a || kept != s.cle_b - s.cle_a) {
         s.phase = kPhFallback;
@@ -527,7 +543,7 @@ __global__ void fused_step_kernel(StepArgs P) {
   if (s.phase == kPhIter) atomicAdd(&P.counters[0], 1u);
   P.cand[c] = s;
   // totals start from zero for the next pass (min starts at +inf bits)
-  T.le = T.sfix = T.kept = T.le_a = T.nonfinite = 0ull;
+  T.le = T.sfix = T.kept = T.le_a = T.nonfinite = T.overflow = 0ull;
   T.mn = 0x7F7FFFFFu; T.mx = 0u; T.sum = 0.0;
 }
 
@@ -587,7 +603,7 @@ __global__ void fused_init_kernel(FusedTot* tot, int C, unsigned int* counters) 
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < C) {
     FusedTot& T = tot[c];
-    T.le = T.sfix = T.kept = T.le_a = T.nonfinite = 0ull;
+    T.le = T.sfix = T.kept = T.le_a = T.nonfinite = T.overflow = 0ull;
     T.mn = 0x7F7FFFFFu; T.mx = 0u; T.sum = 0.0;
   }
   if (c == 0) counters[0] = counters[1] = 0u;
@@ -623,13 +639,65 @@ __global__ void __launch_bounds__(1024) fused_offsets_kernel(const long long* le
 }
 
 // Copies each finishing candidate's compacted elements to its segment.
-__global__ void fused_gather_kernel(const float* __restrict__ zbuf, const long long* __restrict__ off, int C,
-                                    float* __restrict__ zcat) {
+__global__ void fused_gather_kernel(const float* __restrict__ zbuf, long long zstride, const long long* __restrict__ off,
+                                    int C, float* __restrict__ zcat) {
   const int c = blockIdx.x;
   if (c >= C) return;
   const long long o = off[c], len = off[c + 1] - o;
-  const float* src = zbuf + (long long)c * kFCap;
+  const float* src = zbuf + (long long)c * zstride;
   for (long long i = threadIdx.x; i < len; i += blockDim.x) zcat[o + i] = src[i];
+}
+
+// The direct route's gather: candidate c's share of lane l (count cnt[l], from the ring
+// slot of the direct pass) sits at zbuf[c * zstride + l * room]; the shares go to zcat
+// from off[c] in lane order.  One CTA of 8 warps per candidate: warp w takes a contiguous
+// range of lanes, starts after the earlier warps' totals, and walks its lanes 32 at a time
+// (a warp scan gives each share's place), copying each share with consecutive accesses.
+__global__ void __launch_bounds__(256) fused_gather_lanes_kernel(const float* __restrict__ zbuf, long long zstride,
+                                                                 const unsigned int* __restrict__ cnt_all, int nl,
+                                                                 unsigned int room, const long long* __restrict__ off,
+                                                                 int C, float* __restrict__ zcat) {
+  __shared__ unsigned int s_w[8];
+  const int c = blockIdx.x;
+  if (c >= C) return;
+  const long long o = off[c], len = off[c + 1] - o;
+  if (len == 0) return;
+  const unsigned int* cnt = cnt_all + (long long)c * nl;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wper = (nl + 7) / 8;
+  const int wl0 = min(nl, warp * wper), wl1 = min(nl, wl0 + wper);
+  unsigned int t = 0;
+  for (int l = wl0 + lane; l < wl1; l += 32) t += min(cnt[l], room);
+  t = __reduce_add_sync(0xffffffffu, t);
+  if (lane == 0) s_w[warp] = t;
+  __syncthreads();
+  unsigned long long base = (unsigned long long)o;
+  for (int w = 0; w < warp; ++w) base += s_w[w];
+  const float* src = zbuf + (long long)c * zstride;
+  for (int g0 = wl0; g0 < wl1; g0 += 32) {
+    const int l = g0 + lane;
+    const unsigned int m = l < wl1 ? min(cnt[l], room) : 0u;
+    unsigned int incl = m;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned int v = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += v;
+    }
+    const unsigned int excl = incl - m;
+    const int nj = min(32, wl1 - g0);
+    for (int j = 0; j < nj; ++j) {
+      const unsigned int mj = __shfl_sync(0xffffffffu, m, j), ej = __shfl_sync(0xffffffffu, excl, j);
+      const float* sl = src + (long long)(g0 + j) * room;
+      for (unsigned int i = lane; i < mj; i += 32) zcat[base + ej + i] = sl[i];
+    }
+    base += __shfl_sync(0xffffffffu, incl, 31);
+  }
+}
+
+// Lane regions of the direct route: lane (rc, q) of candidate c writes from (rc * 4 + q) * room.
+__global__ void fused_direct_offsets_kernel(unsigned int* loff, int C, int nl, unsigned int room) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < (long long)C * nl) loff[i] = (unsigned int)(i % nl) * room;
 }
 
 // LTS of finishing candidates: the trimmed sum inside the bracket plus the sum below it.
@@ -679,7 +747,6 @@ template <int KS>
 gbs_status launch_pass(int mode, const FusedArgs& A, int num_sms, cudaStream_t s) {
   if (mode == kFStats) return launch_mode<KS, kFStats>(A, num_sms, s);
   if (mode == kFCost) return launch_mode<KS, kFCost>(A, num_sms, s);
-  if (mode == kFCheck) return launch_mode<KS, kFCheck>(A, num_sms, s);
   return launch_mode<KS, kFWrite>(A, num_sms, s);
 }
 
@@ -726,7 +793,7 @@ __global__ void lms_propose_kernel(FusedCand* cand, int C, const float* lo, cons
   s.t = 0.f; s.sigma = 1.f; s.fx = kSFixBits;
   s.it = 0; s.use_bisect = 0; s.stalled = 0; s.dfv = 0;
   s.cle_a = s.clt_b = s.cle_b = 0; s.dF = 0.0; s.mn = 0.f; s.pa_pass = s.pb_pass = -1;
-  s.phase = (s.a < s.b && s.b <= FLT_MAX) ? kPhCheck : kPhFallback;
+  s.phase = (s.a < s.b && s.b <= FLT_MAX) ? kPhDirect : kPhFallback;
   cand[c] = s;
 }
 
@@ -756,6 +823,51 @@ extern "C" gbs_status gbs_lms_lts_fused_f32(gbs_ctx* c, const float* X, const fl
   cudaStream_t strm = static_cast<cudaStream_t>(stream);
   const int KS = p <= 8 ? 1 : 2, P8 = 8 * KS;
   const int ncb = (C + kFCand - 1) / kFCand, Cpad = ncb * kFCand;
+  // persistent grid: every resident CTA; work items (candidate blocks x row chunks) about
+  // eight per CTA, so that the last round of items is a small share of the pass
+  int occ = 0;
+  if ((KS == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fused_pass_kernel<1, kFCost>, kFT, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fused_pass_kernel<2, kFCost>, kFT, 0)) !=
+          cudaSuccess ||
+      occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  const long long resident = (long long)c->num_sms * occ;
+  const long long target = resident * 8;
+  long long nrc = std::max<long long>(1, (target + ncb - 1) / ncb);
+  long long rpi = (n + nrc - 1) / nrc;
+  rpi = (rpi + kFRows - 1) / kFRows * kFRows;
+  nrc = (n + rpi - 1) / rpi;
+  // sampled start: the sample's ranks around k and h (3.5 binomial standard deviations and
+  // 2 ranks of margin on each side: at the medians of 1e6 rows the bracket holds about
+  // 3.9 % of them and a side misses with probability ~2e-4), and the direct route's lane
+  // regions: each lane (2 of every 8 rows of its items) gets room for 1.3 times the
+  // sample's share of its rows plus 6 standard deviations
+  const int ns = kSampleRows;
+  bool sampled = false;
+  long long jl = 0, jh = 0, zstride = kFCap;
+  unsigned int lane_room = 0;
+  const long long nl = nrc * 4;
+  if (c->cfg.lms_start == 0 && n >= kSampleMinN) {
+    const double pl = (double)std::min(k_lms, h_lts) / (double)n, ph = (double)std::max(k_lms, h_lts) / (double)n;
+    jl = (long long)std::floor(ns * pl - 3.5 * std::sqrt(ns * pl * (1.0 - pl))) - 2;
+    jh = (long long)std::ceil(ns * ph + 3.5 * std::sqrt(ns * ph * (1.0 - ph))) + 2;
+    const double f = (double)(std::min<long long>(jh, ns) - std::max<long long>(jl, 1) + 1) / ns;
+    // the expected bracket must fit the finish's shared memory (ranks far apart take the
+    // start from the extremes, which sends such candidates to the materialising form)
+    const bool fits = f * (double)n <= 0.9 * (double)kFCap;
+    const double lane_rows = (double)rpi / 4.0;
+    const double mean = lane_rows * std::min(1.0, f * 1.3);
+    long long R = (long long)std::ceil(mean + 6.0 * std::sqrt(mean) + 8.0);
+    R = std::min<long long>((R + 3) / 4 * 4, (long long)lane_rows);
+    const long long zs = std::max<long long>(kFCap, nl * R);
+    if (fits && (double)C * (double)zs * 8.0 <= 4.0 * 1073741824.0) {   // zbuf + zcat within 4 GiB
+      sampled = true;
+      zstride = zs;
+      lane_room = (unsigned int)R;
+    }
+  }
   // workspace: xi | th | tl | cand | tot | counters | seg_len | kk | kk2 | mask | below | off |
   //            list | zbuf | zcat
   size_t o = 0;
@@ -777,25 +889,9 @@ extern "C" gbs_status gbs_lms_lts_fused_f32(gbs_ctx* c, const float* X, const fl
   const size_t o_plo = o; o = up256f(o + sizeof(float) * (size_t)C);   // sampled start: proposed ends
   const size_t o_phi = o; o = up256f(o + sizeof(float) * (size_t)C);
   const size_t o_srow = o; o = up256f(o + sizeof(float) * (size_t)kSampleRows * (p + 1));   // sampled rows
-  const size_t o_z = o; o = up256f(o + sizeof(float) * (size_t)C * kFCap);
-  const size_t o_zc = o; o = up256f(o + sizeof(float) * (size_t)C * kFCap);
+  const size_t o_z = o; o = up256f(o + sizeof(float) * (size_t)C * zstride);
+  const size_t o_zc = o; o = up256f(o + sizeof(float) * (size_t)C * zstride);
   const size_t o_y = o; o = up256f(o + sizeof(float) * (size_t)n);
-  // persistent grid: every resident CTA; work items (candidate blocks x row chunks) about
-  // eight per CTA, so that the last round of items is a small share of the pass
-  int occ = 0;
-  if ((KS == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fused_pass_kernel<1, kFCost>, kFT, 0)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fused_pass_kernel<2, kFCost>, kFT, 0)) !=
-          cudaSuccess ||
-      occ < 1) {
-    cudaGetLastError();
-    occ = 1;
-  }
-  const long long resident = (long long)c->num_sms * occ;
-  const long long target = resident * 8;
-  long long nrc = std::max<long long>(1, (target + ncb - 1) / ncb);
-  long long rpi = (n + nrc - 1) / nrc;
-  rpi = (rpi + kFRows - 1) / kFRows * kFRows;
-  nrc = (n + rpi - 1) / rpi;
   const size_t o_ring = o; o = up256f(o + sizeof(unsigned int) * (size_t)kRing * C * nrc * 4);
   const size_t o_loff = o; o = up256f(o + sizeof(unsigned int) * (size_t)C * nrc * 4);
   const size_t bytes = o;
@@ -823,6 +919,8 @@ extern "C" gbs_status gbs_lms_lts_fused_f32(gbs_ctx* c, const float* X, const fl
   A.cand = reinterpret_cast<FusedCand*>(b + o_cand);
   A.tot = reinterpret_cast<FusedTot*>(b + o_tot);
   A.zbuf = reinterpret_cast<float*>(b + o_z);
+  A.zstride = zstride;
+  A.lane_room = 0;
   A.rows_per_item = rpi;
   A.nrc = (int)nrc;
   A.lring = reinterpret_cast<unsigned int*>(b + o_ring);
@@ -871,17 +969,11 @@ extern "C" gbs_status gbs_lms_lts_fused_f32(gbs_ctx* c, const float* X, const fl
     return KS == 1 ? launch_pass<1>(mode, A, c->num_sms, strm) : launch_pass<2>(mode, A, c->num_sms, strm);
   };
   int npass = 0;
-  int first_cost = 0;   // index of the first cost pass (ring slot: index % kRing)
-  if (c->cfg.lms_start == 0 && n >= kSampleMinN) {
-    // sampled start: order statistics of the candidates' squares on kSampleRows rows
-    // propose (a, b] around both ranks (3.5 binomial standard deviations and 2 ranks of
-    // margin on each side: at the medians of 1e6 rows the bracket holds about 3.9 % of
-    // them, inside the compaction buffer, and a side misses with probability ~2e-4); the
-    // check pass counts #(s <= a) and #(s <= b) exactly
-    const int ns = kSampleRows;
-    const double pl = (double)P.k_lo / (double)n, ph = (double)P.k_hi / (double)n;
-    const long long jl = (long long)std::floor(ns * pl - 3.5 * std::sqrt(ns * pl * (1.0 - pl))) - 2;
-    const long long jh = (long long)std::ceil(ns * ph + 3.5 * std::sqrt(ns * ph * (1.0 - ph))) + 2;
+  unsigned int h_cnt[2] = {0u, 0u};
+  if (sampled) {
+    // sampled start: order statistics of the candidates' squares on ns sampled rows
+    // propose (a, b] around both ranks; one direct pass counts #(s <= a) and the elements
+    // of (a, b] exactly while compacting them into the lanes' regions and summing s <= a
     const int lo_in = jl >= 1, hi_in = jh <= ns;
     float* plo = reinterpret_cast<float*>(b + o_plo);
     float* phi = reinterpret_cast<float*>(b + o_phi);
@@ -896,53 +988,55 @@ extern "C" gbs_status gbs_lms_lts_fused_f32(gbs_ctx* c, const float* X, const fl
     // both order statistics from one load of each candidate's sample: the segmented
     // select's two-rank mode (its trimmed sums and flags land in buffers the finish fills
     // later)
-    SegLaunch L;
-    if ((st = seg_attach_workspace(c, C, &L)) != GBS_OK) return st;
-    L.x = rs; L.off = off; L.S = C; L.kk = nullptr; L.ctrl = c->ctrl; L.mask = nullptr; L.kk2 = nullptr;
-    L.k_const = std::max<long long>(jl, 1); L.out = plo;
-    L.k2_const = std::min<long long>(jh, ns); L.out2 = phi;
-    L.outsum = P.below; L.flags = flags;
-    if ((st = seg_launch(c, L, 0, strm)) != GBS_OK) return st;
+    SegLaunch Ls;
+    if ((st = seg_attach_workspace(c, C, &Ls)) != GBS_OK) return st;
+    Ls.x = rs; Ls.off = off; Ls.S = C; Ls.kk = nullptr; Ls.ctrl = c->ctrl; Ls.mask = nullptr; Ls.kk2 = nullptr;
+    Ls.k_const = std::max<long long>(jl, 1); Ls.out = plo;
+    Ls.k2_const = std::min<long long>(jh, ns); Ls.out2 = phi;
+    Ls.outsum = P.below; Ls.flags = flags;
+    if ((st = seg_launch(c, Ls, 0, strm)) != GBS_OK) return st;
     lms_propose_kernel<<<sgrid, 256, 0, strm>>>(A.cand, C, plo, phi, lo_in, hi_in);
-    // check pass: ring slots 0 (#(s <= a)) and 1 (#(s <= b))
-    A.ring_slot = 0;
-    P.pass = 0;
-    if ((st = pass(kFCheck)) != GBS_OK) return st;
+    fused_direct_offsets_kernel<<<(unsigned int)(((long long)C * nl + 255) / 256), 256, 0, strm>>>(A.loff, C, (int)nl,
+                                                                                                 lane_room);
+    if (cudaMemsetAsync(P.counters, 0, sizeof(unsigned int) * 2, strm) != cudaSuccess) return GBS_ECUDA;
+    A.lane_room = lane_room;
+    A.ring_slot = 0;   // each lane's share of (a, b], for the gather
+    if ((st = pass(kFWrite)) != GBS_OK) return st;
     ++npass;
-    fused_step_kernel<kFCheck><<<sgrid, 256, 0, strm>>>(P);
+    fused_step_kernel<kFWrite><<<sgrid, 256, 0, strm>>>(P);
+    fused_offsets_kernel<<<1, 1024, 0, strm>>>(P.seg_len, C, off);
+    fused_gather_lanes_kernel<<<C, 256, 0, strm>>>(A.zbuf, zstride, A.lring, (int)nl, lane_room, off, C, zcat);
     if ((st = check()) != GBS_OK) return st;
-    first_cost = 2;
   } else {
     // statistics pass and the starting brackets
     if ((st = pass(kFStats)) != GBS_OK) return st;
     ++npass;
     fused_step_kernel<kFStats><<<sgrid, 256, 0, strm>>>(P);
     if ((st = check()) != GBS_OK) return st;
-  }
-  // cutting-plane passes until every candidate is ready to compact
-  unsigned int h_cnt[2] = {0u, 0u};
-  for (int it = 0; it <= P.maxit + 1; ++it) {
-    if (cudaMemcpyAsync(h_cnt, P.counters, sizeof(h_cnt), cudaMemcpyDeviceToHost, strm) != cudaSuccess ||
-        cudaStreamSynchronize(strm) != cudaSuccess)
-      return GBS_ECUDA;
-    if (h_cnt[0] == 0) break;
-    if (cudaMemsetAsync(P.counters, 0, sizeof(unsigned int), strm) != cudaSuccess) return GBS_ECUDA;
-    A.ring_slot = (first_cost + it) % kRing;
-    P.pass = first_cost + it;
-    if ((st = pass(kFCost)) != GBS_OK) return st;
-    ++npass;
-    fused_step_kernel<kFCost><<<sgrid, 256, 0, strm>>>(P);
+    // cutting-plane passes until every candidate is ready to compact
+    for (int it = 0; it <= P.maxit + 1; ++it) {
+      if (cudaMemcpyAsync(h_cnt, P.counters, sizeof(h_cnt), cudaMemcpyDeviceToHost, strm) != cudaSuccess ||
+          cudaStreamSynchronize(strm) != cudaSuccess)
+        return GBS_ECUDA;
+      if (h_cnt[0] == 0) break;
+      if (cudaMemsetAsync(P.counters, 0, sizeof(unsigned int), strm) != cudaSuccess) return GBS_ECUDA;
+      A.ring_slot = it % kRing;
+      P.pass = it;
+      if ((st = pass(kFCost)) != GBS_OK) return st;
+      ++npass;
+      fused_step_kernel<kFCost><<<sgrid, 256, 0, strm>>>(P);
+      if ((st = check()) != GBS_OK) return st;
+    }
+    // compaction, finish preparation
+    if (cudaMemsetAsync(P.counters, 0, sizeof(unsigned int) * 2, strm) != cudaSuccess) return GBS_ECUDA;
+    fused_offsets_ring_kernel<<<(unsigned int)((C * 32ll + 255) / 256), 256, 0, strm>>>(P);
+    if ((st = pass(kFWrite)) != GBS_OK) return st;
+    npass += 1;
+    fused_step_kernel<kFWrite><<<sgrid, 256, 0, strm>>>(P);
+    fused_offsets_kernel<<<1, 1024, 0, strm>>>(P.seg_len, C, off);
+    fused_gather_kernel<<<C, 256, 0, strm>>>(A.zbuf, zstride, off, C, zcat);
     if ((st = check()) != GBS_OK) return st;
   }
-  // compaction, finish preparation
-  if (cudaMemsetAsync(P.counters, 0, sizeof(unsigned int) * 2, strm) != cudaSuccess) return GBS_ECUDA;
-  fused_offsets_ring_kernel<<<(unsigned int)((C * 32ll + 255) / 256), 256, 0, strm>>>(P);
-  if ((st = pass(kFWrite)) != GBS_OK) return st;
-  npass += 1;
-  fused_step_kernel<kFWrite><<<sgrid, 256, 0, strm>>>(P);
-  fused_offsets_kernel<<<1, 1024, 0, strm>>>(P.seg_len, C, off);
-  fused_gather_kernel<<<C, 256, 0, strm>>>(A.zbuf, off, C, zcat);
-  if ((st = check()) != GBS_OK) return st;
   SegLaunch L;
   if ((st = seg_attach_workspace(c, C, &L)) != GBS_OK) return st;   // already large enough: no reallocation
   L.x = zcat; L.off = off; L.S = C; L.kk = P.kk; L.out = qbuf;
