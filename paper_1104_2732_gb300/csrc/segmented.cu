@@ -195,6 +195,9 @@ struct RadixState {
   unsigned long long rank2;
   unsigned int bucket2;
   int split;                // 1: the two ranks' digits differed in the last round
+  // without a filter: the leading key bits every element shares (set by the caller)
+  int known0;
+  uint32_t prefix0;
 };
 
 constexpr int kRadixV = 2;   // 16-byte loads in flight per thread in the radix sweeps
@@ -285,12 +288,14 @@ __device__ __forceinline__ void radix_gather(const float* buf, int m, bool filte
   radix_sweep<B>(buf, m, fn);
 }
 
-// Known leading key bits of (a, b] (all 32 when a single key lies in it); none without a
-// filter.  (a, b] under IEEE comparison on keys: a zero end takes the key of +0 (x > -0 and
-// x > +0 both exclude the zeros, x <= -0 and x <= +0 both include them).
-__device__ __forceinline__ void radix_known(bool filter, float a, float b, int* known, uint32_t* prefix) {
-  *known = 0;
-  *prefix = 0;
+// Known leading key bits of (a, b] (all 32 when a single key lies in it); without a filter
+// the bits every element shares (known0, prefix0).  (a, b] under IEEE comparison on keys: a
+// zero end takes the key of +0 (x > -0 and x > +0 both exclude the zeros, x <= -0 and
+// x <= +0 both include them).
+__device__ __forceinline__ void radix_known(bool filter, float a, float b, int known0, uint32_t prefix0, int* known,
+                                            uint32_t* prefix) {
+  *known = known0;
+  *prefix = prefix0;
   if (filter) {
     const uint32_t lo = ukey(a == 0.f ? 0.f : a) + 1, hi = ukey(b == 0.f ? 0.f : b);
     const uint32_t diff = lo ^ hi;
@@ -387,7 +392,7 @@ template <int B>
 __device__ __noinline__ uint32_t radix_select(const float* buf, int m, unsigned long long rank, bool filter, float a,
                                               float b, float* zs, int cap, RadixState& st) {
   if (threadIdx.x == 0) {
-    radix_known(filter, a, b, &st.known, &st.prefix);
+    radix_known(filter, a, b, st.known0, st.prefix0, &st.known, &st.prefix);
     st.rank = rank;
   }
   __syncthreads();
@@ -405,7 +410,7 @@ __device__ __noinline__ void radix_select2(const float* buf, int m, unsigned lon
                                            int cap, RadixState& st, uint32_t* key1, uint32_t* key2) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
-    radix_known(filter, a, b, &st.known, &st.prefix);
+    radix_known(filter, a, b, st.known0, st.prefix0, &st.known, &st.prefix);
     st.prefix2 = st.prefix;
     st.rank = rank1;
     st.rank2 = rank2;
@@ -497,6 +502,7 @@ __device__ __noinline__ void radix_select2(const float* buf, int m, unsigned lon
 struct SegShared {
   Sum6 sum6[33];
   float mn[32], mx[32];
+  uint32_t kmn[32], kmx[32];   // per warp: smallest and largest key of a small segment
   RadixState rx;
   uint32_t key1, key2;   // keys of a two-rank select
   unsigned int zcnt;
@@ -690,23 +696,32 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
 
     if (n <= CAP) {
       // ---- small segment: load once, radix select in shared memory ----
-      // load: the scalar head and tail, and the 16-byte body four vectors per thread in flight
+      // load: the scalar head and tail, and the 16-byte body four vectors per thread in flight;
+      // the smallest and largest keys give the leading bits every element shares, where
+      // the radix rounds start
       unsigned int nan_here = 0;
+      uint32_t kmn = 0xffffffffu, kmx = 0u;
+      auto see = [&](float v) {
+        nan_here += (v != v);
+        const uint32_t kv = ukey(v);
+        kmn = min(kmn, kv);
+        kmx = max(kmx, kv);
+      };
       if (tid < g.head) {
         const float v = xs[tid];
-        nan_here += (v != v);
+        see(v);
         zb[tid] = v;
       }
       if (tid < n - g.tail0) {
         const float v = xs[g.tail0 + tid];
-        nan_here += (v != v);
+        see(v);
         zb[g.tail0 + tid] = v;
       }
       {
         const float4* xv = reinterpret_cast<const float4*>(xs + g.head);
         float* zh = zb + g.head;
         auto put = [&](long long q, const float4 r) {
-          nan_here += (r.x != r.x) + (r.y != r.y) + (r.z != r.z) + (r.w != r.w);
+          see(r.x); see(r.y); see(r.z); see(r.w);
           zh[4 * q] = r.x; zh[4 * q + 1] = r.y; zh[4 * q + 2] = r.z; zh[4 * q + 3] = r.w;
         };
         long long q = tid;
@@ -719,9 +734,12 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
         }
         for (; q < g.nv; q += B) put(q, __ldcs(xv + q));
       }
+      kmn = __reduce_min_sync(0xffffffffu, kmn);
+      kmx = __reduce_max_sync(0xffffffffu, kmx);
+      if (lane == 0) { sh.kmn[tid >> 5] = kmn; sh.kmx[tid >> 5] = kmx; }
       Sum6 v6;
       v6.u[0] = nan_here; v6.u[1] = v6.u[2] = v6.u[3] = v6.u[4] = 0; v6.d = 0.0;
-      const Sum6 r6 = cta_sum6<B>(v6, sh.sum6);
+      const Sum6 r6 = cta_sum6<B>(v6, sh.sum6);   // its barriers also publish sh.kmn / sh.kmx
       if (r6.u[0] > 0) {
         if (tid == 0) {
           A.out[s] = NAN;
@@ -731,6 +749,14 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
         }
         __syncthreads();
         continue;
+      }
+      if (tid == 0) {
+        uint32_t lo = sh.kmn[0], hi = sh.kmx[0];
+        for (int w = 1; w < NW; ++w) { lo = min(lo, sh.kmn[w]); hi = max(hi, sh.kmx[w]); }
+        const uint32_t diff = lo ^ hi;
+        const int known = diff == 0 ? 32 : __clz(diff);
+        sh.rx.known0 = known;
+        sh.rx.prefix0 = known == 0 ? 0u : (known == 32 ? hi : (hi >> (32 - known)));
       }
       // trimmed-sum mode: both ranks from shared rounds
       if (LTS) radix_select2<B>(zb, (int)n, (unsigned long long)k, (unsigned long long)k2, false, 0.f, 0.f, nullptr, 0,
