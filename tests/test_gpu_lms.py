@@ -212,12 +212,13 @@ def test_fused_ranks_far_apart_use_the_batched_form(ctx):
     check_against_oracle(lms.cpu().numpy(), lts.cpu().numpy(), X, y, th, k, h)
 
 
-def test_fused_sampled_start_matches_plain_start(ctx):
-    """Brackets proposed by the candidates' order statistics on 8192 sampled rows (checked
-    by counts in the first pass) against the start from the extremes: the same LMS values
-    bit for bit (both select from the same recomputed residuals), LTS within rounding of
-    the sum below the bracket, fewer passes, and both within the oracle's bound."""
-    n, p, C = 300_000, 8, 256
+@pytest.mark.parametrize("p,C,n", [(8, 256, 300_000), (12, 40, 70_001)])
+def test_fused_sampled_start_matches_plain_start(ctx, p, C, n):
+    """Brackets proposed by the candidates' order statistics on 8192 sampled rows (compacted
+    and checked by counts in one pass) against the start from the extremes: the same LMS
+    values bit for bit (both select from the same recomputed residuals), LTS within
+    rounding of the sum below the bracket, fewer passes, and both within the oracle's
+    bound; p = 12 runs the two-block (K = 16) product."""
     X, y, th = problem(n, p, C, seed=96)
     Xt, yt, tt = to_dev(X, y, th)
     k, h = (n + 1) // 2, (n + p + 1) // 2
@@ -232,7 +233,7 @@ def test_fused_sampled_start_matches_plain_start(ctx):
     assert np.array_equal(lp.view(np.uint32), ls.view(np.uint32))
     assert np.all(np.abs(ts - tp) <= 1e-6 * np.abs(tp))
     assert ps < pp, (ps, pp)
-    check_against_oracle(ls, ts, X, y, th, k, h, [0, 17, 255])
+    check_against_oracle(ls, ts, X, y, th, k, h, [0, C // 2, C - 1])
 
 
 def test_fused_nan_row_matches_batched_form(ctx):
