@@ -31,7 +31,8 @@
 // spread rows give order statistics around both ranks, and the proposed bracket (a, b] is
 // compacted straight away in one pass: every lane gets a region of the candidate's buffer
 // sized from the sample's share of (a, b] (1.3 times it plus 6 standard deviations), and
-// the pass counts #(s <= a), the kept elements and the non-finite squares exactly.  When
+// the pass counts #(s <= a), the kept elements and #(s > b) exactly (a NaN square is in none
+// of them, so the three add up to n only without one).  When
 // the bracket holds both ranks and no lane outgrew its region, the lanes' shares are
 // gathered in lane order (each lane's count is kept in the ring) and finished; otherwise
 // the candidate goes to the materialising form.
@@ -78,7 +79,8 @@ struct FusedCand {
 struct FusedTot {
   unsigned long long le, sfix;       // cost pass
   unsigned long long kept, le_a;     // compaction pass: #(a < s <= b), #(s <= a)
-  unsigned long long nonfinite;      // statistics pass; direct compaction pass
+  unsigned long long nonfinite;      // statistics pass
+  unsigned long long gt_b;           // compaction pass: #(s > b)
   unsigned long long overflow;       // direct compaction pass: lanes whose share outgrew their region
   unsigned int mn, mx;               // statistics pass: bits of min / max (s >= 0)
   double sum;                        // statistics: sum of s; compaction: sum of s <= a
@@ -296,9 +298,9 @@ __device__ __forceinline__ void fused_item(const FusedArgs& A, long long item, f
           } else if (MODE == kFCost) {
             core_le(s, pa[j], pt[j], nsig[j], tsig[j], le[j], S[j]);
           } else {
-            // below the bracket: the stage's partial sum; inside: the lane's next slot
-            const bool valid = full || (r0 + lr + (e & 1)) < r_end;
-            nf[j] += (valid && !(s <= FLT_MAX)) ? 1u : 0u;
+            // below the bracket: the stage's partial sum; inside: the lane's next slot; above:
+            // counted (a NaN square, or a row past the end, fails all three tests)
+            nf[j] += (s > pb[j]) ? 1u : 0u;
             const bool below = s <= pa[j];
             const bool keep = (s > pa[j]) & (s <= pb[j]);
             stage_sum[j] += below ? s : 0.f;
@@ -380,7 +382,7 @@ __device__ __forceinline__ void fused_item(const FusedArgs& A, long long item, f
       } else {
         if (lea[j]) atomicAdd(&T.le_a, (unsigned long long)lea[j]);
         if (kept[j]) atomicAdd(&T.kept, (unsigned long long)kept[j]);
-        if (nf[j]) atomicAdd(&T.nonfinite, (unsigned long long)nf[j]);
+        if (nf[j]) atomicAdd(&T.gt_b, (unsigned long long)nf[j]);
         if ((ovf >> j) & 1u) atomicAdd(&T.overflow, 1ull);
         atomicAdd(&T.sum, dsum[j]);
       }
@@ -503,12 +505,14 @@ __global__ void fused_step_kernel(StepArgs P) {
   } else {   // after the write pass: check, and prepare the segmented finish
     int fin = 0;
     if (s.phase == kPhDirect) {
-      // one pass counted #(s <= a), compacted (a, b] into the lanes' regions and summed
-      // s <= a: the bracket holds both ranks, no square is non-finite, no lane's share
-      // outgrew its region and the set fits the finish's shared memory (kFCap, as for the
-      // start from the extremes), or the candidate goes to the fallback
+      // one pass counted #(s <= a), #(s > b), compacted (a, b] into the lanes' regions and
+      // summed s <= a: the bracket holds both ranks, no square is NaN (each row fell in one
+      // of the three ranges; an infinite square above b affects neither objective), no
+      // lane's share outgrew its region and the set fits the finish's shared memory (kFCap,
+      // as for the start from the extremes), or the candidate goes to the fallback
       const long long la = (long long)T.le_a, kept = (long long)T.kept;
-      if (T.nonfinite == 0 && T.overflow == 0 && la < P.k_lo && P.k_hi <= la + kept && kept <= kFCap) {
+      const bool all_rows = la + kept + (long long)T.gt_b == P.n;
+      if (all_rows && T.overflow == 0 && la < P.k_lo && P.k_hi <= la + kept && kept <= kFCap) {
         s.phase = kPhFinish;
         s.cle_a = la; s.cle_b = la + kept; s.clt_b = s.cle_b;
         fin = 1;
@@ -543,7 +547,7 @@ __global__ void fused_step_kernel(StepArgs P) {
   if (s.phase == kPhIter) atomicAdd(&P.counters[0], 1u);
   P.cand[c] = s;
   // totals start from zero for the next pass (min starts at +inf bits)
-  T.le = T.sfix = T.kept = T.le_a = T.nonfinite = T.overflow = 0ull;
+  T.le = T.sfix = T.kept = T.le_a = T.nonfinite = T.gt_b = T.overflow = 0ull;
   T.mn = 0x7F7FFFFFu; T.mx = 0u; T.sum = 0.0;
 }
 
@@ -603,7 +607,7 @@ __global__ void fused_init_kernel(FusedTot* tot, int C, unsigned int* counters) 
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < C) {
     FusedTot& T = tot[c];
-    T.le = T.sfix = T.kept = T.le_a = T.nonfinite = T.overflow = 0ull;
+    T.le = T.sfix = T.kept = T.le_a = T.nonfinite = T.gt_b = T.overflow = 0ull;
     T.mn = 0x7F7FFFFFu; T.mx = 0u; T.sum = 0.0;
   }
   if (c == 0) counters[0] = counters[1] = 0u;

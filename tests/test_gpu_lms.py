@@ -245,6 +245,23 @@ def test_fused_nan_row_matches_batched_form(ctx):
     assert np.all(np.isnan(lms.cpu().numpy()))
 
 
+def test_fused_nan_row_sampled_start(ctx):
+    """A NaN in X on a problem large enough for the sampled start: the one-pass route sees
+    its counts fall short of n and hands every candidate to the batched form (NaN results);
+    an infinite square (huge y) leaves the objectives finite and exact."""
+    n, p, C = 70_001, 8, 12
+    X, y, th = problem(n, p, C, seed=98)
+    Xn = X.copy()
+    Xn[31_337, 5] = np.nan
+    lms, lts, passes = ctx.lms_lts_fused(*to_dev(Xn, y, th))
+    assert passes == 1 and np.all(np.isnan(lms.cpu().numpy()))
+    yi = y.copy()
+    yi[4242] = np.float32(3e38)     # its square overflows to +inf
+    k, h = (n + 1) // 2, (n + p + 1) // 2
+    lms, lts, _ = ctx.lms_lts_fused(*to_dev(X, yi, th), k=k, h=h)
+    check_against_oracle(lms.cpu().numpy(), lts.cpu().numpy(), X, yi, th, k, h, [0, 5, 11])
+
+
 def test_fused_full_size_against_oracle_and_batched(ctx):
     """The benchmark problem (n = 1e6, p = 8, 30% contaminated rows, 2048 candidates):
     12 sampled candidates against the float64 oracle, every candidate within 2e-5 of the
