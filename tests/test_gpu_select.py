@@ -258,6 +258,29 @@ def test_pass_count_matches_cutting_plane_model(ctx):
         assert abs(st["passes"] - info["passes"]) <= 2, (dist, st["passes"], info["passes"])
 
 
+def test_first_iterates_match_cutting_plane_model(ctx):
+    """Pin of the iterate values (Algorithm 1, step 1.1): on continuous data (unique
+    extremes) the GPU's first two tangent intersections equal the float64 model's within
+    1e-5 of the starting bracket's width; they differ only by the rounding of float32
+    partial sums (a swapped slope, a wrong sign or a dropped term moves them by a sizeable
+    part of the bracket)."""
+    n = 2 ** 20
+    for dist in ("uniform", "normal"):
+        x = synth.paper_distribution(dist, n, seed=44)
+        k = (n + 1) // 2
+        _, info = osel.kelley_select(x, k, cap=n // 64)
+        ctx.set_config(cap=n // 64)
+        try:
+            got, st = gpu_select(ctx, x, k)
+        finally:
+            ctx.set_config(cap=0)
+        assert bits(got) == bits(osel.select_kth(x, k))
+        width = float(x.max()) - float(x.min())
+        for i in range(2):
+            assert abs(st["iterates"][i] - info["iterates"][i]) <= 1e-5 * width, (dist, i, st["iterates"][:3],
+                                                                                  info["iterates"][:3])
+
+
 def test_median_entry_point(ctx):
     x = synth.uniform(1_000_000, seed=0)
     got = ctx.median(torch.from_numpy(x).cuda()).cpu().numpy()[0]
