@@ -60,7 +60,7 @@ constexpr int kFVariant = 2;           // segmented variant of the finish (1024 
 constexpr int kRing = 16;              // cost passes whose per-lane counts are kept
 
 enum { kFStats = 0, kFCost = 1, kFWrite = 3 };
-enum { kPhIter = 0, kPhDone = 1, kPhCompact = 2, kPhFallback = 3, kPhFinish = 4, kPhDirect = 6 };
+enum { kPhIter = 0, kPhDone = 1, kPhCompact = 2, kPhFallback = 3, kPhFinish = 4, kPhDirect = 5 };
 constexpr int kSampleRows = 8192;           // rows of the sampled start
 constexpr long long kSampleMinN = 65536;    // smaller problems start from the extremes
 
