@@ -217,6 +217,8 @@ gbs_status gbs_select_segmented_f32(gbs_ctx* ctx, const float* x, const int64_t*
 gbs_status gbs_segmented_autotune_f32(gbs_ctx* ctx, const float* x, const int64_t* offsets, int32_t S,
                                       const int64_t* k, float* out, void* stream, int32_t* chosen,
                                       float* ms_per_variant, int32_t n_variants);
+/* The launch variant of later segmented calls on ctx (0 .. n_variants-1; a new context
+ * uses variant 0: 512 threads, 12288-element shared-memory capacity).  EINVAL otherwise. */
 gbs_status gbs_segmented_set_variant(gbs_ctx* ctx, int32_t variant);
 gbs_status gbs_segmented_get_variant(gbs_ctx* ctx, int32_t* variant, int32_t* threads, int32_t* smem_cap,
                                      int32_t* n_variants);

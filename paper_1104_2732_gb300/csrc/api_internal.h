@@ -30,7 +30,8 @@ struct gbs_ctx {
   size_t z_bytes = 0;
   cudaStream_t last_stream = nullptr;
   int last_grid = 0;
-  int seg_variant = 1;          // launch variant of the segmented select (autotuned)
+  int seg_variant = 0;          // launch variant of the segmented select (autotuned; 0 was fastest on the
+                                // 4096-array benchmark batch in every run)
   int last_segments = 0;
   // LMS / LTS: residual matrix and per-candidate arrays
   void* lms_buf = nullptr;
