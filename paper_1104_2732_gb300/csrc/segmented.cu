@@ -607,27 +607,60 @@ __device__ __noinline__ bool seg_propose(const float* __restrict__ xs, long long
   float* h1 = f + 64;
   float* h2 = h1 + kHid;
   float* o = h2 + kHid;
+  // thread t holds the E consecutive sample keys from position E * t (ascending bitonic
+  // network over the 1024 positions): a stage of distance j < E compares within the
+  // thread, j < 32 E with the lane t ^ (j / E) by a shuffle, longer ones through shared
+  // memory (kb)
+  constexpr int E = kSample / B;
+  static_assert(E >= 1 && E * B == kSample, "the sample is spread evenly over the CTA");
+  const int t = threadIdx.x;
   const long long stride = n / kSample;
   bool bad = false;
-  for (int i = threadIdx.x; i < kSample; i += B) {
-    const float v = xs[i * stride];
+  uint32_t key[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const float v = xs[(long long)(E * t + e) * stride];
     bad |= !(fabsf(v) <= FLT_MAX);
-    kb[i] = ukey(v);
+    key[e] = ukey(v);
   }
   if (__syncthreads_or(bad)) return false;
   for (int k = 2; k <= kSample; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int q = threadIdx.x; q < kSample / 2; q += B) {
-        const int i = 2 * q - (q & (j - 1));   // the pair (i, i + j), bit j of i clear
-        const uint32_t u = kb[i], v = kb[i + j];
-        if ((u > v) == ((i & k) == 0)) {
-          kb[i] = v;
-          kb[i + j] = u;
+      if (j < E) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int e2 = e ^ j;
+          if (e2 > e) {
+            const bool up = (((E * t + e) & k) == 0);
+            const uint32_t u = key[e], v = key[e2];
+            if ((u > v) == up) { key[e] = v; key[e2] = u; }
+          }
         }
+      } else if (j < 32 * E) {
+        const int lanes = j / E;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = E * t + e;
+          const uint32_t w = __shfl_xor_sync(0xffffffffu, key[e], lanes);
+          const bool up = ((i & k) == 0), lower = ((i & j) == 0);
+          key[e] = (up == lower) ? min(key[e], w) : max(key[e], w);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) kb[E * t + e] = key[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = E * t + e;
+          const uint32_t w = kb[i ^ j];
+          const bool up = ((i & k) == 0), lower = ((i & j) == 0);
+          key[e] = (up == lower) ? min(key[e], w) : max(key[e], w);
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
-  for (int i = threadIdx.x; i < kSample; i += B) sv[i] = (double)ukey_value(kb[i], 0.f);
+#pragma unroll
+  for (int e = 0; e < E; ++e) sv[E * t + e] = (double)ukey_value(key[e], 0.f);
   __syncthreads();
   if (threadIdx.x < 32) sketch_features_warp(sv, f, &s_mu, &s_sd);
   __syncthreads();
