@@ -315,6 +315,13 @@ gbs_status gbs_last_stats(gbs_ctx* ctx, gbs_run_stats* out);
 /* Static, human-readable name of a status code. */
 const char* gbs_status_string(gbs_status s);
 
+/* Failure-path check (no paper counterpart): one device-side wait that cannot complete (a
+ * grid barrier of one CTA counting two arrivals) gives up after limit_ns nanoseconds
+ * (1e3 .. 1e9), as every wait of the persistent kernels does after 2 s, and records
+ * GBS_ETIMEOUT in the device status, copied to *device_status (host pointer).
+ * Synchronises stream; the context stays usable.  EINVAL for a bad argument. */
+gbs_status gbs_check_wait_timeout(gbs_ctx* ctx, int64_t limit_ns, int32_t* device_status, void* stream);
+
 /* ---------------------------------------------------------------------------------
  * Sharded selection.  Algorithm 1 (Sec. 3) over a vector split into shards that are
  * reduced separately -- on several devices, in several processes, or as sub-ranges of

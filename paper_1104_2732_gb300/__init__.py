@@ -117,6 +117,7 @@ _SIGS = {
     "gbs_compact_f32": (C.c_int, [_P, _P, _I64, C.c_double, C.c_double, _P, _I64, C.POINTER(_I64), _P]),
     "gbs_compact_f64": (C.c_int, [_P, _P, _I64, C.c_double, C.c_double, _P, _I64, C.POINTER(_I64), _P]),
     "gbs_status_string": (C.c_char_p, [C.c_int]),
+    "gbs_check_wait_timeout": (C.c_int, [_P, _I64, C.POINTER(C.c_int32), _P]),
 }
 
 
@@ -446,6 +447,14 @@ class Context:
         _check(gbs_philox4x32_10(self._h, C.c_void_p(counters.data_ptr()), C.c_void_p(keys.data_ptr()),
                                  C.c_void_p(out.data_ptr()), m, _stream_ptr(stream)), "gbs_philox4x32_10")
         return out
+
+    def check_wait_timeout(self, limit_ns, stream=None):
+        """Runs one device-side wait that cannot complete with a bound of limit_ns
+        nanoseconds and returns the device status it recorded (GBS_ETIMEOUT)."""
+        st = C.c_int32(0)
+        _check(gbs_check_wait_timeout(self._h, int(limit_ns), C.byref(st), _stream_ptr(stream)),
+               "gbs_check_wait_timeout")
+        return st.value
 
     def last_stats(self, raise_on_error=True):
         """Synchronises the last call's stream and returns its record as a dict."""

@@ -13,6 +13,14 @@ using namespace gbs;
 
 namespace {
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// One CTA at a grid barrier that counts two arrivals: the barrier can never complete, so
+// its bounded wait gives up after limit_ns and records GBS_ETIMEOUT (the failure path of
+// every persistent launch, taken without a fault).
+__global__ void wait_probe_kernel(Ctrl* c, unsigned long long limit_ns) {
+  if (!grid_sync(c, 2u, limit_ns)) return;
+  if (threadIdx.x == 0) atomicCAS(&c->status, 0, (int)GBS_EINTERNAL);   // the barrier passed: impossible
+}
 }  // namespace
 
 // ---------------------------------------------------------------------------------
@@ -185,6 +193,25 @@ gbs_status gbs_last_stats(gbs_ctx* c, gbs_run_stats* out) {
     return GBS_ECUDA;
   }
   if (ctrl.status != 0) out->status = ctrl.status;
+  return GBS_OK;
+}
+
+gbs_status gbs_check_wait_timeout(gbs_ctx* c, int64_t limit_ns, int32_t* device_status, void* stream) {
+  if (!c || !device_status || limit_ns < 1000 || limit_ns > 1000000000) return GBS_EINVAL;
+  gbs::DeviceGuard g(c->device);
+  if (!g.ok) return GBS_ECUDA;
+  gbs_status st = gbs_internal_ensure(c, 0);
+  if (st != GBS_OK) return st;
+  cudaStream_t strm = static_cast<cudaStream_t>(stream);
+  Ctrl ctrl;
+  if (cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), strm) != cudaSuccess) return GBS_ECUDA;
+  wait_probe_kernel<<<1, 32, 0, strm>>>(c->ctrl, (unsigned long long)limit_ns);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(strm) != cudaSuccess ||
+      cudaMemcpy(&ctrl, c->ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return GBS_ECUDA;
+  }
+  *device_status = ctrl.status;
   return GBS_OK;
 }
 

@@ -131,10 +131,11 @@ __device__ __forceinline__ unsigned int atom_add_acq_rel_u32(unsigned int* p, un
 // Grid barrier of a cooperative launch.  One acquire-release arrival per CTA on a counter
 // that only grows: barrier number e is passed once the counter reaches (e + 1) * nblocks,
 // and since no CTA can arrive at barrier e + 1 before barrier e is complete, a CTA reads e
-// from the value its own arrival returned.  The wait is bounded: after kWaitLimitNs the
-// CTA records GBS_ETIMEOUT, raises the abort flag and returns false, as does every CTA
-// that sees the abort flag raised.
-__device__ __forceinline__ bool grid_sync(Ctrl* c, unsigned int nblocks) {
+// from the value its own arrival returned.  The wait is bounded: after limit_ns (2 s unless
+// given) the CTA records GBS_ETIMEOUT, raises the abort flag and returns false, as does
+// every CTA that sees the abort flag raised.
+__device__ __forceinline__ bool grid_sync(Ctrl* c, unsigned int nblocks,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -146,7 +147,7 @@ __device__ __forceinline__ bool grid_sync(Ctrl* c, unsigned int nblocks) {
       unsigned int polls = 0;
       while (ld_acquire_u32(&c->bar_count) < target) {
         if (ld_relaxed_i32(&c->abort)) { ok = 0; break; }
-        if ((++polls & 63u) == 0 && globaltimer() - t0 > kWaitLimitNs) {
+        if ((++polls & 63u) == 0 && globaltimer() - t0 > limit_ns) {
           atomicCAS(&c->status, 0, (int)GBS_ETIMEOUT);
           atomicExch(&c->abort, 1);
           ok = 0;

@@ -281,6 +281,20 @@ def test_first_iterates_match_cutting_plane_model(ctx):
                                                                                   info["iterates"][:3])
 
 
+def test_bounded_wait_gives_up_and_context_stays_usable(ctx, lib):
+    """Failure path without a fault: a grid-barrier wait that cannot complete gives up after
+    its bound (2 ms here, 2 s in the kernels) and records GBS_ETIMEOUT; the context then
+    selects correctly."""
+    import time
+    t0 = time.perf_counter()
+    assert ctx.check_wait_timeout(2_000_000) == lib.GBS_ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    x = synth.heavy_mixture("mixture", 300_001, seed=45)
+    k = 150_001
+    got, _ = gpu_select(ctx, x, k)
+    assert bits(got) == bits(osel.select_kth(x, k))
+
+
 def test_median_entry_point(ctx):
     x = synth.uniform(1_000_000, seed=0)
     got = ctx.median(torch.from_numpy(x).cuda()).cpu().numpy()[0]
