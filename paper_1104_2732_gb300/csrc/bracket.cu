@@ -106,7 +106,7 @@ template <typename T>
 __device__ bool sketch(const T* __restrict__ x, long long n, double* sv, float* f, double* mu, double* sd) {
   using K = decltype(ukey(T()));
   __shared__ K kb[2][kSample];
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x;
   if (n < kSample) return false;
   const long long stride = n / kSample;
   const T v = x[tid * stride];
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(kGradWarps * 32) grad_kernel(const float* __re
                                                                 double* __restrict__ loss) {
   __shared__ float g[kNParams];
   __shared__ float fs[kGradWarps][kIn];
-  __shared__ float h1s[kGradWarps][kHid], h2s[kGradWarps][kHid], gu2s[kGradWarps][kHid];
+  __shared__ float h1s[kGradWarps][kHid], gu2s[kGradWarps][kHid];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kNParams; i += blockDim.x) g[i] = 0.f;
   __syncthreads();
@@ -296,7 +296,6 @@ __global__ void __launch_bounds__(kGradWarps * 32) grad_kernel(const float* __re
       for (int i = 0; i < kHid; ++i) u = fmaf(W[kOffW2 + j * kHid + i], h1s[w][i], u);
       u2[q] = u;
       h2v[q] = gelu(u);
-      h2s[w][j] = h2v[q];
     }
     __syncwarp();
     float o0 = 0.f, o1 = 0.f;
@@ -369,7 +368,7 @@ __global__ void adam_kernel(float* __restrict__ W, const float* __restrict__ gra
 gbs_status ensure_model(gbs_ctx* c) {
   if (c->model) return GBS_OK;
   void* p = nullptr;
-  const size_t bytes = sizeof(float) * kNParams * 4 + sizeof(double) * 8;
+  const size_t bytes = sizeof(float) * kNParams * 4;
   if (cudaMalloc(&p, bytes) != cudaSuccess) {
     cudaGetLastError();
     return GBS_ENOMEM;
@@ -378,7 +377,7 @@ gbs_status ensure_model(gbs_ctx* c) {
     cudaFree(p);
     return GBS_ECUDA;
   }
-  c->model = static_cast<float*>(p);   // weights | Adam m | Adam v | gradient | scalars
+  c->model = static_cast<float*>(p);   // weights | Adam m | Adam v | gradient
   c->model_loaded = 0;
   c->adam_t = 0;
   return GBS_OK;
@@ -386,7 +385,6 @@ gbs_status ensure_model(gbs_ctx* c) {
 float* adam_m(gbs_ctx* c) { return c->model + kNParams; }
 float* adam_v(gbs_ctx* c) { return c->model + 2 * kNParams; }
 float* gradbuf(gbs_ctx* c) { return c->model + 3 * kNParams; }
-double* scalars(gbs_ctx* c) { return reinterpret_cast<double*>(c->model + 4 * kNParams); }
 
 }  // namespace
 
