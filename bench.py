@@ -737,9 +737,10 @@ def main():
     torch.cuda.synchronize()
     sort_ms = s0.elapsed_time(s1) / 3
 
-    # ---------------- other rows of the hot path ----------------
+    # ---------------- other rows of the hot path (one GPU: the replicas of N > 1 time only
+    # the headline, so the N GPUs are not held for rows that say nothing about scaling) ----
     rows = {}
-    if not args.only_single:
+    if not args.only_single and world == 1:
         del pinned
         rows["small_n1e6"] = bench_small(gbs, ctx, torch, np, args)
         rows["sharded_4_shards"] = bench_sharded(gbs, ctx, torch, np, args, x)
