@@ -254,13 +254,18 @@ gbs_status gbs_lms_lts_f32(gbs_ctx* ctx, const float* X, const float* y, int64_t
  * plane (Algorithm 1, Sec. 3) recomputes s_ic = (y_i - x_i . theta_c)^2 on the tensor
  * cores (TF32 x 3 split, as precision 1 above) and reduces it per candidate in the
  * product's epilogue; the passes bracket the ranks k_lms and h_lts together, compact each
- * candidate's bracket and finish in the segmented select's trimmed-sum mode.  Candidates
- * whose residuals are not all finite, or whose bracket does not fit the compaction
- * buffer (49152 elements), are recomputed by the batched form of gbs_lms_lts_f32.
- * X: n x p row-major, y: n, theta: C x p row-major, all float32 device arrays (any
- * alignment; p <= 16, n <= 2^31).  Outputs as gbs_lms_lts_f32.  passes (host pointer, may
- * be NULL) receives the number of passes over the rows.  Synchronises `stream` once per
- * pass (the host stops when every candidate is ready to compact). */
+ * candidate's bracket and finish in the segmented select's trimmed-sum mode.  With
+ * gbs_config.lms_start 0 (the default), n >= 65536 and ranks close enough that the
+ * expected bracket fits the compaction buffer, the starting brackets are instead order
+ * statistics of each candidate's squares on 8192 sampled rows, and a single pass over
+ * the rows checks them by exact counts and compacts them.  Candidates whose residuals are
+ * not all finite, whose sampled bracket misses a rank, or whose bracket does not fit the
+ * compaction buffer (49152 elements), are recomputed by the batched form of
+ * gbs_lms_lts_f32.  X: n x p row-major, y: n, theta: C x p row-major, all float32 device
+ * arrays (any alignment; p <= 16, n <= 2^31).  Outputs as gbs_lms_lts_f32.  passes (host
+ * pointer, may be NULL) receives the number of passes over the rows.  Synchronises
+ * `stream` once per cutting-plane pass (the host stops when every candidate is ready to
+ * compact) and once at the end. */
 gbs_status gbs_lms_lts_fused_f32(gbs_ctx* ctx, const float* X, const float* y, int64_t n, int32_t p,
                                  const float* theta, int32_t C, int64_t k_lms, int64_t h_lts,
                                  float* lms_out, double* lts_out, int32_t* passes, void* stream);
