@@ -170,6 +170,20 @@ def test_relative_cost_matches_cost_differences():
             assert osel.relative_cost(x, k, a, t) == pytest.approx(want, rel=1e-12, abs=1e-9)
 
 
+def test_relative_cost_at_tied_data_points():
+    """Bracket ends on data values with ties: the elements equal to a count in the
+    slope #(x <= a), not in the sum over (a, t); those equal to t add t - x = 0.  The
+    difference of Eq. (med_objOS) costs fixes the value for every k."""
+    x = np.array([-2.0, 0.0, 0.0, 0.0, 1.0, 3.0, 3.0, 5.0, 8.0, 8.0], dtype=np.float64)
+    n = x.size
+    for k in range(1, n + 1):
+        for a, t in [(0.0, 3.0), (-2.0, 8.0), (3.0, 5.0), (0.0, 8.0), (1.0, 3.0)]:
+            want = (osel.pinball_cost(x, k, t) - osel.pinball_cost(x, k, a)) / n
+            assert osel.relative_cost(x, k, a, t) == pytest.approx(want, rel=1e-12, abs=1e-12)
+    # k = 5, (a, t) = (0, 3): slope #(x <= 0) - 5 + 1/2 = -1/2 over width 3, plus 3 - 1 = 2
+    assert osel.relative_cost(x, 5, 0.0, 3.0) == -1.5 + 2.0
+
+
 def test_relative_cost_ignores_far_outliers():
     x = np.array([1.0, 2.0, 3.0, 4.0, 1e30, -1e30], dtype=np.float64)
     # only 2 and 3 lie strictly inside (1.5, 3.5)
@@ -205,6 +219,46 @@ def test_kelley_model_ties_infinities_zeros():
     z = np.array([0.0, -0.0] * 50 + [1.0, -1.0] * 10, dtype=np.float32)
     for k in range(1, z.size + 1, 7):
         assert _bits(osel.kelley_select(z, k, cap=4)[0]) == _bits(osel.select_kth(z, k))
+
+
+def test_kelley_model_exhaustive_small_alphabet():
+    """Every array of length <= 4 over {-inf, -1, -0, +0, 2, +inf} and every rank: the
+    hybrid selection returns the rank definition's element, sign of zero included
+    (the early exits at the extremes and at +-inf reach every branch here)."""
+    alph = [-np.inf, -1.0, -0.0, 0.0, 2.0, np.inf]
+    for n in range(1, 5):
+        for tup in itertools.product(alph, repeat=n):
+            x = np.array(tup, dtype=np.float32)
+            for k in range(1, n + 1):
+                got, _ = osel.kelley_select(x, k, cap=1)
+                assert _bits(got) == _bits(_rank_brute(x, k)), (tup, k)
+
+
+def test_kelley_model_integer_ties_every_rank():
+    """Small integer arrays with heavy ties, every rank: the result is the rank
+    definition's element, and after every step the bracket (y_L, y_R] rebuilt from the
+    iterates by the rule of step 1.4 holds exactly the recorded number of elements.
+    Iterates that land on a run of equal values below x_(k) occur in this set."""
+    rng = np.random.default_rng(17)
+    tied_low = 0
+    for _ in range(300):
+        n = int(rng.integers(5, 40))
+        x = rng.integers(0, 6, n).astype(np.float64)
+        for k in range(1, n + 1):
+            got, info = osel.kelley_select(x, k, cap=1)
+            assert got == _rank_brute(x, k), (x.tolist(), k)
+            lo, hi = x.min(), x.max()   # step 0: the extremes
+            for t, pop in zip(info["iterates"], info["pops"]):
+                below, upto = np.count_nonzero(x < t), np.count_nonzero(x <= t)
+                if below < k <= upto:
+                    break
+                if upto < k:
+                    lo = t
+                    tied_low += below < upto
+                else:
+                    hi = t
+                assert pop == np.count_nonzero((x > lo) & (x <= hi)), (x.tolist(), k)
+    assert tied_low > 0
 
 
 def test_kelley_model_permutation_invariant():
