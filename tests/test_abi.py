@@ -66,3 +66,37 @@ def test_struct_sizes_match_header(libpath):
     assert ctypes.sizeof(gbs.gbs_array_stats) == 88
     assert ctypes.sizeof(gbs.gbs_shard_state) == 3 * 8 + 8 * 4 + 5 * 8 + 5 * 8
     assert ctypes.sizeof(gbs.gbs_run_stats) == 4 * 8 + 3 * 8 + 64 * 8 * 2 + 72 * 8 + 64 * 8 + 8
+
+
+def test_struct_layouts_and_constants_match_the_c_compiler(libpath, tmp_path):
+    """Every field offset and struct size of the ctypes mirrors, every GBS_* constant of
+    the binding and its names of the GBS_HOW_* codes equal what a C compiler reads from
+    include/gbselect.h (a field or constant missing from the header fails to compile)."""
+    import paper_1104_2732_gb300 as gbs
+    structs = [gbs.gbs_config, gbs.gbs_run_stats, gbs.gbs_array_stats, gbs.gbs_cost_eval, gbs.gbs_shard_state]
+    consts = sorted(n for n in dir(gbs) if re.fullmatch(r"GBS_[A-Z0-9_]+", n) and isinstance(getattr(gbs, n), int))
+    assert consts
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gbselect.h"', "int main(void) {"]
+    want = []
+    for s in structs:
+        name = s.__name__
+        lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        want.append(f"{name} sizeof {ctypes.sizeof(s)}")
+        for f, _ in s._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+            want.append(f"{name} {f} {getattr(s, f).offset}")
+    for n in consts:
+        lines.append(f'  printf("{n} %lld\\n", (long long)({n}));')
+        want.append(f"{n} {getattr(gbs, n)}")
+    for code, how in sorted(gbs.HOW.items()):   # the binding's names of GBS_HOW_*
+        lines.append(f'  printf("GBS_HOW_{how.upper()} %d\\n", (int)GBS_HOW_{how.upper()});')
+        want.append(f"GBS_HOW_{how.upper()} {code}")
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")[:-1]
+    assert got == want
+
