@@ -88,6 +88,9 @@ MUTANTS = [
     ("select_rank_off_by_one", osel, "select_kth",
      "np.partition(keys, k - 1)[k - 1]", "np.partition(keys, min(k, keys.size - 1))[min(k, keys.size - 1)]", 1,
      [(S, "test_brute_force_all_small_arrays_exhaustive", {}), (S, "test_min_max_special_cases", {})]),
+    ("select_rank_reversed", osel, "select_kth",
+     "np.partition(keys, k - 1)[k - 1]", "np.partition(keys, keys.size - k)[keys.size - k]", 1,
+     [(S, "test_order_statistics_commute_with_monotone_transforms", {})]),
     ("median_rank_rounded_up", osel, "median",
      "(x.size + 1) // 2", "(x.size + 2) // 2", 1,
      [(S, "test_golden_order_statistics_and_costs", {}), (R, "test_lms_brute_force_rank", {})]),
