@@ -184,6 +184,27 @@ def test_select_edge_cases(ctx, dtype):
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_select_monotone_transforms(ctx, dtype):
+    """Sec. 4 (Discussion): order statistics commute with monotone transforms.  exp of the
+    heavy-tailed mixture (long runs of +0 and +inf from under- and overflow), its cube and
+    its reflection: the GPU's x_(k) of F(x) equals the oracle's bit for bit, and equals
+    F(x_(k)) (x_(n-k+1) for the reflection)."""
+    x = synth.heavy_mixture("mixture", 200003, seed=47, dtype=dtype)
+    n = x.size
+    with np.errstate(over="ignore", under="ignore"):
+        images = [(np.exp(x), False), (x * x * x, False), (-x, True)]
+    for Fx, reverse in images:
+        Fx = np.ascontiguousarray(Fx.astype(dtype))
+        for k in ranks(n):
+            got, st = gpu_select(ctx, Fx, k)
+            want = osel.select_kth(Fx, k)
+            assert bits(got) == bits(want), (dtype, k, got, want, st["how"])
+            # F(x_(k)) read from the same transformed array (an element equal to x_(k))
+            base = osel.select_kth(x, n - k + 1 if reverse else k)
+            assert got == Fx[np.flatnonzero(x == base)[0]], (dtype, k)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
 def test_select_huge_outliers_do_not_add_passes(ctx, dtype):
     """Sec. 4 (Discussion): a few values of 1e9 or more leave the cutting plane's pass
     count essentially unchanged."""
