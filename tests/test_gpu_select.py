@@ -369,3 +369,28 @@ def test_whole_array_compaction_fills_every_region(ctx, dtype):
                 check(ctx, x, [1, 2, n // 3, (n + 1) // 2, n - 1, n], offset=offset)
     finally:
         ctx.set_config(cap=0)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_beyond_2_31_elements_rank_property(ctx, dtype):
+    """n = 2^31 + 5 elements (8 or 16 GiB, past every 32-bit element index), read from an
+    offset of one element: the result satisfies the rank definition of Sec. 1,
+    #(x < v) < k <= #(x <= v), with the counts taken by torch on the device.  float32:
+    rounded normals (runs of ~10^7 equal values, +-0) with +-inf; float64: plain normals."""
+    n = 2 ** 31 + 5
+    g = torch.Generator(device="cuda")
+    g.manual_seed(71)
+    buf = torch.empty(n + 1, dtype=dtype, device="cuda")
+    x = buf[1:]
+    x.normal_(generator=g)
+    if dtype == torch.float32:
+        x.mul_(4.0).round_()
+        x[:: 2 ** 24] = float("inf")
+        x[7:: 2 ** 24] = float("-inf")
+    for k in (1, n // 3, (n + 1) // 2, n - 7, n):
+        v = ctx.select_kth(x, k)
+        lt = int((x < v).sum())
+        le = int((x <= v).sum())
+        assert lt < k <= le, (dtype, k, v.item(), lt, le, ctx.last_stats()["how"])
+    del x, buf
+    torch.cuda.empty_cache()
