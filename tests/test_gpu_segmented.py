@@ -289,3 +289,29 @@ def test_segmented_full_size_batch_sampled(ctx):
     for s in sorted(check):
         seg = x[off[s]:off[s + 1]]
         assert bits(got[s]) == bits(np.float32(osel.select_kth(seg, (seg.size + 1) // 2))), s
+
+
+def test_batch_beyond_2_31_elements_rank_property(ctx):
+    """4096 segments of 524291 float32 elements (2^31 + 12288 in all, so the later
+    segments start past every 32-bit element offset), medians and a low rank: every
+    result satisfies the rank definition #(x_s < v_s) < k_s <= #(x_s <= v_s) of Sec. 1,
+    counted by torch on the device.  Rounded normals with per-segment scales give runs of
+    equal values and +-0."""
+    S, m = 4096, 524291
+    g = torch.Generator(device="cuda")
+    g.manual_seed(73)
+    x = torch.empty(S * m, dtype=torch.float32, device="cuda")
+    x.normal_(generator=g)
+    X = x.view(S, m)
+    scale = torch.pow(10.0, torch.linspace(-1.0, 2.0, S, device="cuda"))
+    X.mul_(scale[:, None]).round_()
+    off = torch.arange(S + 1, dtype=torch.int64, device="cuda") * m
+    for kk in (None, torch.full((S,), m // 100, dtype=torch.int64, device="cuda")):
+        out = ctx.select_segmented(x, off, kk)
+        k = torch.full((S,), (m + 1) // 2, dtype=torch.int64, device="cuda") if kk is None else kk
+        lt = (X < out[:, None]).sum(1)
+        le = (X <= out[:, None]).sum(1)
+        bad = ~((lt < k) & (k <= le))
+        assert int(bad.sum()) == 0, int(bad.nonzero()[0])
+    del X, x
+    torch.cuda.empty_cache()
