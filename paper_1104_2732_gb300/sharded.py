@@ -8,7 +8,8 @@ runs on a shard through a *backend*, and the per-pass totals are formed by a *co
 
 * backend (per-shard work): ``stats(x) -> dict`` (the gbs_array_stats fields),
   ``cost_pass(x, a, t) -> dict`` (c_lt_t, c_le_t, c_le_a, S), ``compact(x, a, b) ->
-  shard's elements of (a, b]``, ``select(z, r) -> z_(r)`` and ``concat(list)``.
+  shard's elements of (a, b]``, ``select(z, r) -> z_(r)``, ``concat(list)`` and
+  ``empty(elem_bytes)`` (a set of no elements, for a process that holds none).
   :class:`GpuBackend` runs them with a :class:`~paper_1104_2732_gb300.Context`.
 * comm (totals over processes): ``sum_i64``, ``sum_f64``, ``min_f64``, ``max_f64`` on
   lists of numbers and ``gather(z)`` of the compacted sets.  :class:`LocalComm` is one
@@ -125,6 +126,11 @@ class GpuBackend:
         import torch
         return torch.cat(list(zs)) if zs else None
 
+    def empty(self, elem_bytes):
+        import torch
+        return torch.empty(0, dtype=torch.float32 if elem_bytes == 4 else torch.float64,
+                           device=f"cuda:{self.ctx.device}")
+
     def select(self, z, r):
         return float(self.ctx.select_kth(z, r).item())
 
@@ -132,12 +138,12 @@ class GpuBackend:
 def select_kth_sharded(shards, k, backend, comm=None, elem_bytes=4, cap=0, maxit=0, trace=None):
     """x_(k) of the concatenation of the shards of every process (1-based k).
 
-    ``shards``: this process's shards (any number, empty ones allowed); ``k`` is the rank
-    in the whole vector.  Returns a Python float holding the element (``-0.0`` kept)."""
+    ``shards``: this process's shards (any number, empty ones allowed: a process with no
+    element still takes part in every collective, with zero counts and an empty set at
+    the gather); ``k`` is the rank in the whole vector.  Returns a Python float holding
+    the element (``-0.0`` kept)."""
     comm = comm or LocalComm()
     shards = [s for s in shards if s is not None and len(s) > 0]
-    if not shards:
-        raise ValueError("every process needs at least one non-empty shard")
     # pass 0 on every shard (Sec. 3, step 0), totals over the shards and processes
     st = [backend.stats(s) for s in shards]
     sums = comm.sum_i64([sum(int(r[f]) for r in st) for f in _STAT_SUMS])
@@ -175,6 +181,6 @@ def select_kth_sharded(shards, k, backend, comm=None, elem_bytes=4, cap=0, maxit
     # finish: compaction of (a, b] on every shard, selection inside the union (Sec. 3)
     assert state.phase == GBS_SHARD_COMPACT
     local = [backend.compact(s, state.a, state.b) for s in shards]
-    z = comm.gather(backend.concat(local), backend)
+    z = comm.gather(backend.concat(local) if local else backend.empty(elem_bytes), backend)
     r = int(k - state.cle_a)
     return backend.select(z, r)

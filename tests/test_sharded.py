@@ -45,6 +45,9 @@ class NumpyBackend:
     def concat(self, zs):
         return np.concatenate([np.asarray(z) for z in zs])
 
+    def empty(self, elem_bytes):
+        return np.empty(0, dtype=np.float32 if elem_bytes == 4 else np.float64)
+
     def select(self, z, r):
         return float(osel.select_kth(z, r))
 
@@ -88,6 +91,32 @@ def test_sharded_matches_oracle(name, make):
         select_kth_sharded([y[:100], y[100:]], 1, NumpyBackend(), elem_bytes=eb)
 
 
+def test_sharded_empty_and_single_element_shards():
+    """Empty shards anywhere in the list, single-element shards, and data that are all
+    infinite: the result is the single-array one bit for bit."""
+    gbs()
+    from paper_1104_2732_gb300.sharded import select_kth_sharded
+    x = synth.heavy_mixture("mixture", 5001, seed=2)
+    layouts = ([x[:0], x], [x, x[:0]], [x[:0], x[:10], x[10:10], x[10:]], [x[:1], x[1:]], [x[:1], x[1:2], x[2:]])
+    for shards in layouts:
+        for k in (1, 2, 2500, 5000, 5001):
+            got = select_kth_sharded(shards, k, NumpyBackend(), elem_bytes=4, cap=64)
+            assert bits(got, np.float32) == bits(osel.select_kth(x, k), np.float32), (len(shards), k)
+    y = np.array([np.inf] * 3 + [-np.inf] * 2, dtype=np.float32)
+    for k in range(1, 6):
+        got = select_kth_sharded([y[:2], y[2:], y[:0]], k, NumpyBackend(), elem_bytes=4)
+        assert bits(got, np.float32) == bits(osel.select_kth(y, k), np.float32), k
+
+
+def test_sharded_no_elements_at_all_is_rejected():
+    g = gbs()
+    from paper_1104_2732_gb300.sharded import select_kth_sharded
+    e = np.empty(0, dtype=np.float32)
+    for shards in ([], [e, e]):
+        with pytest.raises(g.GbsError):
+            select_kth_sharded(shards, 1, NumpyBackend(), elem_bytes=4)
+
+
 def test_state_machine_rejects_bad_totals():
     g = gbs()
     import ctypes as C
@@ -116,7 +145,16 @@ def _free_port():
     return p
 
 
-def _rank_main(rank, world, port, out):
+GLOO_RANKS = (1, 400, 20005, 39000, 40009)
+
+
+def _gloo_data(layout):
+    if layout == "two_each":
+        return synth.heavy_mixture("mixture", 40009, seed=11)
+    return synth.heavy_mixture("cauchy", 40009, seed=12, dtype=np.float64)
+
+
+def _rank_main(rank, world, port, out, layout):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -124,33 +162,39 @@ def _rank_main(rank, world, port, out):
     try:
         import paper_1104_2732_gb300  # noqa: F401  (built by the parent)
         from paper_1104_2732_gb300.sharded import TorchComm, select_kth_sharded
-        x = synth.heavy_mixture("mixture", 40009, seed=11)
-        own = split(x, 4, seed=3)[rank * 2:(rank + 1) * 2]     # two shards per rank
+        x = _gloo_data(layout)
+        if layout == "two_each":
+            own = split(x, 4, seed=3)[rank * 2:(rank + 1) * 2]     # two shards per rank
+        else:
+            own = [x] if rank == 0 else []                        # rank 1 holds no element
         res = []
-        for k in (1, 400, 20005, 39000, 40009):
-            res.append(select_kth_sharded(own, k, NumpyBackend(), TorchComm(), elem_bytes=4, cap=1000))
+        for k in GLOO_RANKS:
+            res.append(select_kth_sharded(own, k, NumpyBackend(), TorchComm(), elem_bytes=x.itemsize, cap=1000))
         out.put((rank, res))
     finally:
         dist.destroy_process_group()
 
 
-def test_sharded_two_gloo_ranks():
+@pytest.mark.parametrize("layout", ["two_each", "one_rank_empty"])
+def test_sharded_two_gloo_ranks(layout):
+    """Two gloo ranks: two shards each (float32), or every element on rank 0 and none on
+    rank 1 (float64); both ranks return the single-array result."""
     gbs()
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q, layout)) for r in range(2)]
     for p in procs:
         p.start()
     got = dict(q.get(timeout=240) for _ in procs)
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    x = synth.heavy_mixture("mixture", 40009, seed=11)
-    want = [osel.select_kth(x, k) for k in (1, 400, 20005, 39000, 40009)]
+    x = _gloo_data(layout)
+    want = [osel.select_kth(x, k) for k in GLOO_RANKS]
     for r in (0, 1):
-        assert [bits(v, np.float32) for v in got[r]] == [bits(v, np.float32) for v in want]
+        assert [bits(v, x.dtype) for v in got[r]] == [bits(v, x.dtype) for v in want]
 
 
 @pytest.mark.gpu
