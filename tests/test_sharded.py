@@ -214,3 +214,56 @@ def test_sharded_gpu_shards_match_oracle(lib, dtype):
                 assert bits(got, x.dtype) == bits(want, x.dtype), (fam, k, got, want)
     finally:
         ctx.close()
+
+
+class _FailingBackend(NumpyBackend):
+    """Raises on its third cost pass (a host-side failure of one rank between passes)."""
+
+    def __init__(self):
+        self.calls = 0
+
+    def cost_pass(self, x, a, t):
+        self.calls += 1
+        if self.calls == 3:
+            raise RuntimeError("injected failure on this rank")
+        return super().cost_pass(x, a, t)
+
+
+def _failing_rank_main(rank, world, port, out):
+    import datetime
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    import paper_1104_2732_gb300  # noqa: F401  (built by the parent)
+    from paper_1104_2732_gb300.sharded import TorchComm, select_kth_sharded
+    x = synth.heavy_mixture("mixture", 40009, seed=11)
+    own = split(x, 2, seed=3)[rank:rank + 1]
+    backend = _FailingBackend() if rank == 1 else NumpyBackend()
+    try:
+        select_kth_sharded(own, 20005, backend, TorchComm(), elem_bytes=4, cap=10)
+        out.put((rank, "finished"))
+    except Exception as e:   # the injected failure (rank 1) or the failed collective (rank 0)
+        out.put((rank, type(e).__name__))
+    # no destroy_process_group: the peer may be gone
+
+
+def test_sharded_rank_failure_surfaces_on_the_other_rank():
+    """A rank that fails between passes (an exception on the host, no GPU involved) ends
+    the other rank's next collective with an error within the process group's timeout,
+    instead of leaving it waiting."""
+    gbs()
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=30)
+        if p.is_alive():
+            p.kill()
+    assert got[1] == "RuntimeError"
+    assert got[0] != "finished"
