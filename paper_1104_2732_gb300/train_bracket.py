@@ -1,6 +1,6 @@
 """Trains the bracket-proposal network on the GPU with the library's own kernels.
 
-Usage: ``python paper_1104_2732_gb300/train_bracket.py [--arrays N] [--steps S] [--out PATH]``
+Usage: ``python paper_1104_2732_gb300/train_bracket.py [--arrays N] [--steps S] [--out PATH] [--resume CKPT]``
 
 Training data: N arrays generated on the device (Philox4x32-10) with n log-uniform in
 [2^20, 2^24] from four families -- normal, Student-t with nu in {1,...,5}, lognormal with
@@ -81,6 +81,16 @@ def init_weights(seed, np):
     return np.concatenate([b.ravel() for b in blocks]).astype(np.float32)
 
 
+def checkpoint_step(path):
+    """The Adam step stored in a GBSBRKT1 checkpoint (u64 little-endian after the 8-byte
+    magic and five u32 header words)."""
+    with open(path, "rb") as f:
+        head = f.read(36)
+    if len(head) != 36 or head[:8] != b"GBSBRKT1":
+        raise ValueError(f"{path} is not a bracket-model checkpoint")
+    return int.from_bytes(head[28:36], "little")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--arrays", type=int, default=100_000)
@@ -88,6 +98,9 @@ def main():
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default=DEFAULT_MODEL)
+    ap.add_argument("--resume", default=None,
+                    help="checkpoint to continue from (weights, Adam moments and step); the "
+                         "row permutation is then seeded from the stored step")
     args = ap.parse_args()
 
     import numpy as np
@@ -99,9 +112,14 @@ def main():
     t0 = time.time()
     F, Z = make_dataset(ctx, args.arrays, 10 ** 6, torch, np)
     print(f"dataset: {F.shape[0]} arrays in {time.time() - t0:.1f} s", flush=True)
-    ctx.set_bracket_model(init_weights(0, np))
+    seed = 1
+    if args.resume:
+        ctx.load_bracket_model(args.resume)
+        seed = 1 + checkpoint_step(args.resume)
+    else:
+        ctx.set_bracket_model(init_weights(0, np))
     t1 = time.time()
-    hist = ctx.bracket_train(F, Z, args.batch, args.steps, lr=args.lr, seed=1)
+    hist = ctx.bracket_train(F, Z, args.batch, args.steps, lr=args.lr, seed=seed)
     print(f"trained {args.steps} steps in {time.time() - t1:.1f} s; loss {hist[0]:.4f} -> "
           f"{np.mean(hist[-100:]):.4f}", flush=True)
     ctx.save_bracket_model(args.out)

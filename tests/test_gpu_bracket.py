@@ -184,6 +184,35 @@ def test_model_checkpoint_roundtrip(ctx, tmp_path):
         ctx.load_bracket_model(path)
 
 
+def test_checkpoint_keeps_optimizer_state_for_resume(ctx, lib, tmp_path):
+    """A checkpoint holds the Adam step and both moments besides the weights: after two
+    training steps the file records step 2 and non-zero moments, and a fresh context that
+    loads it writes the same bytes back, so training resumes from step 2."""
+    from paper_1104_2732_gb300 import train_bracket as tb
+    rng = np.random.default_rng(209)
+    B = 256
+    F = rng.normal(size=(B, 36)).astype(np.float32)
+    Z = (0.3 * F[:, 0] + 0.1 * rng.normal(size=B)).astype(np.float32)
+    ctx.set_bracket_model(random_weights(9))
+    ctx.bracket_train(torch.from_numpy(F).cuda(), torch.from_numpy(Z).cuda(), batch=B, steps=2, lr=1e-3, seed=0)
+    p1, p2 = str(tmp_path / "a.bin"), str(tmp_path / "b.bin")
+    ctx.save_bracket_model(p1)
+    raw = open(p1, "rb").read()
+    n = ob.N_PARAMS
+    assert len(raw) == 8 + 20 + 8 + 12 * n
+    assert tb.checkpoint_step(p1) == 2
+    body = np.frombuffer(raw[36:], dtype="<f4").reshape(3, n)
+    assert np.array_equal(body[0], ctx.get_bracket_model())
+    assert np.count_nonzero(body[1]) > n // 2 and np.count_nonzero(body[2]) > n // 2
+    c2 = lib.Context()
+    try:
+        c2.load_bracket_model(p1)
+        c2.save_bracket_model(p2)
+    finally:
+        c2.close()
+    assert open(p2, "rb").read() == raw
+
+
 @pytest.mark.skipif(not os.path.exists(MODEL), reason="no trained model in the package")
 def test_trained_model_saves_passes_on_held_out_arrays(ctx):
     """Held-out arrays (generator seeds 2e6 + i): identical medians, fewer passes with
