@@ -66,3 +66,24 @@ def test_residual_sign_and_shape():
     th = np.array([[1.0, 0.0], [1.0, 1.0]], dtype=np.float32)
     r = oreg.residuals(X, y, th)
     assert r.tolist() == [[2.0, 3.0], [-1.0, 2.0]]
+
+
+def test_extreme_ranks_and_row_permutation():
+    """LTS with h = n is the full sum of squares and with h = 1 the smallest square; LMS at
+    k = 1 and k = n are the smallest and largest squares; both objectives are invariant
+    under a permutation of the rows (Sec. 5: they depend on the residuals' multiset)."""
+    X, y, _ = synth.regression(301, 4, seed=16)
+    th = synth.elemental_thetas(X, y, 3, seed=17)
+    r = oreg.residuals(X, y, th)
+    s = r * r
+    n = s.shape[0]
+    for c in range(3):
+        sc = s[:, c]
+        assert oreg.lts(sc, n) == pytest.approx(math.fsum(sc.tolist()), rel=1e-15)
+        assert oreg.lts(sc, 1) == sc.min()
+        assert oreg.lms(sc, 1) == sc.min() and oreg.lms(sc, n) == sc.max()
+    perm = np.random.default_rng(18).permutation(n)
+    a = oreg.lms_lts(X, y, th, k=151, h=153)
+    b = oreg.lms_lts(X[perm], y[perm], th, k=151, h=153)
+    assert np.array_equal(a[0], b[0])
+    assert np.allclose(a[1], b[1], rtol=1e-15, atol=0)
