@@ -157,13 +157,32 @@ def _suffix(x):
     raise TypeError(f"float32 or float64 expected, got {x.dtype}")
 
 
-def _as_input(x):
+def _require(t, name, dtype=None, dim=None, cols=None, numel=None, min_numel=None, device=None):
+    """Checks a tensor before its pointer crosses the ABI, where the kernels take sizes
+    from the other arguments: element type, rank, row width and element count first (a
+    short buffer would be read or written past its end), then that it is a contiguous
+    CUDA tensor on the context's device."""
     import torch
-    if not isinstance(x, torch.Tensor) or not x.is_cuda:
-        raise TypeError("a CUDA tensor is required")
-    if not x.is_contiguous():
-        raise ValueError("a contiguous tensor is required")
-    return x
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: a torch tensor is required")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name}: {dtype} expected, got {t.dtype}")
+    if dim is not None and t.dim() != dim:
+        raise ValueError(f"{name}: {dim}-d expected, got shape {tuple(t.shape)}")
+    if cols is not None and t.shape[-1] != cols:
+        raise ValueError(f"{name}: rows of {cols} expected, got shape {tuple(t.shape)}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name}: {numel} elements expected, got {t.numel()}")
+    if min_numel is not None and t.numel() < min_numel:
+        raise ValueError(f"{name}: at least {min_numel} elements expected, got {t.numel()}")
+    if not t.is_cuda:
+        raise TypeError(f"{name}: a CUDA tensor is required")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: a contiguous tensor is required")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the context on cuda:{device}")
+    return t
+
 
 
 class Context:
@@ -193,8 +212,15 @@ class Context:
     def handle(self):
         return self._h
 
+    def _in(self, t, name, **kw):
+        return _require(t, name, device=self.device, **kw)
+
     # -------------------------------------------------------------- configuration
     def set_config(self, **kw):
+        known = {f for f, _ in gbs_config._fields_ if f != "reserved"}
+        unknown = sorted(set(kw) - known)
+        if unknown:
+            raise TypeError(f"unknown configuration keys {unknown}; known: {sorted(known)}")
         cfg = gbs_config()
         _check(gbs_get_config(self._h, C.byref(cfg)), "gbs_get_config")
         for key, val in kw.items():
@@ -214,9 +240,10 @@ class Context:
     def select_kth(self, x, k, out=None, stream=None):
         """x_(k) of a contiguous CUDA tensor (1-based k); returns a 1-element device tensor."""
         import torch
-        x = _as_input(x)
+        x = self._in(x, "x")
         if out is None:
             out = torch.empty(1, dtype=x.dtype, device=x.device)
+        self._in(out, "out", dtype=x.dtype, min_numel=1)
         fn = globals()["gbs_select_kth_" + _suffix(x)]
         _check(fn(self._h, C.c_void_p(x.data_ptr()), x.numel(), int(k), C.c_void_p(out.data_ptr()),
                   _stream_ptr(stream)), "gbs_select_kth")
@@ -224,9 +251,10 @@ class Context:
 
     def median(self, x, out=None, stream=None):
         import torch
-        x = _as_input(x)
+        x = self._in(x, "x")
         if out is None:
             out = torch.empty(1, dtype=x.dtype, device=x.device)
+        self._in(out, "out", dtype=x.dtype, min_numel=1)
         fn = globals()["gbs_median_" + _suffix(x)]
         _check(fn(self._h, C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(out.data_ptr()),
                   _stream_ptr(stream)), "gbs_median")
@@ -234,7 +262,7 @@ class Context:
 
     def array_stats(self, x, stream=None):
         import torch
-        x = _as_input(x)
+        x = self._in(x, "x")
         buf = torch.empty(C.sizeof(gbs_array_stats), dtype=torch.uint8, device=x.device)
         fn = globals()["gbs_array_stats_" + _suffix(x)]
         _check(fn(self._h, C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(buf.data_ptr()),
@@ -244,7 +272,7 @@ class Context:
 
     def cost_pass(self, x, k, a, t, stream=None):
         import torch
-        x = _as_input(x)
+        x = self._in(x, "x")
         buf = torch.empty(C.sizeof(gbs_cost_eval), dtype=torch.uint8, device=x.device)
         fn = globals()["gbs_cost_pass_" + _suffix(x)]
         _check(fn(self._h, C.c_void_p(x.data_ptr()), x.numel(), int(k), float(a), float(t),
@@ -256,9 +284,10 @@ class Context:
         """The elements of x in (a, b] (any order), as a view of z (allocated with room
         for all of x when None)."""
         import torch
-        x = _as_input(x)
+        x = self._in(x, "x")
         if z is None:
             z = torch.empty(x.numel(), dtype=x.dtype, device=x.device)
+        self._in(z, "z", dtype=x.dtype)
         cnt = _I64(0)
         fn = globals()["gbs_compact_" + _suffix(x)]
         _check(fn(self._h, C.c_void_p(x.data_ptr()), x.numel(), float(a), float(b), C.c_void_p(z.data_ptr()),
@@ -268,19 +297,14 @@ class Context:
     # -------------------------------------------------------------- segmented
     def _seg_args(self, x, offsets, k, out):
         import torch
-        x = _as_input(x)
-        if x.dtype != torch.float32:
-            raise TypeError("the segmented select takes float32")
-        offsets = _as_input(offsets)
-        if offsets.dtype != torch.int64:
-            raise TypeError("offsets must be int64")
+        x = self._in(x, "x", dtype=torch.float32)
+        offsets = self._in(offsets, "offsets", dtype=torch.int64, min_numel=1)
         S = offsets.numel() - 1
         if k is not None:
-            k = _as_input(k)
-            if k.dtype != torch.int64 or k.numel() != S:
-                raise TypeError("k must be int64 with one rank per segment")
+            k = self._in(k, "k", dtype=torch.int64, numel=S)
         if out is None:
             out = torch.empty(S, dtype=torch.float32, device=x.device)
+        self._in(out, "out", dtype=torch.float32, min_numel=S)
         kp = C.c_void_p(k.data_ptr()) if k is not None else None
         return x, offsets, S, kp, out
 
@@ -320,13 +344,11 @@ class Context:
     # -------------------------------------------------------------- robust regression
     def _reg_args(self, X, y, theta):
         import torch
-        X, y, theta = _as_input(X), _as_input(y), _as_input(theta)
-        for t in (X, y, theta):
-            if t.dtype != torch.float32:
-                raise TypeError("X, y and theta must be float32")
+        X = self._in(X, "X", dtype=torch.float32, dim=2)
         n, p = X.shape
-        if theta.dim() != 2 or theta.shape[1] != p:
-            raise ValueError("theta must be (C, p): one row of p coefficients per candidate")
+        y = self._in(y, "y", dtype=torch.float32, numel=n)
+        theta = self._in(theta, "theta (C, p): one row of p coefficients per candidate", dtype=torch.float32,
+                         dim=2, cols=p)
         return X, y, theta, n, p, theta.shape[0]
 
     def residual_sq(self, X, y, theta, precision=1, out=None, stream=None):
@@ -335,6 +357,7 @@ class Context:
         X, y, theta, n, p, Cn = self._reg_args(X, y, theta)
         if out is None:
             out = torch.empty(Cn, n, dtype=torch.float32, device=X.device)
+        self._in(out, "out", dtype=torch.float32, min_numel=Cn * n)
         _check(gbs_residual_sq_f32(self._h, C.c_void_p(X.data_ptr()), C.c_void_p(y.data_ptr()), n, p,
                                    C.c_void_p(theta.data_ptr()), Cn, C.c_void_p(out.data_ptr()), int(precision),
                                    _stream_ptr(stream)), "gbs_residual_sq")
@@ -372,6 +395,13 @@ class Context:
 
     # -------------------------------------------------------------- learned bracket
     N_PARAMS = 6658
+    N_FEATURES = 36
+
+    def _train_args(self, F, Z):
+        import torch
+        F = self._in(F, "F (B, 36 features)", dtype=torch.float32, dim=2, cols=self.N_FEATURES)
+        Z = self._in(Z, "Z (B standardised medians)", dtype=torch.float32, numel=F.shape[0])
+        return F, Z
 
     def set_bracket_model(self, weights):
         import numpy as np
@@ -392,7 +422,7 @@ class Context:
 
     def bracket_features(self, x, stream=None):
         import torch
-        x = _as_input(x)
+        x = self._in(x, "x", dtype=torch.float32)
         feat = torch.empty(36, dtype=torch.float32, device=x.device)
         musd = torch.empty(2, dtype=torch.float64, device=x.device)
         _check(gbs_bracket_features_f32(self._h, C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(feat.data_ptr()),
@@ -401,7 +431,7 @@ class Context:
 
     def bracket_propose(self, x, stream=None):
         import torch
-        x = _as_input(x)
+        x = self._in(x, "x", dtype=torch.float32)
         out = torch.empty(3, dtype=torch.float64, device=x.device)
         _check(gbs_bracket_propose_f32(self._h, C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(out.data_ptr()),
                                        _stream_ptr(stream)), "gbs_bracket_propose")
@@ -409,7 +439,7 @@ class Context:
 
     def bracket_forward(self, F, stream=None):
         import torch
-        F = _as_input(F)
+        F = self._in(F, "F (B, 36 features)", dtype=torch.float32, dim=2, cols=self.N_FEATURES)
         out = torch.empty(F.shape[0], 2, dtype=torch.float32, device=F.device)
         _check(gbs_bracket_forward(self._h, C.c_void_p(F.data_ptr()), F.shape[0], C.c_void_p(out.data_ptr()),
                                    _stream_ptr(stream)), "gbs_bracket_forward")
@@ -417,7 +447,7 @@ class Context:
 
     def bracket_grad(self, F, Z, stream=None):
         import torch
-        F, Z = _as_input(F), _as_input(Z)
+        F, Z = self._train_args(F, Z)
         grad = torch.empty(self.N_PARAMS, dtype=torch.float32, device=F.device)
         loss = torch.empty(1, dtype=torch.float64, device=F.device)
         _check(gbs_bracket_grad(self._h, C.c_void_p(F.data_ptr()), C.c_void_p(Z.data_ptr()), F.shape[0],
@@ -426,14 +456,15 @@ class Context:
         return grad, loss
 
     def bracket_train(self, F, Z, batch, steps, lr=1e-3, seed=0, stream=None):
-        F, Z = _as_input(F), _as_input(Z)
+        F, Z = self._train_args(F, Z)
         hist = (C.c_float * int(steps))()
         _check(gbs_bracket_train(self._h, C.c_void_p(F.data_ptr()), C.c_void_p(Z.data_ptr()), F.shape[0], int(batch),
                                  int(steps), float(lr), int(seed), hist, _stream_ptr(stream)), "gbs_bracket_train")
         return list(hist)
 
     def generate_training_array(self, out, family, p0=0.0, p1=0.0, p2=1.0, loc=0.0, scale=1.0, seed=0, stream=None):
-        out = _as_input(out)
+        import torch
+        out = self._in(out, "out", dtype=torch.float32)
         _check(gbs_generate_training_array_f32(self._h, C.c_void_p(out.data_ptr()), out.numel(), int(family),
                                                float(p0), float(p1), float(p2), float(loc), float(scale), int(seed),
                                                _stream_ptr(stream)), "gbs_generate_training_array")
@@ -441,8 +472,11 @@ class Context:
 
     def philox(self, counters, keys, stream=None):
         import torch
-        counters, keys = _as_input(counters), _as_input(keys)
+        if isinstance(counters, torch.Tensor) and counters.numel() % 4:
+            raise ValueError("counters: a multiple of 4 words expected")
+        counters = self._in(counters, "counters (m x 4 words)", dtype=torch.int32)
         m = counters.numel() // 4
+        keys = self._in(keys, "keys (m x 2 words)", dtype=torch.int32, numel=2 * m)
         out = torch.empty(4 * m, dtype=torch.int32, device=counters.device)
         _check(gbs_philox4x32_10(self._h, C.c_void_p(counters.data_ptr()), C.c_void_p(keys.data_ptr()),
                                  C.c_void_p(out.data_ptr()), m, _stream_ptr(stream)), "gbs_philox4x32_10")
