@@ -13,7 +13,8 @@ Modules
 -------
 select      exact order statistics, counts, the pinball cost, Kelley's cutting plane
 regression  LMS / LTS objectives of robust regression
+knn         k-nearest-neighbour regression and classification through d_(k)
 bracket     sketch features and the bracket-proposal MLP (float64 forward/backward)
 philox      the Philox4x32-10 counter-based generator (for the training-data generator)
 """
-from . import select, regression, bracket, philox  # noqa: F401
+from . import select, regression, knn, bracket, philox  # noqa: F401

@@ -1,0 +1,156 @@
+"""Pins of the kNN oracle (Sec. 5, last application) by brute force over neighbour sets,
+closed forms and invariances.  CPU only."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import knn as ok
+
+
+def _d2_loop(X, q):
+    """Squared distances by plain loops (independent of the oracle's einsum)."""
+    return [sum((float(q[t]) - float(x[t])) ** 2 for t in range(len(q))) for x in X]
+
+
+def _nearest_sets(d2, k):
+    """Every k-subset that is a valid set of k nearest points (ties broken any way)."""
+    n = len(d2)
+    sets = []
+    for S in itertools.combinations(range(n), k):
+        inside = max(d2[i] for i in S)
+        outside = min((d2[i] for i in range(n) if i not in S), default=math.inf)
+        if inside <= outside:
+            sets.append(S)
+    return sets
+
+
+def _w(d, kind, eps=1e-6):
+    return 1.0 if kind == "uniform" else 1.0 / (d + eps)
+
+
+def test_squared_distances_hand_worked():
+    X = np.array([[0.0, 0.0], [3.0, 4.0], [1.0, 1.0]])
+    assert ok.squared_distances(X, np.array([[0.0, 0.0]])).tolist() == [[0.0, 25.0, 2.0]]
+    assert ok.squared_distances(X, np.array([[1.0, 1.0]])).tolist() == [[2.0, 13.0, 0.0]]
+
+
+def test_indicator_is_inclusion_frequency_over_tie_breaks():
+    """rho_i equals the fraction of valid k-nearest sets that contain point i, so the
+    rho sum to exactly k (Eq. (med_reg) weights at the order statistic)."""
+    rng = np.random.default_rng(40)
+    for _ in range(200):
+        n = int(rng.integers(1, 9))
+        d2 = rng.integers(0, 4, n).astype(np.float64)      # heavy ties
+        for k in range(1, n + 1):
+            sets = _nearest_sets(list(d2), k)
+            freq = np.array([sum(i in S for S in sets) / len(sets) for i in range(n)])
+            rho = ok.indicator(d2, k)
+            assert np.allclose(rho, freq, rtol=0, atol=1e-15), (d2, k)
+            assert math.fsum(rho.tolist()) == pytest.approx(k, abs=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "inverse"])
+def test_regression_is_the_mean_over_tie_breaks(kind):
+    """The prediction equals the plain kNN estimate sum_S w_i f_i / sum_S w_i averaged
+    over every valid set S of k nearest points (tied points share one distance, so the
+    denominator is the same for every S)."""
+    rng = np.random.default_rng(41)
+    for _ in range(60):
+        n = int(rng.integers(2, 8))
+        X = rng.integers(-2, 3, (n, 2)).astype(np.float64)   # lattice points: tied distances
+        f = rng.normal(size=n)
+        Q = rng.integers(-2, 3, (3, 2)).astype(np.float64)
+        for k in range(1, n + 1):
+            got = ok.regress(X, f, Q, k, kind)
+            for j, q in enumerate(Q):
+                d2 = _d2_loop(X, q)
+                ests = []
+                for S in _nearest_sets(d2, k):
+                    ws = [_w(math.sqrt(d2[i]), kind) for i in S]
+                    ests.append(sum(w * f[i] for w, i in zip(ws, S)) / sum(ws))
+                assert got[j] == pytest.approx(sum(ests) / len(ests), rel=1e-12, abs=1e-12), (kind, k)
+
+
+def test_votes_are_the_mean_over_tie_breaks():
+    rng = np.random.default_rng(42)
+    for _ in range(60):
+        n = int(rng.integers(2, 8))
+        X = rng.integers(-2, 3, (n, 2)).astype(np.float64)
+        lab = rng.integers(0, 3, n)
+        Q = rng.integers(-2, 3, (2, 2)).astype(np.float64)
+        for k in range(1, n + 1):
+            V = ok.votes(X, lab, Q, k, 3)
+            for j, q in enumerate(Q):
+                sets = _nearest_sets(_d2_loop(X, q), k)
+                mean = np.array([sum(sum(lab[i] == c for i in S) for S in sets) / len(sets) for c in range(3)])
+                assert np.allclose(V[j], mean, rtol=0, atol=1e-12)
+
+
+def test_without_ties_matches_sorting():
+    """Continuous data (no tied distances): the k nearest by a full sort of the
+    distances, the textbook method the paper replaces."""
+    rng = np.random.default_rng(43)
+    X = rng.normal(size=(300, 5))
+    f = rng.normal(size=300)
+    lab = rng.integers(0, 4, 300)
+    Q = rng.normal(size=(7, 5))
+    for k in (1, 2, 17, 150, 300):
+        for kind in ("uniform", "inverse"):
+            got = ok.regress(X, f, Q, k, kind)
+            for j, q in enumerate(Q):
+                d = np.sqrt(np.array(_d2_loop(X, q)))
+                idx = np.argsort(d)[:k]
+                w = np.array([_w(d[i], kind) for i in idx])
+                assert got[j] == pytest.approx(float(w @ f[idx] / w.sum()), rel=1e-12)
+        cls = ok.classify(X, lab, Q, k, 4)
+        for j, q in enumerate(Q):
+            idx = np.argsort(np.array(_d2_loop(X, q)))[:k]
+            counts = np.bincount(lab[idx], minlength=4)
+            assert cls[j] == int(np.argmax(counts))
+
+
+def test_closed_forms_k_one_and_k_all():
+    rng = np.random.default_rng(44)
+    X = rng.normal(size=(50, 3))
+    f = rng.normal(size=50)
+    Q = rng.normal(size=(5, 3))
+    # k = n with uniform weights: the mean of every ordinate
+    assert np.allclose(ok.regress(X, f, Q, 50), math.fsum(f.tolist()) / 50, rtol=1e-14, atol=0)
+    # k = 1: the ordinate of the nearest point, whatever the weight
+    for kind in ("uniform", "inverse"):
+        got = ok.regress(X, f, Q, 1, kind)
+        for j, q in enumerate(Q):
+            d2 = _d2_loop(X, q)
+            assert got[j] == f[int(np.argmin(d2))]
+    # a query on a training point with k = 1 returns that point's ordinate
+    assert ok.regress(X, f, X[7:8], 1, "inverse")[0] == f[7]
+
+
+def test_rigid_motion_and_row_permutation_invariance():
+    """Distances, hence predictions, do not change under a rotation plus translation of
+    every point, nor under a permutation of the training rows."""
+    rng = np.random.default_rng(45)
+    X = rng.normal(size=(200, 4))
+    f = rng.normal(size=200)
+    lab = rng.integers(0, 3, 200)
+    Q = rng.normal(size=(6, 4))
+    R, _ = np.linalg.qr(rng.normal(size=(4, 4)))
+    t = rng.normal(size=4)
+    for k in (1, 9, 100):
+        base = ok.regress(X, f, Q, k, "inverse")
+        moved = ok.regress(X @ R.T + t, f, Q @ R.T + t, k, "inverse")
+        assert np.allclose(moved, base, rtol=1e-9, atol=1e-12)
+        perm = rng.permutation(200)
+        assert np.array_equal(ok.regress(X[perm], f[perm], Q, k, "inverse"), base)
+        assert np.array_equal(ok.classify(X[perm], lab[perm], Q, k, 3), ok.classify(X, lab, Q, k, 3))
+
+
+def test_class_ties_go_to_the_smallest_label():
+    X = np.array([[1.0], [-1.0], [2.0], [-2.0]])
+    lab = np.array([2, 1, 0, 0])
+    # k = 2 around 0: one vote each for classes 1 and 2 -> class 1
+    assert ok.classify(X, lab, np.array([[0.0]]), 2, 3).tolist() == [1]
+    # k = 4: class 0 has two votes
+    assert ok.classify(X, lab, np.array([[0.0]]), 4, 3).tolist() == [0]

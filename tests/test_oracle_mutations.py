@@ -18,6 +18,7 @@ import textwrap
 import pytest
 
 from oracle import bracket as ob
+from oracle import knn as oknn
 from oracle import philox as oph
 from oracle import regression as oreg
 from oracle import select as osel
@@ -51,7 +52,7 @@ def _run(pin):
     getattr(_pins(mod), test)(**kwargs)
 
 
-S, R, B = "test_oracle_select", "test_oracle_regression", "test_oracle_bracket"
+S, R, B, K = "test_oracle_select", "test_oracle_regression", "test_oracle_bracket", "test_oracle_knn"
 
 # (id, module, function, old, new, occurrences, pins)
 MUTANTS = [
@@ -129,6 +130,21 @@ MUTANTS = [
      "y[:, None] - X @ theta", "y[:, None] - X[:, ::-1] @ theta", 1,
      [(R, "test_residual_sign_and_shape", {}),
       (R, "test_exact_fit_candidate_has_zero_residuals_on_its_subset", {})]),
+    ("knn_tie_weight_full", oknn, "indicator",
+     "rho[tie] = a / b", "rho[tie] = 1.0", 1,
+     [(K, "test_indicator_is_inclusion_frequency_over_tie_breaks", {})]),
+    ("knn_indicator_closed_below", oknn, "indicator",
+     "below = d2 < q", "below = d2 <= q", 1,
+     [(K, "test_indicator_is_inclusion_frequency_over_tie_breaks", {})]),
+    ("knn_weight_on_squared_distance", oknn, "regress",
+     "weight(np.sqrt(D2[j]), kind, eps)", "weight(D2[j], kind, eps)", 1,
+     [(K, "test_regression_is_the_mean_over_tie_breaks", {"kind": "inverse"})]),
+    ("knn_prediction_not_normalised", oknn, "regress",
+     "/ math.fsum(w.tolist())", "/ k", 1,
+     [(K, "test_regression_is_the_mean_over_tie_breaks", {"kind": "inverse"})]),
+    ("knn_distance_operand_dropped", oknn, "squared_distances",
+     "diff = Q[:, None, :] - X[None, :, :]", "diff = Q[:, None, :] - 0 * X[None, :, :]", 1,
+     [(K, "test_squared_distances_hand_worked", {})]),
     ("gelu_grad_term_dropped", ob, "gelu_grad",
      "return Phi + u * phi", "return Phi", 1,
      [(B, "test_gelu_closed_forms", {}), (B, "test_backward_matches_central_differences", {})]),
