@@ -149,7 +149,7 @@ GLOO_RANKS = (1, 400, 20005, 39000, 40009)
 
 
 def _gloo_data(layout):
-    if layout == "two_each":
+    if layout in ("two_each", "three_uneven"):
         return synth.heavy_mixture("mixture", 40009, seed=11)
     return synth.heavy_mixture("cauchy", 40009, seed=12, dtype=np.float64)
 
@@ -165,6 +165,9 @@ def _rank_main(rank, world, port, out, layout):
         x = _gloo_data(layout)
         if layout == "two_each":
             own = split(x, 4, seed=3)[rank * 2:(rank + 1) * 2]     # two shards per rank
+        elif layout == "three_uneven":
+            parts = split(x, 4, seed=5)                            # ranks hold 3, 0 and 1 shards
+            own = parts[:3] if rank == 0 else ([] if rank == 1 else parts[3:])
         else:
             own = [x] if rank == 0 else []                        # rank 1 holds no element
         res = []
@@ -175,16 +178,17 @@ def _rank_main(rank, world, port, out, layout):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("layout", ["two_each", "one_rank_empty"])
-def test_sharded_two_gloo_ranks(layout):
-    """Two gloo ranks: two shards each (float32), or every element on rank 0 and none on
-    rank 1 (float64); both ranks return the single-array result."""
+@pytest.mark.parametrize("layout,world", [("two_each", 2), ("one_rank_empty", 2), ("three_uneven", 3)])
+def test_sharded_gloo_ranks(layout, world):
+    """gloo ranks on the CPU: two shards on each of two ranks (float32); every element on
+    rank 0 and none on rank 1 (float64); three ranks holding 3, 0 and 1 uneven shards
+    (float32).  Every rank returns the single-array result."""
     gbs()
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q, layout)) for r in range(2)]
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, q, layout)) for r in range(world)]
     for p in procs:
         p.start()
     got = dict(q.get(timeout=240) for _ in procs)
@@ -193,7 +197,7 @@ def test_sharded_two_gloo_ranks(layout):
         assert p.exitcode == 0
     x = _gloo_data(layout)
     want = [osel.select_kth(x, k) for k in GLOO_RANKS]
-    for r in (0, 1):
+    for r in range(world):
         assert [bits(v, x.dtype) for v in got[r]] == [bits(v, x.dtype) for v in want]
 
 
