@@ -12,6 +12,7 @@ deterministic given the seed.  They stand in for the paper's synthetic data sets
 * ``segment_sizes``, ``segmented``     thousands of normal arrays of log-uniform sizes
 * ``regression``, ``elemental_thetas`` contaminated linear model and p-subset candidates
 * ``training_array``                   arrays of the families the bracket MLP learns from
+* ``knn_problem``                      labelled Gaussian clusters and queries for kNN
 """
 from __future__ import annotations
 
@@ -153,6 +154,25 @@ def elemental_thetas(X, y, C, seed):
         out[:, c] = np.linalg.solve(A, yd[rows])
         c += 1
     return out.astype(np.float32)
+
+
+def knn_problem(n, p, m, n_classes, seed, lattice=False):
+    """kNN workload: n training points in p dimensions from n_classes Gaussian clusters
+    (centres ~ N(0, 4^2 I), unit spread), each point labelled with its cluster.  The
+    ordinate is f = sum of sin(x_t) over the coordinates plus N(0, 0.1^2) noise.  The m
+    queries are drawn the same way.  ``lattice`` rounds every coordinate to an integer,
+    so float32 distances are exact and tied distances are common.  Returns X (n, p) and
+    Q (m, p) float32, f (n,) float32 and labels (n,) int32."""
+    rng = np.random.default_rng(seed)
+    n, p, m, K = int(n), int(p), int(m), int(n_classes)
+    centres = rng.normal(0.0, 4.0, (K, p))
+    labels = rng.integers(0, K, n)
+    X = centres[labels] + rng.standard_normal((n, p))
+    Q = centres[rng.integers(0, K, m)] + rng.standard_normal((m, p))
+    if lattice:
+        X, Q = np.rint(X), np.rint(Q)
+    f = np.sin(X).sum(axis=1) + 0.1 * rng.standard_normal(n)
+    return X.astype(np.float32), Q.astype(np.float32), f.astype(np.float32), labels.astype(np.int32)
 
 
 TRAIN_FAMILIES = ("normal", "student", "lognormal", "contaminated")

@@ -154,3 +154,20 @@ def test_class_ties_go_to_the_smallest_label():
     assert ok.classify(X, lab, np.array([[0.0]]), 2, 3).tolist() == [1]
     # k = 4: class 0 has two votes
     assert ok.classify(X, lab, np.array([[0.0]]), 4, 3).tolist() == [0]
+
+
+def test_knn_problem_recipe():
+    """The seeded kNN inputs: shapes, dtypes, determinism, and lattice coordinates that
+    are integers (so float32 squared distances are exact for |coordinates| < 2^11)."""
+    import synth
+    X, Q, f, lab = synth.knn_problem(1000, 8, 16, 5, seed=3)
+    assert X.shape == (1000, 8) and Q.shape == (16, 8) and f.shape == (1000,) and lab.shape == (1000,)
+    assert X.dtype == Q.dtype == f.dtype == np.float32 and lab.dtype == np.int32
+    assert set(np.unique(lab)) <= set(range(5))
+    X2, Q2, f2, lab2 = synth.knn_problem(1000, 8, 16, 5, seed=3)
+    assert np.array_equal(X, X2) and np.array_equal(Q, Q2) and np.array_equal(f, f2) and np.array_equal(lab, lab2)
+    XL, QL, _, _ = synth.knn_problem(1000, 8, 16, 5, seed=3, lattice=True)
+    assert np.array_equal(XL, np.rint(XL)) and np.array_equal(QL, np.rint(QL))
+    assert np.abs(XL).max() < 2 ** 11
+    d32 = ((QL[0][None, :] - XL) ** 2).sum(axis=1, dtype=np.float32)
+    assert np.array_equal(d32.astype(np.float64), ok.squared_distances(XL, QL[:1])[0])
