@@ -62,8 +62,8 @@ enum {
 /* Tuning knobs.  Zero fields take the defaults given beside them. */
 typedef struct {
     int64_t cap;         /* the pass that sees a bracket of <= cap elements compacts it and
-                            the cutting plane stops (Sec. 3: "the algorithm stops when the
-                            cost of its iteration outweighs the benefit"); 0 = max(n/8, 4096) */
+                            the cutting plane stops (Sec. 3 ends the iterations once one more
+                            would cost more than it saves the finish); 0 = max(n/8, 4096) */
     int32_t maxit;       /* cutting-plane iterations before compaction is forced; 0 = 64 */
     int32_t blocks_per_sm; /* CTAs per SM of the persistent kernel; 0 = 1 below 32 MiB of
                               input, else 2 (at most what fits) */
@@ -144,7 +144,14 @@ typedef struct {
     double result;         /* x_(k) once DONE */
 } gbs_shard_state;
 
-/* Context lifetime.  `device` is the CUDA ordinal the context works on. */
+/* Context lifetime.  gbs_create makes a context for CUDA ordinal `device`.  Creation
+ * touches only the host: the device workspace is allocated on first use or by
+ * gbs_reserve.  Errors:
+ *  - EINVAL for a NULL ctx or an ordinal outside [0, device count);
+ *  - ECUDA when the device cannot be queried or lacks cooperative launch;
+ *  - ENOMEM when the host record cannot be allocated.
+ * gbs_destroy synchronises the device and frees everything the context holds; NULL is a
+ * no-op. */
 gbs_status gbs_create(gbs_ctx** ctx, int device);
 void gbs_destroy(gbs_ctx* ctx);
 
@@ -152,11 +159,16 @@ void gbs_destroy(gbs_ctx* ctx);
  * run without allocating.  Synchronous. */
 gbs_status gbs_reserve(gbs_ctx* ctx, int64_t n, int32_t elem_bytes);
 
+/* Replaces or reads the context's gbs_config; cfg is a host struct, copied.  The values
+ * apply from the next call.  EINVAL for NULL pointers, a negative cap, maxit or
+ * blocks_per_sm, or lms_start outside {0, 1}. */
 gbs_status gbs_set_config(gbs_ctx* ctx, const gbs_config* cfg);
 gbs_status gbs_get_config(gbs_ctx* ctx, gbs_config* cfg);
 
 /* x_(k) of x[0..n) (Sec. 1; Algorithm 1 and the hybrid finish of Sec. 3).
- * x: n elements, device, contiguous, any alignment.  out: 1 element, device. */
+ * x: n elements, device, contiguous, aligned to its element size (any 16-byte phase).
+ * out: 1 element, device.  EINVAL for NULL pointers, n < 1, k outside [1, n] or a
+ * misaligned x; ENAN (device record) when x holds a NaN. */
 gbs_status gbs_select_kth_f32(gbs_ctx* ctx, const float* x, int64_t n, int64_t k, float* out,
                               void* stream);
 gbs_status gbs_select_kth_f64(gbs_ctx* ctx, const double* x, int64_t n, int64_t k, double* out,
