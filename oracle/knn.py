@@ -19,11 +19,14 @@ Readings (the passage is silent on each point):
 * Weights.  w(d) = 1 (uniform) or w(d) = 1 / (d + eps) (inverse distance, eps > 0).
   The prediction is normalised: sum rho_i w_i f_i / sum rho_i w_i.
 * Vote.  Class c scores sum rho_i [label_i = c] (unweighted).  The prediction is the
-  highest score, and a tie between classes goes to the smallest label.
+  highest score, and a tie between classes goes to the smallest label.  Scores are
+  exact rationals (the tie share a/b as a fraction), so whether two classes tie is
+  decided exactly, not by the rounding of a float sum.
 """
 from __future__ import annotations
 
 import math
+from fractions import Fraction
 
 import numpy as np
 
@@ -73,18 +76,32 @@ def regress(X, f, Q, k, kind="uniform", eps=1e-6):
     return out
 
 
-def votes(X, labels, Q, k, n_classes):
-    """(m, n_classes) vote totals sum rho_i [label_i = c]."""
+def exact_votes(X, labels, Q, k, n_classes):
+    """Per query, the list of n_classes vote totals sum rho_i [label_i = c] as exact
+    Fractions: the points below d_(k) count 1 each, the b points at d_(k) count a/b."""
     labels = np.asarray(labels)
     D2 = squared_distances(X, Q)
-    V = np.zeros((D2.shape[0], n_classes))
+    out = []
     for j in range(D2.shape[0]):
-        rho = indicator(D2[j], k)
-        for c in range(n_classes):
-            V[j, c] = math.fsum(rho[labels == c].tolist())
-    return V
+        q = float(select_kth(D2[j], k))
+        below = D2[j] < q
+        tie = D2[j] == q
+        share = Fraction(k - int(np.count_nonzero(below)), int(np.count_nonzero(tie)))
+        out.append([int(np.count_nonzero(below & (labels == c))) + share * int(np.count_nonzero(tie & (labels == c)))
+                    for c in range(n_classes)])
+    return out
+
+
+def votes(X, labels, Q, k, n_classes):
+    """(m, n_classes) vote totals as floats (each the rounding of its exact value)."""
+    return np.array([[float(v) for v in row] for row in exact_votes(X, labels, Q, k, n_classes)])
 
 
 def classify(X, labels, Q, k, n_classes):
-    """Majority class among the k nearest (ties between classes: smallest label)."""
-    return np.argmax(votes(X, labels, Q, k, n_classes), axis=1)
+    """Majority class among the k nearest: the highest exact vote total, a tie between
+    classes going to the smallest label."""
+    out = []
+    for row in exact_votes(X, labels, Q, k, n_classes):
+        best = max(row)
+        out.append(row.index(best))
+    return np.array(out, dtype=np.int64)

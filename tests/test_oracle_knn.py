@@ -171,3 +171,17 @@ def test_knn_problem_recipe():
     assert np.abs(XL).max() < 2 ** 11
     d32 = ((QL[0][None, :] - XL) ** 2).sum(axis=1, dtype=np.float32)
     assert np.array_equal(d32.astype(np.float64), ok.squared_distances(XL, QL[:1])[0])
+
+
+def test_vote_totals_are_exact_fractions():
+    """Three points below d_(k) and three tied at d_(k) with k = 4: each tied point counts
+    1/3, so class 1 (one below, three tied) and class 0 (two below) both score exactly 2,
+    and the tie goes to class 0."""
+    from fractions import Fraction
+    X = np.array([[1.0], [-1.0], [-1.0], [2.0], [-2.0], [2.0]])
+    lab = np.array([1, 0, 0, 1, 1, 1])
+    Q = np.array([[0.0]])
+    assert ok.exact_votes(X, lab, Q, 4, 2) == [[Fraction(2), Fraction(2)]]
+    assert ok.classify(X, lab, Q, 4, 2).tolist() == [0]
+    assert ok.exact_votes(X, lab, Q, 5, 2) == [[Fraction(2), Fraction(1) + 3 * Fraction(2, 3)]]
+    assert ok.classify(X, lab, Q, 5, 2).tolist() == [1]
