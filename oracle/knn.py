@@ -42,6 +42,21 @@ def squared_distances(X, Q):
     return np.einsum("mnp,mnp->mn", diff, diff)
 
 
+def squared_distances_f32(X, Q):
+    """(m, n) squared distances in float32 with a fixed order of operations: for
+    t = 0, 1, ..., p-1, diff = q_t - x_t, then acc = acc + diff * diff, every product and
+    sum rounded to float32 (no fused multiply-add).  Which points are the k nearest is
+    an integer decision taken on these floats, so a float32 path takes it on exactly
+    these values."""
+    X = np.asarray(X, dtype=np.float32)
+    Q = np.asarray(Q, dtype=np.float32)
+    acc = np.zeros((Q.shape[0], X.shape[0]), dtype=np.float32)
+    for t in range(X.shape[1]):
+        diff = Q[:, None, t] - X[None, :, t]
+        acc = acc + diff * diff
+    return acc
+
+
 def indicator(d2, k):
     """rho_i for one query: 1 for d_i < d_(k), a/b for d_i = d_(k), 0 above."""
     d2 = np.asarray(d2, dtype=np.float64)
@@ -66,8 +81,13 @@ def weight(d, kind="uniform", eps=1e-6):
 
 def regress(X, f, Q, k, kind="uniform", eps=1e-6):
     """kNN regression prediction for every query row of Q (m values)."""
+    return regress_d2(squared_distances(X, Q), f, k, kind, eps)
+
+
+def regress_d2(D2, f, k, kind="uniform", eps=1e-6):
+    """kNN regression from given squared distances D2 (m, n), in float64."""
     f = np.asarray(f, dtype=np.float64)
-    D2 = squared_distances(X, Q)
+    D2 = np.asarray(D2, dtype=np.float64)
     out = np.empty(D2.shape[0])
     for j in range(D2.shape[0]):
         rho = indicator(D2[j], k)
@@ -79,8 +99,13 @@ def regress(X, f, Q, k, kind="uniform", eps=1e-6):
 def exact_votes(X, labels, Q, k, n_classes):
     """Per query, the list of n_classes vote totals sum rho_i [label_i = c] as exact
     Fractions: the points below d_(k) count 1 each, the b points at d_(k) count a/b."""
+    return exact_votes_d2(squared_distances(X, Q), labels, k, n_classes)
+
+
+def exact_votes_d2(D2, labels, k, n_classes):
+    """exact_votes from given squared distances D2 (m, n)."""
     labels = np.asarray(labels)
-    D2 = squared_distances(X, Q)
+    D2 = np.asarray(D2, dtype=np.float64)
     out = []
     for j in range(D2.shape[0]):
         q = float(select_kth(D2[j], k))
@@ -100,8 +125,12 @@ def votes(X, labels, Q, k, n_classes):
 def classify(X, labels, Q, k, n_classes):
     """Majority class among the k nearest: the highest exact vote total, a tie between
     classes going to the smallest label."""
+    return classify_d2(squared_distances(X, Q), labels, k, n_classes)
+
+
+def classify_d2(D2, labels, k, n_classes):
+    """classify from given squared distances D2 (m, n)."""
     out = []
-    for row in exact_votes(X, labels, Q, k, n_classes):
-        best = max(row)
-        out.append(row.index(best))
+    for row in exact_votes_d2(D2, labels, k, n_classes):
+        out.append(row.index(max(row)))
     return np.array(out, dtype=np.int64)

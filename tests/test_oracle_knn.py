@@ -185,3 +185,40 @@ def test_vote_totals_are_exact_fractions():
     assert ok.classify(X, lab, Q, 4, 2).tolist() == [0]
     assert ok.exact_votes(X, lab, Q, 5, 2) == [[Fraction(2), Fraction(1) + 3 * Fraction(2, 3)]]
     assert ok.classify(X, lab, Q, 5, 2).tolist() == [1]
+
+
+def test_float32_distances_follow_their_stated_order():
+    """squared_distances_f32: every entry equals a scalar float32 loop of the stated
+    definition (diff = q_t - x_t, acc = acc + diff * diff, t = 0..p-1, no fused
+    multiply-add); it lies within (p + 2) * 2^-24 of the float64 distance; on integer
+    lattice data it is exact."""
+    rng = np.random.default_rng(46)
+    X = (rng.normal(size=(40, 6)) * 3).astype(np.float32)
+    Q = (rng.normal(size=(5, 6)) * 3).astype(np.float32)
+    D32 = ok.squared_distances_f32(X, Q)
+    assert D32.dtype == np.float32
+    for j in range(5):
+        for i in range(40):
+            acc = np.float32(0.0)
+            for t in range(6):
+                d = np.float32(Q[j, t]) - np.float32(X[i, t])
+                acc = np.float32(acc + np.float32(d * d))
+            assert D32[j, i] == acc
+    D64 = ok.squared_distances(X, Q)
+    assert np.all(np.abs(D32.astype(np.float64) - D64) <= (6 + 2) * 2.0 ** -24 * D64 + 1e-30)
+    import synth
+    XL, QL, _, _ = synth.knn_problem(500, 8, 4, 3, seed=9, lattice=True)
+    assert np.array_equal(ok.squared_distances_f32(XL, QL).astype(np.float64), ok.squared_distances(XL, QL))
+
+
+def test_from_distances_entry_points_agree():
+    rng = np.random.default_rng(47)
+    X = rng.integers(-3, 4, (60, 3)).astype(np.float64)
+    f = rng.normal(size=60)
+    lab = rng.integers(0, 4, 60)
+    Q = rng.integers(-3, 4, (4, 3)).astype(np.float64)
+    D2 = ok.squared_distances(X, Q)
+    for k in (1, 7, 30, 60):
+        assert np.array_equal(ok.regress_d2(D2, f, k, "inverse"), ok.regress(X, f, Q, k, "inverse"))
+        assert ok.exact_votes_d2(D2, lab, k, 4) == ok.exact_votes(X, lab, Q, k, 4)
+        assert np.array_equal(ok.classify_d2(D2, lab, k, 4), ok.classify(X, lab, Q, k, 4))

@@ -136,15 +136,22 @@ MUTANTS = [
     ("knn_indicator_closed_below", oknn, "indicator",
      "below = d2 < q", "below = d2 <= q", 1,
      [(K, "test_indicator_is_inclusion_frequency_over_tie_breaks", {})]),
-    ("knn_weight_on_squared_distance", oknn, "regress",
+    ("knn_weight_on_squared_distance", oknn, "regress_d2",
      "weight(np.sqrt(D2[j]), kind, eps)", "weight(D2[j], kind, eps)", 1,
      [(K, "test_regression_is_the_mean_over_tie_breaks", {"kind": "inverse"})]),
-    ("knn_prediction_not_normalised", oknn, "regress",
+    ("knn_prediction_not_normalised", oknn, "regress_d2",
      "/ math.fsum(w.tolist())", "/ k", 1,
      [(K, "test_regression_is_the_mean_over_tie_breaks", {"kind": "inverse"})]),
     ("knn_distance_operand_dropped", oknn, "squared_distances",
      "diff = Q[:, None, :] - X[None, :, :]", "diff = Q[:, None, :] - 0 * X[None, :, :]", 1,
      [(K, "test_squared_distances_hand_worked", {})]),
+    ("knn_f32_distance_accumulated_in_float64", oknn, "squared_distances_f32",
+     "acc = acc + diff * diff\n", "acc = (acc.astype(np.float64) + diff.astype(np.float64) ** 2).astype(np.float32)\n", 1,
+     [(K, "test_float32_distances_follow_their_stated_order", {})]),
+    ("knn_vote_share_inverted", oknn, "exact_votes_d2",
+     "share = Fraction(k - int(np.count_nonzero(below)), int(np.count_nonzero(tie)))",
+     "share = Fraction(int(np.count_nonzero(tie)), max(1, k - int(np.count_nonzero(below))))", 1,
+     [(K, "test_vote_totals_are_exact_fractions", {}), (K, "test_votes_are_the_mean_over_tie_breaks", {})]),
     ("gelu_grad_term_dropped", ob, "gelu_grad",
      "return Phi + u * phi", "return Phi", 1,
      [(B, "test_gelu_closed_forms", {}), (B, "test_backward_matches_central_differences", {})]),
