@@ -194,9 +194,9 @@ gbs_status gbs_cost_pass_f64(gbs_ctx* ctx, const double* x, int64_t n, int64_t k
 
 /* x_(k) of float32 x[0..n) without allocating anything: no context, no cudaMalloc,
  * cudaFree or allocating library call.  The paper has no counterpart; this is for
- * callers that cannot let a library allocate device memory (code running while a stream
- * is captured into a graph, hosts whose device memory belongs to their own arena, loops
- * where an allocation's implicit device synchronisation is not acceptable).
+ * callers that cannot let a library allocate device memory (hosts whose device memory
+ * belongs to their own arena or caching allocator, runtimes with a fixed device budget,
+ * loops where an allocation's implicit device synchronisation is not acceptable).
  * Same kernel and same result as gbs_select_kth_f32.  Its scratch is one static device
  * array of about 4.1 MiB that every GPU loading the library holds until process exit.
  * Limits: 1 <= k <= n <= 1048576 (2^20), else GBS_EINVAL before any launch.
@@ -204,7 +204,8 @@ gbs_status gbs_cost_pass_f64(gbs_ctx* ctx, const double* x, int64_t n, int64_t k
  * there (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the array: calls whose GPU work overlaps in time (different streams,
  * several threads) race and give wrong results; serialise them.  There is no per-call
- * record to read back; a NaN input yields a NaN result. */
+ * record to read back: a NaN result means that x holds a NaN or that the device work
+ * failed (a bounded wait gave up, an internal check failed). */
 gbs_status gbs_select_kth_f32_noalloc(const float* x, int64_t n, int64_t k, float* out, void* stream);
 
 /* Segmented batched select: out[s] = x_(k[s]) of the segment x[offsets[s], offsets[s+1])

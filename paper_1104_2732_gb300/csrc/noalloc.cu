@@ -2,9 +2,9 @@
 // gbs_select_kth_f32, with its scratch memory in a fixed device array of this file
 // instead of a context's cudaMalloc'd workspace.
 //
-// Some callers cannot let a library allocate device memory: code that runs while a
-// stream is being captured into a CUDA graph, hosts whose device memory is owned by an
-// arena or pool of their own, and latency-critical loops where cudaMalloc / cudaFree
+// Some callers cannot let a library allocate device memory: hosts whose device memory is
+// owned by an arena or pool of their own (a framework's caching allocator, an embedded
+// runtime with a fixed budget), and latency-critical loops where cudaMalloc / cudaFree
 // would synchronise the device.  This entry point serves them.  Its scratch is the
 // static array below (about 4.1 MiB), which every GPU that loads the library holds
 // until the process exits.
@@ -111,9 +111,9 @@ extern "C" gbs_status gbs_select_kth_f32_noalloc(const float* x, int64_t n, int6
   A.eval_out = nullptr;
   A.proposal = nullptr;
   // The array keeps the previous call's contents: the barrier and status words must
-  // start at zero (the radix histograms are cleared by the kernel itself).
-  if (cudaMemsetAsync(A.ctrl, 0, sizeof(Ctrl), strm) != cudaSuccess ||
-      cudaMemsetAsync(A.rs, 0, sizeof(gbs_run_stats), strm) != cudaSuccess) {
+  // start at zero.  The radix histograms are cleared by the kernel itself, and the run
+  // record is rewritten by CTA 0 on every normal exit and never read back here.
+  if (cudaMemsetAsync(A.ctrl, 0, sizeof(Ctrl), strm) != cudaSuccess) {
     cudaGetLastError();
     return GBS_ECUDA;
   }

@@ -350,6 +350,9 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
   const long long per_thread = per_thread_bound(nch, G, Ops<T>::kVec);
 
   if (tid == 0) { s_ntns = 0; s_nk = 0; s_nb = 0; }
+  // a selection that ends early (a wait that gave up, an internal inconsistency) leaves a
+  // quiet NaN in *out; the normal exit overwrites it with the result
+  if (A.mode == kModeSelect && bid == 0 && tid == 0) *A.out = T(NAN);
   if (bid == 0) {   // zero the radix histograms (visible after the first barrier)
     for (int i = tid; i < kMaxRounds * kBins; i += kThreads) A.ghist[i] = 0ull;
   }
@@ -932,7 +935,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
         if (who == 0 && tid == 0) {   // no bin holds the rank: inconsistent counts
           atomicCAS(&A.ctrl->status, 0, (int)GBS_EINTERNAL);
           s_known = W;
-          s_prefix = 0;
+          s_prefix = 0;                 // ukey_value(0) is a NaN: the result is flagged
         }
       }
       ++rounds;

@@ -1,6 +1,6 @@
 """Small, fixed invocations of the library's kernels for profiling (ncu) and timing.
 
-Usage: ``python paper_1104_2732_gb300/profile_cases.py CASE [--reps R] [--warmup W]``
+Usage: ``python profile_cases.py CASE [--reps R] [--warmup W]``
 
 Cases (inputs from ``synth``; every case holds at most a few GB on the device):
   select     median and 1% rank of the 2^27 float32 mixture (seed 4), R calls each
@@ -21,7 +21,7 @@ import os
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-sys.path.insert(0, os.path.dirname(HERE))
+sys.path.insert(0, HERE)
 
 
 def main():
@@ -46,7 +46,7 @@ def main():
         x = torch.from_numpy(synth.heavy_mixture("mixture", n, seed=4, dtype=dt)).cuda()
         ctx.reserve(n, x.element_size())
         if case == "learned":
-            ctx.load_bracket_model(os.path.join(HERE, "bracket_model.bin"))
+            ctx.load_bracket_model(os.path.join(HERE, "paper_1104_2732_gb300", "bracket_model.bin"))
             ctx.set_config(use_learned=1)
             ks = [(n + 1) // 2]
         else:
@@ -63,7 +63,7 @@ def main():
         out = torch.empty(4096, device="cuda")
         ctx.set_segmented_variant(0)
         if case == "segmented_learned":
-            ctx.load_bracket_model(os.path.join(HERE, "bracket_model.bin"))
+            ctx.load_bracket_model(os.path.join(HERE, "paper_1104_2732_gb300", "bracket_model.bin"))
             ctx.set_config(use_learned=1)
 
         def rep():
@@ -82,7 +82,7 @@ def main():
     else:
         x = torch.empty(1 << 24, device="cuda")
         ctx.generate_training_array(x, 1, 3.0, 0.0, 1.0, 5.0, 2.0, seed=123)
-        ctx.load_bracket_model(os.path.join(HERE, "bracket_model.bin"))
+        ctx.load_bracket_model(os.path.join(HERE, "paper_1104_2732_gb300", "bracket_model.bin"))
 
         def rep():
             ctx.bracket_propose(x)
