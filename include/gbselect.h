@@ -75,7 +75,12 @@ typedef struct {
                             8192 sampled rows and checked by counts in the first pass (a
                             candidate whose check fails goes to the materialising form);
                             1 = start from the extremes (Algorithm 1, step 0) */
-    int32_t reserved[6];
+    int32_t knn_start;   /* kNN (n >= 65536): 0 = each query starts from a bracket of sampled
+                            distance order statistics, checked by counts in one fused pass (a
+                            query whose check fails takes the plain form); 1 = the plain form
+                            for every query: its distance row written out, d_(k) by the
+                            segmented select, then the indicator reduction */
+    int32_t reserved[5];
 } gbs_config;
 
 /* Per-call record of the last selection on a context (host copy). */
@@ -161,7 +166,7 @@ gbs_status gbs_reserve(gbs_ctx* ctx, int64_t n, int32_t elem_bytes);
 
 /* Replaces or reads the context's gbs_config; cfg is a host struct, copied.  The values
  * apply from the next call.  EINVAL for NULL pointers, a negative cap, maxit or
- * blocks_per_sm, or lms_start outside {0, 1}. */
+ * blocks_per_sm, or lms_start or knn_start outside {0, 1}. */
 gbs_status gbs_set_config(gbs_ctx* ctx, const gbs_config* cfg);
 gbs_status gbs_get_config(gbs_ctx* ctx, gbs_config* cfg);
 
@@ -282,6 +287,46 @@ gbs_status gbs_lms_lts_f32(gbs_ctx* ctx, const float* X, const float* y, int64_t
 gbs_status gbs_lms_lts_fused_f32(gbs_ctx* ctx, const float* X, const float* y, int64_t n, int32_t p,
                                  const float* theta, int32_t C, int64_t k_lms, int64_t h_lts,
                                  float* lms_out, double* lts_out, int32_t* passes, void* stream);
+
+/* ---- k-nearest-neighbour regression and classification through the k-th order
+ * statistic of the distances (Sec. 5, last application).  For each query q_j the k
+ * nearest of the n points x_i (Euclidean) are marked by an indicator against d_(k), the
+ * k-th smallest distance: 1 below it, 0 above it, and (k - #(d < d_(k))) / #(d = d_(k))
+ * for every point exactly at it (the a/b weight at the order statistic of
+ * Eq. (med_reg)), so that exactly k points count whatever the ties.
+ * Distances: the squared distance is formed in float32 in a fixed order -- for
+ * t = 0..p-1, e = q_t - x_t, acc = acc + e*e, every operation rounded on its own, no
+ * fused multiply-add -- and the order statistic is taken on it; which points count is
+ * therefore decided exactly on those float32 values.
+ * Layout: X n x p and Q m x p row-major float32, device; 1 <= p <= 32, 1 <= k <= n < 2^31,
+ * m >= 1.  kth_d2 (m floats, device, may be NULL) receives d_(k)^2 per query.
+ * Route: with gbs_config.knn_start 0 (default) and n >= 65536, each query's distances to
+ * 8192 evenly spread rows propose a bracket around rank k; one fused pass counts the
+ * points below it and at its upper end and compacts those inside, and a finish per query
+ * selects d_(k) among them.  A query whose bracket fails its count check (or outgrows its
+ * buffer) takes the plain form: its distance row is written to the workspace, the
+ * segmented select finds d_(k), and the pass reduces the points below and at d_(k).
+ * Device-side errors (gbs_last_stats): GBS_ENAN for a non-finite coordinate in X or Q
+ * (the outputs then hold NaN, class -1); GBS_EINVAL for a label outside [0, n_classes).
+ * The workspace grows on demand (synchronously); the call synchronises `stream` once per
+ * 16384 queries to read how many queries need the plain form. */
+
+/* Regression: pred[j] = sum_i rho_ij w_ij f_i / sum_i rho_ij w_ij, rho the indicator above,
+ * w = 1 (weight 0) or w = 1 / (d + eps) with d = sqrt(d^2) in float64 (weight 1, eps > 0).
+ * f: n float32, device; pred: m float64, device (sums in float64).  EINVAL for NULL X, Q,
+ * f or pred, a bad size or rank, weight outside {0, 1}, or a non-positive eps with
+ * weight 1. */
+gbs_status gbs_knn_regress_f32(gbs_ctx* ctx, const float* X, int64_t n, int32_t p, const float* f, const float* Q,
+                               int32_t m, int64_t k, int32_t weight, double eps, double* pred, float* kth_d2,
+                               void* stream);
+/* Classification: votes[j][c] = sum_i rho_ij [label_i = c] (m x n_classes float64, device,
+ * may be NULL; each the correctly rounded value of an exact rational), cls[j] = the class
+ * with the largest vote, the smallest label among equal votes (decided on the exact
+ * rationals; m int32, device).  labels: n int32 in [0, n_classes), device;
+ * 1 <= n_classes <= 1024. */
+gbs_status gbs_knn_classify_f32(gbs_ctx* ctx, const float* X, int64_t n, int32_t p, const int32_t* labels,
+                                int32_t n_classes, const float* Q, int32_t m, int64_t k, int32_t* cls,
+                                double* votes, float* kth_d2, void* stream);
 
 /* ---- Learned starting bracket (no counterpart in the paper; it replaces the starting
  * bracket of Algorithm 1, step 0).  A sketch of x -- 1024 samples x[j*floor(n/1024)],

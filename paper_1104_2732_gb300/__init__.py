@@ -33,7 +33,8 @@ class GbsError(RuntimeError):
 # ------------------------------------------------------------------ structures
 class gbs_config(C.Structure):
     _fields_ = [("cap", C.c_int64), ("maxit", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("use_learned", C.c_int32), ("lms_start", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("use_learned", C.c_int32), ("lms_start", C.c_int32), ("knn_start", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 class gbs_run_stats(C.Structure):
@@ -97,6 +98,10 @@ _SIGS = {
                                   C.c_int32, _P]),
     "gbs_lms_lts_fused_f32": (C.c_int, [_P, _P, _P, _I64, C.c_int32, _P, C.c_int32, _I64, _I64, _P, _P,
                                         C.POINTER(C.c_int32), _P]),
+    "gbs_knn_regress_f32": (C.c_int, [_P, _P, _I64, C.c_int32, _P, _P, C.c_int32, _I64, C.c_int32, C.c_double, _P,
+                                      _P, _P]),
+    "gbs_knn_classify_f32": (C.c_int, [_P, _P, _I64, C.c_int32, _P, C.c_int32, _P, C.c_int32, _I64, _P, _P, _P,
+                                       _P]),
     "gbs_bracket_model_set": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int32]),
     "gbs_bracket_model_get": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int32]),
     "gbs_bracket_model_save": (C.c_int, [_P, C.c_char_p]),
@@ -231,7 +236,7 @@ class Context:
         cfg = gbs_config()
         _check(gbs_get_config(self._h, C.byref(cfg)), "gbs_get_config")
         return {"cap": cfg.cap, "maxit": cfg.maxit, "blocks_per_sm": cfg.blocks_per_sm,
-                "use_learned": cfg.use_learned, "lms_start": cfg.lms_start}
+                "use_learned": cfg.use_learned, "lms_start": cfg.lms_start, "knn_start": cfg.knn_start}
 
     def reserve(self, n, elem_bytes=4):
         _check(gbs_reserve(self._h, int(n), int(elem_bytes)), "gbs_reserve")
@@ -392,6 +397,46 @@ class Context:
                                      C.c_void_p(lts.data_ptr()), C.byref(npass), _stream_ptr(stream)),
                "gbs_lms_lts_fused")
         return lms, lts, npass.value
+
+    # -------------------------------------------------------------- kNN
+    def _knn_args(self, X, Q, k):
+        import torch
+        X = self._in(X, "X (n, p points)", dtype=torch.float32, dim=2)
+        n, p = X.shape
+        Q = self._in(Q, "Q (m, p queries)", dtype=torch.float32, dim=2, cols=p)
+        if not 1 <= int(k) <= n:
+            raise ValueError(f"k = {k} outside [1, {n}]")
+        return X, Q, n, p, Q.shape[0]
+
+    def knn_regress(self, X, f, Q, k, weight="uniform", eps=1e-6, stream=None):
+        """(pred, kth_d2): kNN regression of f at every query row of Q (float64) and the
+        k-th smallest squared distance per query (float32)."""
+        import torch
+        X, Q, n, p, m = self._knn_args(X, Q, k)
+        f = self._in(f, "f", dtype=torch.float32, numel=n)
+        w = {"uniform": 0, "inverse": 1}[weight]
+        pred = torch.empty(m, dtype=torch.float64, device=X.device)
+        kth = torch.empty(m, dtype=torch.float32, device=X.device)
+        _check(gbs_knn_regress_f32(self._h, C.c_void_p(X.data_ptr()), n, p, C.c_void_p(f.data_ptr()),
+                                   C.c_void_p(Q.data_ptr()), m, int(k), w, float(eps), C.c_void_p(pred.data_ptr()),
+                                   C.c_void_p(kth.data_ptr()), _stream_ptr(stream)), "gbs_knn_regress")
+        return pred, kth
+
+    def knn_classify(self, X, labels, n_classes, Q, k, votes=True, stream=None):
+        """(cls, votes, kth_d2): the majority class among the k nearest points of every
+        query (int32), the vote totals (float64, m x n_classes, or None) and the k-th
+        smallest squared distance (float32)."""
+        import torch
+        X, Q, n, p, m = self._knn_args(X, Q, k)
+        labels = self._in(labels, "labels", dtype=torch.int32, numel=n)
+        cls = torch.empty(m, dtype=torch.int32, device=X.device)
+        v = torch.empty(m, int(n_classes), dtype=torch.float64, device=X.device) if votes else None
+        kth = torch.empty(m, dtype=torch.float32, device=X.device)
+        _check(gbs_knn_classify_f32(self._h, C.c_void_p(X.data_ptr()), n, p, C.c_void_p(labels.data_ptr()),
+                                    int(n_classes), C.c_void_p(Q.data_ptr()), m, int(k), C.c_void_p(cls.data_ptr()),
+                                    C.c_void_p(v.data_ptr()) if v is not None else None, C.c_void_p(kth.data_ptr()),
+                                    _stream_ptr(stream)), "gbs_knn_classify")
+        return cls, v, kth
 
     # -------------------------------------------------------------- learned bracket
     N_PARAMS = 6658

@@ -131,6 +131,7 @@ gbs_status gbs_set_config(gbs_ctx* c, const gbs_config* cfg) {
   if (!c || !cfg) return GBS_EINVAL;
   if (cfg->cap < 0 || cfg->maxit < 0 || cfg->blocks_per_sm < 0) return GBS_EINVAL;
   if (cfg->lms_start < 0 || cfg->lms_start > 1) return GBS_EINVAL;
+  if (cfg->knn_start < 0 || cfg->knn_start > 1) return GBS_EINVAL;
   c->cfg = *cfg;
   return GBS_OK;
 }

@@ -41,6 +41,9 @@ struct gbs_ctx {
   // fused LMS / LTS: split X and theta, per-candidate state, compaction buffers
   void* fused_buf = nullptr;
   size_t fused_bytes = 0;
+  // kNN: padded rows and queries, brackets, compaction buffers, partial sums
+  void* knn_buf = nullptr;
+  size_t knn_bytes = 0;
   // bracket-proposal network: weights | Adam m | Adam v | gradient | scalars (device)
   float* model = nullptr;
   int model_loaded = 0;
@@ -54,3 +57,4 @@ void gbs_internal_release(gbs_ctx* c);
 void gbs_internal_release_lms(gbs_ctx* c);
 void gbs_internal_release_fused(gbs_ctx* c);
 void gbs_internal_release_model(gbs_ctx* c);
+void gbs_internal_release_knn(gbs_ctx* c);

@@ -56,6 +56,8 @@ def test_host_side_checks_need_no_gpu(libpath):
     assert gbs.gbs_median_f64(None, None, 0, None, None) == gbs.GBS_EINVAL
     assert gbs.gbs_cost_pass_f32(None, None, 5, 1, 0.0, 1.0, None, None) == gbs.GBS_EINVAL
     assert gbs.gbs_create(None, 0) == gbs.GBS_EINVAL
+    assert gbs.gbs_knn_regress_f32(None, None, 10, 2, None, None, 1, 1, 0, 0.0, None, None, None) == gbs.GBS_EINVAL
+    assert gbs.gbs_knn_classify_f32(None, None, 10, 2, None, 3, None, 1, 1, None, None, None, None) == gbs.GBS_EINVAL
 
 
 def test_struct_sizes_match_header(libpath):

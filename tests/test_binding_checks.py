@@ -47,7 +47,9 @@ def test_host_tensors_are_never_accepted(ctx):
                  lambda: ctx.cost_pass(x, 1, 0.0, 1.0), lambda: ctx.compact(x, 0.0, 1.0),
                  lambda: ctx.select_segmented(x, torch.tensor([0, 100])),
                  lambda: ctx.bracket_features(x), lambda: ctx.bracket_propose(x),
-                 lambda: ctx.generate_training_array(x, 0)):
+                 lambda: ctx.generate_training_array(x, 0),
+                 lambda: ctx.knn_regress(x.view(25, 4), x, x.view(25, 4), 1),
+                 lambda: ctx.knn_classify(x.view(25, 4), x.int(), 3, x.view(25, 4), 1)):
         with pytest.raises(TypeError, match="CUDA"):
             call()
 
@@ -70,6 +72,11 @@ def test_shapes_that_would_overrun_a_buffer_are_refused(ctx):
         ctx.lms_lts(torch.zeros(10, 3, dtype=torch.float64), torch.zeros(10), torch.zeros(2, 3))
     with pytest.raises(ValueError, match="2-d"):
         ctx.lms_lts_fused(torch.zeros(30), torch.zeros(10), torch.zeros(2, 3))
+    # kNN: float32 point and query rows
+    with pytest.raises(TypeError, match="float32"):
+        ctx.knn_regress(torch.zeros(10, 3, dtype=torch.float64), torch.zeros(10), torch.zeros(2, 3), 1)
+    with pytest.raises(ValueError, match="2-d"):
+        ctx.knn_classify(torch.zeros(30), torch.zeros(30, dtype=torch.int32), 2, torch.zeros(2, 3), 1)
     # segmented: float32 values, int64 offsets
     with pytest.raises(TypeError, match="float32"):
         ctx.select_segmented(torch.zeros(10, dtype=torch.float64), torch.tensor([0, 10]))
