@@ -388,6 +388,125 @@ def bench_lms(gbs, ctx, torch, np, args):
     }
 
 
+KNN_N, KNN_P, KNN_M, KNN_K, KNN_C, KNN_SEED = 1 << 20, 8, 4096, 256, 16, 350
+
+
+_KNN_DATA = None
+
+
+def _knn_worker_init():
+    """Pool worker start-up: the kNN problem, generated once per process."""
+    global _KNN_DATA
+    import synth
+    _KNN_DATA = synth.knn_problem(KNN_N, KNN_P, KNN_M, KNN_C, seed=KNN_SEED)
+
+
+def _knn_oracle_queries(idx):
+    """CPU oracle for a few kNN queries (one task of the pool): float32 distances in the
+    stated order, then the regression and the class vote of each query."""
+    import numpy as np
+    from oracle import knn as oknn
+    X, Q, f, labels = _KNN_DATA
+    D2 = oknn.squared_distances_f32(X, Q[idx]).astype(np.float64)
+    oknn.regress_d2(D2, f, KNN_K, "inverse", 1e-6)
+    oknn.classify_d2(D2, labels, KNN_K, KNN_C)
+    return len(idx)
+
+
+def oracle_pool_time(fn, tasks, init=None):
+    """Wall time of fn over tasks on every host core (a spawn-started process pool, so no
+    process forks after CUDA is initialised; `init` runs in each worker before the timed
+    region) and the cores used."""
+    import multiprocessing as mp
+    cores = min(len(tasks), os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(cores, initializer=init) as pool:
+        pool.map(fn, tasks[:cores], chunksize=1)   # start-up outside the timed region
+        t0 = time.perf_counter()
+        pool.map(fn, tasks, chunksize=1)
+        wall = time.perf_counter() - t0
+    return wall, cores
+
+
+def bench_knn(gbs, ctx, torch, np, args):
+    """kNN regression (inverse-distance weights) and classification through d_(k) (Sec. 5):
+    n = 2^20 points in p = 8 dimensions from 16 Gaussian clusters, 4096 queries, k = 256;
+    the sampled-bracket form (one fused pass) against the plain form (distance rows written
+    out, d_(k) by the segmented select, then the reduction pass).  Roofline of the fused
+    pass kernel: 3p floating-point operations per (query, point) pair -- the distance in
+    its stated order (p differences, p products, p - 1 sums) and one comparison -- against
+    the float32 issue rate of the SMs (128 lanes each per clock at the sampled clock)."""
+    import synth
+    X, Q, f, labels = synth.knn_problem(KNN_N, KNN_P, KNN_M, KNN_C, seed=KNN_SEED)
+    Xt, Qt, ft, lt = (torch.from_numpy(a).cuda() for a in (X, Q, f, labels))
+    m = KNN_M
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    reps = max(3, min(20, args.steps // 5))
+    res = {}
+    pass_ms = []
+    for start in (0, 1):
+        ctx.set_config(knn_start=start)
+        r_ms, (pred, kth) = timed(lambda: ctx.knn_regress(Xt, ft, Qt, KNN_K, weight="inverse"), reps)
+        rec = ctx.knn_last_stats()
+        if start == 0 and rec["pass_launches"]:
+            pass_ms.append(rec["pass_ms"] / rec["pass_launches"])
+        c_ms, (cls, votes, kth2) = timed(lambda: ctx.knn_classify(Xt, lt, KNN_C, Qt, KNN_K), reps)
+        rec2 = ctx.knn_last_stats()
+        if start == 0 and rec2["pass_launches"]:
+            pass_ms.append(rec2["pass_ms"] / rec2["pass_launches"])
+        res[start] = (r_ms, c_ms, pred.cpu().numpy(), cls.cpu().numpy(), kth.cpu().numpy(), rec)
+    ctx.set_config(knn_start=0)
+    same = bool(np.array_equal(res[0][3], res[1][3]) and np.array_equal(res[0][4].view(np.uint32),
+                                                                         res[1][4].view(np.uint32)))
+    pred_diff = float(np.max(np.abs(res[0][2] - res[1][2]) / np.maximum(np.abs(res[1][2]), 1e-300)))
+    # roofline of the fused pass kernel (ALU issue)
+    clk = None
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(torch.cuda.current_device()), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10).stdout
+        clk = float(out.strip().splitlines()[0])
+    except Exception:
+        clk = 2070.0
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak_ops = sms * 128 * clk * 1e6
+    ops = 3 * KNN_P * KNN_M * KNN_N
+    pms = statistics.median(pass_ms) if pass_ms else None
+    achieved = ops / (pms * 1e-3) if pms else None
+    # CPU oracle: 64 queries on every host core
+    cpu = None
+    if not args.no_cpu:
+        tasks = [[i] for i in range(0, 64 * 16, 16)]
+        wall, cores = oracle_pool_time(_knn_oracle_queries, tasks, init=_knn_worker_init)
+        cpu = {"value": len(tasks) / wall, "unit": "queries/s", "cores": cores, "kind": "oracle",
+               "sample": f"{len(tasks)} of the {KNN_M} queries (regression and vote each), one query per task"}
+    return {
+        "workload": f"kNN, n=2^20 points, p={KNN_P}, {KNN_C} Gaussian clusters, {KNN_M} queries, k={KNN_K}; "
+                    "regression with inverse-distance weights and class vote",
+        "metric": "queries/s", "value": m / (res[0][0] * 1e-3), "regress_ms": res[0][0], "classify_ms": res[0][1],
+        "classify_queries_s": m / (res[0][1] * 1e-3), "passes": res[0][5]["passes"],
+        "plain_queries": res[0][5]["plain_queries"],
+        "plain_form": {"regress_ms": res[1][0], "classify_ms": res[1][1], "value": m / (res[1][0] * 1e-3),
+                       "passes": res[1][5]["passes"]},
+        "speedup_vs_plain": res[1][0] / res[0][0], "identical_classes_and_kth": same,
+        "max_rel_pred_diff_vs_plain": pred_diff,
+        "roofline": {"bound": "alu", "kernel": "knn_pass_kernel<8,4>", "achieved": achieved, "peak": peak_ops,
+                     "unit": "FP32 lane-ops/s", "frac": achieved / peak_ops if achieved else None,
+                     "algorithmic_ops_per_launch": ops, "pass_ms": pms,
+                     "peak_derivation": f"{sms} SMs x 128 FP32 lanes x {clk:.0f} MHz (max SM clock)"},
+        "cpu_baseline": cpu,
+    }
+
+
 def bench_learned(gbs, ctx, torch, np, args, x_big=None):
     """Median select from the data's extremes against the same select started from the
     trained network's proposed bracket (results must be identical), on (1) held-out
@@ -747,6 +866,7 @@ def main():
         rows["learned_bracket"] = bench_learned(gbs, ctx, torch, np, args, x_big=x)
         rows["segmented"] = bench_segmented(gbs, ctx, torch, np, args)
         rows["lms_lts"] = bench_lms(gbs, ctx, torch, np, args)
+        rows["knn"] = bench_knn(gbs, ctx, torch, np, args)
         rows["f64_n2e26"] = bench_f64(gbs, ctx, torch, np, args)
         rows["families_f32"] = bench_families(gbs, ctx, torch, np, args)
 

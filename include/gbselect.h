@@ -328,6 +328,20 @@ gbs_status gbs_knn_classify_f32(gbs_ctx* ctx, const float* X, int64_t n, int32_t
                                 int32_t n_classes, const float* Q, int32_t m, int64_t k, int32_t* cls,
                                 double* votes, float* kth_d2, void* stream);
 
+/* Host record of the last kNN call on ctx (synchronises its stream): queries, queries that
+ * took the plain form, full passes over the points for the first 16384 queries (the
+ * fused pass counts 1; the plain form adds its distance rows and its second pass), and
+ * the device time of the sampled start's fused pass launches (CUDA events recorded on the
+ * call's stream around each launch), with their count. */
+typedef struct {
+    int64_t queries;
+    int64_t plain_queries;
+    int32_t passes;
+    int32_t pass_launches;
+    double pass_ms;
+} gbs_knn_stats;
+gbs_status gbs_knn_last_stats(gbs_ctx* ctx, gbs_knn_stats* out);
+
 /* ---- Learned starting bracket (no counterpart in the paper; it replaces the starting
  * bracket of Algorithm 1, step 0).  A sketch of x -- 1024 samples x[j*floor(n/1024)],
  * sorted; features: the 32 sample quantiles at sorted positions 16+32i standardised by

@@ -66,6 +66,11 @@ class gbs_shard_state(C.Structure):
                 ("result", C.c_double)]
 
 
+class gbs_knn_stats(C.Structure):
+    _fields_ = [("queries", C.c_int64), ("plain_queries", C.c_int64), ("passes", C.c_int32),
+                ("pass_launches", C.c_int32), ("pass_ms", C.c_double)]
+
+
 GBS_SHARD_ITERATE, GBS_SHARD_DONE, GBS_SHARD_COMPACT, GBS_SHARD_NAN = range(4)
 
 _P = C.c_void_p
@@ -102,6 +107,7 @@ _SIGS = {
                                       _P, _P]),
     "gbs_knn_classify_f32": (C.c_int, [_P, _P, _I64, C.c_int32, _P, C.c_int32, _P, C.c_int32, _I64, _P, _P, _P,
                                        _P]),
+    "gbs_knn_last_stats": (C.c_int, [_P, C.POINTER(gbs_knn_stats)]),
     "gbs_bracket_model_set": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int32]),
     "gbs_bracket_model_get": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int32]),
     "gbs_bracket_model_save": (C.c_int, [_P, C.c_char_p]),
@@ -437,6 +443,12 @@ class Context:
                                     C.c_void_p(v.data_ptr()) if v is not None else None, C.c_void_p(kth.data_ptr()),
                                     _stream_ptr(stream)), "gbs_knn_classify")
         return cls, v, kth
+
+    def knn_last_stats(self):
+        """Record of the last kNN call (synchronises its stream)."""
+        rec = gbs_knn_stats()
+        _check(gbs_knn_last_stats(self._h, C.byref(rec)), "gbs_knn_last_stats")
+        return {f: getattr(rec, f) for f, _ in gbs_knn_stats._fields_}
 
     # -------------------------------------------------------------- learned bracket
     N_PARAMS = 6658

@@ -44,6 +44,8 @@ struct gbs_ctx {
   // kNN: padded rows and queries, brackets, compaction buffers, partial sums
   void* knn_buf = nullptr;
   size_t knn_bytes = 0;
+  cudaEvent_t knn_ev[2] = {nullptr, nullptr};   // around the fused pass launches
+  gbs_knn_stats knn_last{};
   // bracket-proposal network: weights | Adam m | Adam v | gradient | scalars (device)
   float* model = nullptr;
   int model_loaded = 0;

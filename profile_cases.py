@@ -11,6 +11,7 @@ Cases (inputs from ``synth``; every case holds at most a few GB on the device):
   lms        LMS/LTS objectives, n = 1e6, p = 8, 512 candidates (seeds 6, 7), TF32x3 + batched
   lms_fused  the same objectives for 2048 candidates with the residuals recomputed per pass
   propose    the bracket-proposal kernel on a 2^24 array, R calls
+  knn        kNN regression, n = 2^20, p = 8, 4096 queries, k = 256 (seed 350), sampled brackets
 Each case runs W warm-up repetitions, then R timed ones, prints one line with the mean
 device time per repetition and exits 0.
 """
@@ -27,7 +28,7 @@ sys.path.insert(0, HERE)
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["select", "select64", "learned", "segmented", "segmented_learned", "lms",
-                                     "lms_fused", "propose"])
+                                     "lms_fused", "propose", "knn"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
     args = ap.parse_args()
@@ -79,6 +80,12 @@ def main():
                 ctx.lms_lts(Xd, yd, td, (n + 1) // 2, (n + p + 1) // 2, precision=1, batched=1)
             else:
                 ctx.lms_lts_fused(Xd, yd, td, (n + 1) // 2, (n + p + 1) // 2)
+    elif case == "knn":
+        X, Q, f, _ = synth.knn_problem(1 << 20, 8, 4096, 16, seed=350)
+        Xt, Qt, ft = (torch.from_numpy(a).cuda() for a in (X, Q, f))
+
+        def rep():
+            ctx.knn_regress(Xt, ft, Qt, 256, weight="inverse")
     else:
         x = torch.empty(1 << 24, device="cuda")
         ctx.generate_training_array(x, 1, 3.0, 0.0, 1.0, 5.0, 2.0, seed=123)
