@@ -130,6 +130,23 @@ MUTANTS = [
      "y[:, None] - X @ theta", "y[:, None] - X[:, ::-1] @ theta", 1,
      [(R, "test_residual_sign_and_shape", {}),
       (R, "test_exact_fit_candidate_has_zero_residuals_on_its_subset", {})]),
+    ("rho_tie_share_inverted", oreg, "rho_weights",
+     "rho[tie] = a / b", "rho[tie] = b / max(a, 1)", 1,
+     [(R, "test_rho_weights_sum_to_h_and_give_the_lts_objective", {})]),
+    ("c_step_unweighted_response", oreg, "c_step",
+     "b = Xd.T @ (rho * yd)", "b = Xd.T @ yd", 1,
+     [(R, "test_c_step_fixed_point_and_recovery_of_the_clean_model", {}),
+      (R, "test_c_steps_never_increase_the_objective", {})]),
+    ("c_step_gram_transposed_weights", oreg, "c_step",
+     "A = Xd.T @ (rho[:, None] * Xd)", "A = Xd.T @ Xd", 1,
+     [(R, "test_c_step_fixed_point_and_recovery_of_the_clean_model", {}),
+      (R, "test_lts_brute_force_optimum_is_a_c_step_fixed_point", {})]),
+    ("f32_residual_fused_in_float64", oreg, "squared_residuals_f32",
+     "acc = acc + X[:, j] * theta[j]", "acc = (acc.astype(np.float64) + X[:, j].astype(np.float64) * theta[j]).astype(np.float32)", 1,
+     [(R, "test_float32_residuals_follow_their_stated_order", {})]),
+    ("c_steps_accepts_increase", oreg, "c_steps",
+     "if not Fn < F:", "if False:", 1,
+     [(R, "test_c_step_fixed_point_and_recovery_of_the_clean_model", {})]),
     ("knn_tie_weight_full", oknn, "indicator",
      "rho[tie] = a / b", "rho[tie] = 1.0", 1,
      [(K, "test_indicator_is_inclusion_frequency_over_tie_breaks", {})]),
