@@ -288,6 +288,40 @@ gbs_status gbs_lms_lts_fused_f32(gbs_ctx* ctx, const float* X, const float* y, i
                                  const float* theta, int32_t C, int64_t k_lms, int64_t h_lts,
                                  float* lms_out, double* lts_out, int32_t* passes, void* stream);
 
+/* ---- The LMS / LTS estimator search (Sec. 5: computing the estimator takes many
+ * evaluations of F(theta)).  Candidates theta_c (C x p row-major float32, device; elemental
+ * fits, for instance) are given.
+ * C-steps (concentration steps) refine an LTS fit: refit the model by least squares on
+ * the h observations the objective retains -- the rows weighted by the rho of
+ * Eq. (med_reg), 1 below q = s_(h), a/b at q, 0 above -- and repeat while the objective
+ * decreases; it cannot increase.  Which rows are retained is decided on float32 squared
+ * residuals formed in a stated order (for j = 0..p-1, acc = acc + x_j * theta_j, each
+ * product and sum rounded, no fused multiply-add; r = y - acc; s = r * r); the refit is
+ * solved in float64 (normal equations, Cholesky) and rounded to float32; objectives are
+ * float64 sums of those squares. */
+
+/* For each candidate c: theta_out[c] (C x p float32, device) = the best fit reached from
+ * theta[c] by at most max_steps refits, obj_out[c] (C float64, device) its LTS objective,
+ * refits_out[c] (C int32, device, may be NULL) the refits kept.  1 <= p <= 16,
+ * 1 <= h <= n <= 2^31, 0 <= max_steps <= 1000.  A refit whose retained rows do not
+ * determine the coefficients (a non-positive Cholesky pivot) ends that candidate.  Squares
+ * of up to 1 GiB of candidates at a time are written to the workspace.  Synchronises
+ * `stream` once per refit round. */
+gbs_status gbs_lts_csteps_f32(gbs_ctx* ctx, const float* X, const float* y, int64_t n, int32_t p, const float* theta,
+                              int32_t C, int64_t h, int32_t max_steps, float* theta_out, double* obj_out,
+                              int32_t* refits_out, void* stream);
+/* The estimators: both objectives of every candidate by gbs_lms_lts_fused_f32; LMS: the
+ * candidate of least LMS objective (the smallest index among equal values) -> lms_theta
+ * (p floats), lms_value, lms_index; LTS: the n_refine candidates of least LTS objective
+ * (smaller index first on ties) refined by C-steps, the refined fit of least objective
+ * (the better-ranked start on ties) -> lts_theta (p floats), lts_value (float64),
+ * lts_index (its start).  All outputs are device pointers; lms_index and lts_index may be
+ * NULL.  1 <= C <= 65536 (candidates are ranked by counting); other limits as above. */
+gbs_status gbs_lms_lts_search_f32(gbs_ctx* ctx, const float* X, const float* y, int64_t n, int32_t p,
+                                  const float* theta, int32_t C, int64_t k_lms, int64_t h_lts, int32_t n_refine,
+                                  int32_t max_steps, float* lms_theta, float* lms_value, int32_t* lms_index,
+                                  float* lts_theta, double* lts_value, int32_t* lts_index, void* stream);
+
 /* ---- k-nearest-neighbour regression and classification through the k-th order
  * statistic of the distances (Sec. 5, last application).  For each query q_j the k
  * nearest of the n points x_i (Euclidean) are marked by an indicator against d_(k), the

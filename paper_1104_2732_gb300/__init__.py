@@ -103,6 +103,9 @@ _SIGS = {
                                   C.c_int32, _P]),
     "gbs_lms_lts_fused_f32": (C.c_int, [_P, _P, _P, _I64, C.c_int32, _P, C.c_int32, _I64, _I64, _P, _P,
                                         C.POINTER(C.c_int32), _P]),
+    "gbs_lts_csteps_f32": (C.c_int, [_P, _P, _P, _I64, C.c_int32, _P, C.c_int32, _I64, C.c_int32, _P, _P, _P, _P]),
+    "gbs_lms_lts_search_f32": (C.c_int, [_P, _P, _P, _I64, C.c_int32, _P, C.c_int32, _I64, _I64, C.c_int32, C.c_int32,
+                                         _P, _P, _P, _P, _P, _P, _P]),
     "gbs_knn_regress_f32": (C.c_int, [_P, _P, _I64, C.c_int32, _P, _P, C.c_int32, _I64, C.c_int32, C.c_double, _P,
                                       _P, _P]),
     "gbs_knn_classify_f32": (C.c_int, [_P, _P, _I64, C.c_int32, _P, C.c_int32, _P, C.c_int32, _I64, _P, _P, _P,
@@ -403,6 +406,42 @@ class Context:
                                      C.c_void_p(lts.data_ptr()), C.byref(npass), _stream_ptr(stream)),
                "gbs_lms_lts_fused")
         return lms, lts, npass.value
+
+    def lts_csteps(self, X, y, theta, h=None, max_steps=20, stream=None):
+        """(theta_out (C, p) float32, objective (C,) float64, refits (C,) int32): C-steps of
+        the LTS objective from every candidate row of theta (gbs_lts_csteps_f32)."""
+        import torch
+        X, y, theta, n, p, Cn = self._reg_args(X, y, theta)
+        h = (n + p + 1) // 2 if h is None else int(h)
+        th_out = torch.empty(Cn, p, dtype=torch.float32, device=X.device)
+        obj = torch.empty(Cn, dtype=torch.float64, device=X.device)
+        ref = torch.empty(Cn, dtype=torch.int32, device=X.device)
+        _check(gbs_lts_csteps_f32(self._h, C.c_void_p(X.data_ptr()), C.c_void_p(y.data_ptr()), n, p,
+                                  C.c_void_p(theta.data_ptr()), Cn, h, int(max_steps), C.c_void_p(th_out.data_ptr()),
+                                  C.c_void_p(obj.data_ptr()), C.c_void_p(ref.data_ptr()), _stream_ptr(stream)),
+               "gbs_lts_csteps")
+        return th_out, obj, ref
+
+    def lms_lts_search(self, X, y, theta, k=None, h=None, n_refine=10, max_steps=20, stream=None):
+        """The LMS and LTS estimates over the candidate rows of theta: a dict of device
+        tensors lms_theta, lms_value, lms_index, lts_theta, lts_value, lts_index."""
+        import torch
+        X, y, theta, n, p, Cn = self._reg_args(X, y, theta)
+        k = (n + 1) // 2 if k is None else int(k)
+        h = (n + p + 1) // 2 if h is None else int(h)
+        dev = X.device
+        out = {"lms_theta": torch.empty(p, dtype=torch.float32, device=dev),
+               "lms_value": torch.empty(1, dtype=torch.float32, device=dev),
+               "lms_index": torch.empty(1, dtype=torch.int32, device=dev),
+               "lts_theta": torch.empty(p, dtype=torch.float32, device=dev),
+               "lts_value": torch.empty(1, dtype=torch.float64, device=dev),
+               "lts_index": torch.empty(1, dtype=torch.int32, device=dev)}
+        ptr = {kk: C.c_void_p(v.data_ptr()) for kk, v in out.items()}
+        _check(gbs_lms_lts_search_f32(self._h, C.c_void_p(X.data_ptr()), C.c_void_p(y.data_ptr()), n, p,
+                                      C.c_void_p(theta.data_ptr()), Cn, k, h, int(n_refine), int(max_steps),
+                                      ptr["lms_theta"], ptr["lms_value"], ptr["lms_index"], ptr["lts_theta"],
+                                      ptr["lts_value"], ptr["lts_index"], _stream_ptr(stream)), "gbs_lms_lts_search")
+        return out
 
     # -------------------------------------------------------------- kNN
     def _knn_args(self, X, Q, k):

@@ -46,6 +46,11 @@ struct gbs_ctx {
   size_t knn_bytes = 0;
   cudaEvent_t knn_ev[2] = {nullptr, nullptr};   // around the fused pass launches
   gbs_knn_stats knn_last{};
+  // LMS / LTS search: squares of a batch of candidates, C-step state; search arrays
+  void* search_buf = nullptr;
+  size_t search_bytes = 0;
+  void* search_aux = nullptr;
+  size_t search_aux_bytes = 0;
   // bracket-proposal network: weights | Adam m | Adam v | gradient | scalars (device)
   float* model = nullptr;
   int model_loaded = 0;
@@ -60,3 +65,4 @@ void gbs_internal_release_lms(gbs_ctx* c);
 void gbs_internal_release_fused(gbs_ctx* c);
 void gbs_internal_release_model(gbs_ctx* c);
 void gbs_internal_release_knn(gbs_ctx* c);
+void gbs_internal_release_search(gbs_ctx* c);

@@ -6,4 +6,5 @@ void gbs_internal_release(gbs_ctx* c) {
   gbs_internal_release_fused(c);
   gbs_internal_release_model(c);
   gbs_internal_release_knn(c);
+  gbs_internal_release_search(c);
 }
