@@ -320,7 +320,7 @@ def bench_lms(gbs, ctx, torch, np, args):
     import synth
     from oracle import regression as oreg
     n, p, C = 1_000_000, 8, 2048
-    X, y, _ = synth.regression(n, p, 6)
+    X, y, beta = synth.regression(n, p, 6)
     th = np.ascontiguousarray(synth.elemental_thetas(X, y, C, 7).T)
     k, h = (n + 1) // 2, (n + p + 1) // 2
     Xt, yt, tt = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (X, y, th))
@@ -346,6 +346,10 @@ def bench_lms(gbs, ctx, torch, np, args):
     fx_same = bool(torch.equal(lms_x.view(torch.int32), lms_f.view(torch.int32)))
     mat_ms, (lms_m, lts_m) = timed(lambda: ctx.lms_lts(Xt, yt, tt, k=k, h=h, precision=1, batched=True), reps)
     plain_ms, (lms_p, lts_p) = timed(lambda: ctx.lms_lts(Xt, yt, tt, k=k, h=h, precision=0, batched=False), 1)
+    # the estimator search: LMS argmin and LTS refined by C-steps from the 10 best candidates
+    search_ms, srch = timed(lambda: ctx.lms_lts_search(Xt, yt, tt, k=k, h=h, n_refine=10, max_steps=20),
+                            max(2, reps // 4))
+    srch = {kk: v.cpu().numpy() for kk, v in srch.items()}
     # the residual kernel alone (materialised form): bytes written against HBM
     S = torch.empty(C, n, dtype=torch.float32, device="cuda")
     res_ms, _ = timed(lambda: ctx.residual_sq(Xt, yt, tt, precision=1, out=S), reps)
@@ -382,6 +386,11 @@ def bench_lms(gbs, ctx, torch, np, args):
                             "hbm_frac": C * n * 4 / (res_ms * 1e-3) / 1e9 / hbm, "peak_kind": f"{kind} hbm_gbs"},
         "cpu_baseline": {"value": len(sample) / cpu_s, "unit": "candidates/s", "cores": 1, "kind": "oracle",
                          "sample": f"float64 LMS and LTS of {len(sample)} of the {C} candidates"},
+        "search": {"ms": search_ms, "n_refine": 10, "max_steps": 20,
+                   "lms_value": float(srch["lms_value"][0]), "lts_value": float(srch["lts_value"][0]),
+                   "lts_start_index": int(srch["lts_index"][0]),
+                   "lts_theta_max_abs_err_vs_beta": float(np.max(np.abs(srch["lts_theta"] - beta))),
+                   "lms_theta_max_abs_err_vs_beta": float(np.max(np.abs(srch["lms_theta"] - beta)))},
         "fused_vs_materialised_max_rel_diff": {
             "lms": float(np.max(np.abs(forms["fused"][0] / forms["materialised"][0] - 1))),
             "lts": float(np.max(np.abs(forms["fused"][1] / forms["materialised"][1] - 1)))},

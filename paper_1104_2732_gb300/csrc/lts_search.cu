@@ -15,9 +15,10 @@
 //   select     the segmented select in its trimmed-sum mode: q_c = s_(h) and the
 //              objective F_c = sum of the h smallest (float64), Eq. (med_reg);
 //   counts     #(s < q_c) and #(s = q_c), so the tie weight a/b is known;
-//   normal eqs the rho-weighted Gram matrix X^T diag(rho) X and X^T diag(rho) y in
-//              float64 (products of float32 values are exact in float64), CTA partials
-//              per row chunk, summed in a fixed order;
+//   normal eqs the rho-weighted Gram matrix X^T diag(rho) X and X^T diag(rho) y: exact
+//              products of float32 values summed as float32 pairs (the float64 pipe of
+//              this GPU is narrow), CTA partials per row chunk summed in float64 in a
+//              fixed order;
 //   solve      Cholesky in float64, one thread per candidate; the refit is rounded to
 //              float32 (coefficients are float32, as the candidates).
 // A candidate stops when the objective of its latest refit is not lower than the best
@@ -93,7 +94,12 @@ __global__ void __launch_bounds__(256) cs_count_kernel(const float* __restrict__
 // CTA (chunk, candidate): the rho-weighted normal equations over the chunk's rows.  Entry
 // e < p(p+1)/2 is G[j][k] (j <= k, row-major upper triangle), then p entries of X^T rho y.
 // Thread t takes entry t % E over the rows t / E, t / E + P, ... of each staged tile
-// (P = kGT / E phases), accumulating in float64; the phases are summed in order.
+// (P = kGT / E phases).  The rows with weight 1 are summed exactly enough without the
+// narrow float64 pipe: each product of two float32 values is split exactly into a float32
+// pair (p = a b rounded, e = fma(a, b, -p)), and the pairs are added to a float32 pair
+// accumulator (two-sum of the high parts, low parts added), about 2^-44 relative per add;
+// the rare tied rows (weight a/b) are summed in float64.  The phases are combined in
+// float64, in order.
 __global__ void __launch_bounds__(kGT) cs_gram_kernel(const float* __restrict__ X, const float* __restrict__ y,
                                                      const float* __restrict__ S, long long n, int p,
                                                      long long rows_per_chunk, const float* q,
@@ -123,7 +129,8 @@ __global__ void __launch_bounds__(kGT) cs_gram_kernel(const float* __restrict__ 
   const double w_eq = neq > 0 ? (double)(h - nlt) / (double)neq : 0.0;
   const long long r0 = (long long)blockIdx.x * rows_per_chunk;
   const long long r1 = min(n, r0 + rows_per_chunk);
-  double acc = 0.0;
+  float hi = 0.f, lo = 0.f;   // float32 pair accumulator of the weight-1 rows
+  double tie = 0.0;           // the tied rows, float64
   for (long long rt = r0; rt < r1; rt += kGRows) {
     const int rows = (int)min((long long)kGRows, r1 - rt);
     __syncthreads();
@@ -138,15 +145,24 @@ __global__ void __launch_bounds__(kGT) cs_gram_kernel(const float* __restrict__ 
       for (int i = ph; i < rows; i += phases) {
         const float rho = s_rho[i];
         if (rho == 0.f) continue;
-        const double a = (double)s_x[i * p + ej];
-        const double b = ek >= 0 ? (double)s_x[i * p + ek] : (double)s_y[i];
-        if (rho > 0.f) acc = fma(a, b, acc);
-        else acc += w_eq * (a * b);
+        const float a = s_x[i * p + ej];
+        const float b = ek >= 0 ? s_x[i * p + ek] : s_y[i];
+        if (rho > 0.f) {
+          const float pr = __fmul_rn(a, b);
+          const float pe = __fmaf_rn(a, b, -pr);           // a b = pr + pe exactly
+          const float t = __fadd_rn(hi, pr);
+          const float bv = __fsub_rn(t, hi);
+          const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bv)), __fsub_rn(pr, bv));   // hi + pr = t + err
+          hi = t;
+          lo = __fadd_rn(lo, __fadd_rn(err, pe));
+        } else {
+          tie += w_eq * ((double)a * (double)b);
+        }
       }
     }
   }
   __syncthreads();
-  s_acc[tid] = acc;
+  s_acc[tid] = ((double)hi + (double)lo) + tie;
   __syncthreads();
   if (tid < nE) {
     double t = 0.0;
@@ -155,49 +171,67 @@ __global__ void __launch_bounds__(kGT) cs_gram_kernel(const float* __restrict__ 
   }
 }
 
-// Per candidate: the objective of its current fit against the best so far (a refit is
-// kept while it lowers the objective), then -- when refits continue -- the normal
-// equations summed over the chunks in order, solved by Cholesky in float64 and rounded
-// to float32.  A candidate whose retained rows do not determine the fit (a pivot that is
-// not positive) stops with its best fit.
-__global__ void cs_update_kernel(int C, int p, int step, int max_steps, const float* q, const unsigned long long* cnt,
-                                 const double* sum_part, int nsum, long long h, int* active, float* th,
-                                 float* th_best, double* F_best, int* refits, const double* part, int nchunks) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= C || !active[c]) return;
+// One CTA per candidate: the objective of its current fit against the best so far (a
+// refit is kept while it lowers the objective), then -- when refits continue -- the normal
+// equations summed over the chunks in order (a thread per entry), solved by Cholesky in
+// float64 by thread 0 and rounded to float32.  A candidate whose retained rows do not
+// determine the fit (a pivot that is not positive) stops with its best fit.
+__global__ void __launch_bounds__(256) cs_update_kernel(int p, int step, int max_steps, const float* q,
+                                                        const unsigned long long* cnt, const double* sum_part,
+                                                        int nsum, long long h, int* active, float* th,
+                                                        float* th_best, double* F_best, int* refits,
+                                                        const double* part, int nchunks) {
+  __shared__ double s_e[kPMax * (kPMax + 1) / 2 + kPMax];
+  __shared__ double s_w[8];
+  __shared__ int s_go;
+  const int c = blockIdx.x, tid = threadIdx.x;
+  if (!active[c]) return;
   float* tc = th + (long long)c * p;
   float* bc = th_best + (long long)c * p;
   // the objective of the current fit, Eq. (med_reg): the squares below q plus (h - #(s < q)) q
   double below = 0.0;
-  for (int b = 0; b < nsum; ++b) below += sum_part[(long long)c * nsum + b];
-  const double Fc = below + (double)(h - (long long)cnt[2 * c]) * (double)q[c];
-  if (step == 0) {
-    F_best[c] = Fc;
-    for (int j = 0; j < p; ++j) bc[j] = tc[j];
-  } else if (Fc < F_best[c]) {
-    F_best[c] = Fc;
-    refits[c] += 1;
-    for (int j = 0; j < p; ++j) bc[j] = tc[j];
-  } else {
-    active[c] = 0;
-    return;
+  for (int b = tid; b < nsum; b += 256) below += sum_part[(long long)c * nsum + b];
+  for (int o = 16; o > 0; o >>= 1) below += __shfl_xor_sync(0xffffffffu, below, o);
+  if ((tid & 31) == 0) s_w[tid >> 5] = below;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += s_w[w];
+    const double Fc = t + (double)(h - (long long)cnt[2 * c]) * (double)q[c];
+    int go = 1;
+    if (step == 0) {
+      F_best[c] = Fc;
+      for (int j = 0; j < p; ++j) bc[j] = tc[j];
+    } else if (Fc < F_best[c]) {
+      F_best[c] = Fc;
+      refits[c] += 1;
+      for (int j = 0; j < p; ++j) bc[j] = tc[j];
+    } else {
+      go = 0;
+    }
+    if (step == max_steps) go = 0;
+    if (!go) active[c] = 0;
+    s_go = go;
   }
-  if (step == max_steps) {
-    active[c] = 0;
-    return;
-  }
+  __syncthreads();
+  if (!s_go) return;
   const int nE = p * (p + 1) / 2 + p;
-  double G[kPMax][kPMax], v[kPMax];
-  for (int e = 0; e < nE; ++e) {
+  for (int e = tid; e < nE; e += 256) {
     double t = 0.0;
     for (int ch = 0; ch < nchunks; ++ch) t += part[((long long)c * nchunks + ch) * nE + e];
+    s_e[e] = t;
+  }
+  __syncthreads();
+  if (tid != 0) return;
+  double G[kPMax][kPMax], v[kPMax];
+  for (int e = 0; e < nE; ++e) {
     if (e < p * (p + 1) / 2) {
       int r = e, j = 0;
       while (r >= p - j) { r -= p - j; ++j; }
-      G[j][j + r] = t;
-      G[j + r][j] = t;
+      G[j][j + r] = s_e[e];
+      G[j + r][j] = s_e[e];
     } else {
-      v[e - p * (p + 1) / 2] = t;
+      v[e - p * (p + 1) / 2] = s_e[e];
     }
   }
   // Cholesky G = L L^T in place (lower triangle)
@@ -341,8 +375,8 @@ gbs_status csteps_run(gbs_ctx* c, const float* X, const float* y, long long n, i
       if (step < max_steps)
         cs_gram_kernel<<<dim3((unsigned)nch, (unsigned)mb), kGT, 0, strm>>>(X, y, S, n, p, rpc, q, cnt, h, active, part,
                                                                            nch);
-      cs_update_kernel<<<(mb + 127) / 128, 128, 0, strm>>>(mb, p, step, max_steps, q, cnt, sum_part, (int)rgrid, h,
-                                                         active, th, th_best, F_best, refits, part, nch);
+      cs_update_kernel<<<mb, 256, 0, strm>>>(p, step, max_steps, q, cnt, sum_part, (int)rgrid, h, active, th, th_best,
+                                             F_best, refits, part, nch);
       if ((st = check()) != GBS_OK) return st;
       if (step < max_steps) {   // the candidates still refitting (none: stop)
         if (cudaMemcpyAsync(h_act.data(), active, sizeof(int) * (size_t)mb, cudaMemcpyDeviceToHost, strm) != cudaSuccess ||
