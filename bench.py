@@ -705,6 +705,42 @@ def bench_families(gbs, ctx, torch, np, args):
     return {"workload": "2^27 float32 single-family arrays, 5 ranks per step", "metric": "Gelem/s", **res}
 
 
+def bench_drivers(gbs, ctx, torch, np, args):
+    """The paper's comparison of drivers (Sec. 4, Tables 1-2 and Discussion) on GB300: the
+    median of 2^25 normal float32 elements, plain and with one element set to 1e9, 1e20 or
+    3e38, selected by the host-driven state machine (one device pass per iterate, the
+    totals read back between passes, as the paper's implementation did) with each driver:
+    Kelley's cutting plane, bisection, Brent's root-finder, Kelley on u = log1p(x - x_(1)).
+    Passes and host wall time per selection; results must all equal the oracle's."""
+    from oracle import select as osel
+    from paper_1104_2732_gb300.sharded import GpuBackend, select_kth_sharded
+    import synth
+    n = 1 << 25
+    base = synth.paper_distribution("normal", n, 75)
+    k = (n + 1) // 2
+    out = {}
+    for big in (None, 1e9, 1e20, 3e38):
+        x = base.copy()
+        if big is not None:
+            x[n // 3] = np.float32(big)
+        want = np.float32(osel.select_kth(x, k)).view(np.uint32)
+        xt = torch.from_numpy(x).cuda()
+        row = {}
+        for driver in ("kelley", "bisect", "brent", "log"):
+            select_kth_sharded([xt], k, GpuBackend(ctx), elem_bytes=4, driver=driver)   # warm-up
+            torch.cuda.synchronize()
+            trace = []
+            t0 = time.perf_counter()
+            r = select_kth_sharded([xt], k, GpuBackend(ctx), elem_bytes=4, driver=driver, trace=trace)
+            ms = (time.perf_counter() - t0) * 1e3
+            row[driver] = {"passes": len(trace) + 1, "ms": ms,
+                           "identical_to_oracle": bool(np.float32(r).view(np.uint32) == want)}
+        out["none" if big is None else f"{big:g}"] = row
+        del xt
+    return {"workload": "median of 2^25 normal float32, plain and with one outlier; host-driven passes",
+            "metric": "passes per selection (the pass-0 statistics pass included)", "rows": out}
+
+
 def bench_sharded(gbs, ctx, torch, np, args, x):
     """The 2^27 array as four host-simulated shards on this device (per-shard passes with
     the library's kernels, totals summed on the host between passes); median; wall time of
@@ -872,6 +908,7 @@ def main():
         del pinned
         rows["small_n1e6"] = bench_small(gbs, ctx, torch, np, args)
         rows["sharded_4_shards"] = bench_sharded(gbs, ctx, torch, np, args, x)
+        rows["drivers"] = bench_drivers(gbs, ctx, torch, np, args)
         rows["learned_bracket"] = bench_learned(gbs, ctx, torch, np, args, x_big=x)
         rows["segmented"] = bench_segmented(gbs, ctx, torch, np, args)
         rows["lms_lts"] = bench_lms(gbs, ctx, torch, np, args)

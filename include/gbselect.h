@@ -145,9 +145,31 @@ typedef struct {
     int64_t cle_a, clt_b, cle_b;      /* #(x <= a) (-1 until counted), #(x < b), #(x <= b) */
     double a, b;           /* bracket: x_(k) lies in (a, b] */
     double t;              /* next point to evaluate (after gbs_shard_next) */
-    double dF;             /* Phi(b) - Phi(a), Phi = F/n of Eq. (med_objOS) */
+    double dF;             /* Phi(b) - Phi(a), Phi = F/n of Eq. (med_objOS) (in u = log1p(x - xmin) for
+                              the log driver) */
     double result;         /* x_(k) once DONE */
+    int32_t driver;        /* GBS_DRIVER_*: how the next point is chosen (gbs_shard_set_driver) */
+    int32_t pad2;
+    double xmin;           /* finite minimum of x (the log driver's origin) */
+    double px, pg;         /* root-finding driver: the last point evaluated and its g */
+    double step1, step2;   /* root-finding driver: the last two steps */
 } gbs_shard_state;
+
+/* How the sharded state machine picks the next point (gbs_shard_set_driver).  The
+ * paper compares Kelley's cutting plane with minimisers and root-finders of the same
+ * objective (Sec. 2, Sec. 4 Tables 1-2 and Discussion); all share the exact finish, so
+ * they differ only in the passes taken. */
+enum {
+    GBS_DRIVER_KELLEY = 0,   /* tangent intersection (Algorithm 1, step 1.1), the default */
+    GBS_DRIVER_BISECT = 1,   /* bisection of 0 in g(y): the midpoint of (a, b) in value */
+    GBS_DRIVER_BRENT = 2,    /* Brent's root-finder on g(y): inverse quadratic or secant
+                                interpolation of the subgradient counts, bisection when the
+                                interpolant leaves the bracket or does not halve the step */
+    GBS_DRIVER_LOG = 3       /* Kelley's method on the monotone image u = log(1 + x - xmin)
+                                (Sec. 4 Discussion): the cost is evaluated by
+                                gbs_cost_pass_log_*, the iterate mapped back by
+                                x = xmin + expm1(u) */
+};
 
 /* Context lifetime.  gbs_create makes a context for CUDA ordinal `device`.  Creation
  * touches only the host: the device workspace is allocated on first use or by
@@ -466,6 +488,23 @@ gbs_status gbs_shard_next(gbs_shard_state* s);
 /* Steps 1.3-1.4 from the totals of the pass at (a, t).  EINTERNAL when the totals are
  * inconsistent (c_le_a differs from the state's, or counts out of order). */
 gbs_status gbs_shard_update(gbs_shard_state* s, const gbs_cost_eval* total);
+/* Selects the driver (GBS_DRIVER_*) of a state made by gbs_shard_begin, before its first
+ * gbs_shard_next.  The log driver starts from a bisection (its cost difference over the
+ * starting bracket is not known from pass 0) and needs the passes of
+ * gbs_cost_pass_log_*.  EINVAL for an unknown driver or a state that has iterated. */
+gbs_status gbs_shard_set_driver(gbs_shard_state* s, int32_t driver);
+
+/* One pass at the points a < t for rank k in the coordinates u = log1p(x - xmin)
+ * (Sec. 4 Discussion: order statistics commute with increasing maps, and the log map
+ * keeps huge elements from swamping the cost sums): the counts #(x < t), #(x <= t),
+ * #(x <= a) as gbs_cost_pass_*, S = sum over a < x_i < t of (u(t) - u(x_i)) and
+ * dphi = (c_le_a - k + 1/2)(u(t) - u(a)) + S; u is taken of the elements inside (a, t)
+ * only (float32 arithmetic: the cost steers iterates, never results).  out: device
+ * pointer to one gbs_cost_eval.  EINVAL unless xmin - 1 < a < t, both finite. */
+gbs_status gbs_cost_pass_log_f32(gbs_ctx* ctx, const float* x, int64_t n, int64_t k, double a, double t,
+                                 double xmin, gbs_cost_eval* out, void* stream);
+gbs_status gbs_cost_pass_log_f64(gbs_ctx* ctx, const double* x, int64_t n, int64_t k, double a, double t,
+                                 double xmin, gbs_cost_eval* out, void* stream);
 
 /* Copies the elements x_i with a < x_i <= b (IEEE comparison; NaN never qualifies) into
  * z[0..z_cap) in no particular order, and stores how many qualify in *count (host

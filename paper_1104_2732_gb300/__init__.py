@@ -63,7 +63,8 @@ class gbs_shard_state(C.Structure):
                 ("use_bisect", C.c_int32), ("stalled", C.c_int32), ("dfv", C.c_int32), ("n_neginf", C.c_int64),
                 ("n_negzero", C.c_int64), ("cle_a", C.c_int64), ("clt_b", C.c_int64), ("cle_b", C.c_int64),
                 ("a", C.c_double), ("b", C.c_double), ("t", C.c_double), ("dF", C.c_double),
-                ("result", C.c_double)]
+                ("result", C.c_double), ("driver", C.c_int32), ("pad2", C.c_int32), ("xmin", C.c_double),
+                ("px", C.c_double), ("pg", C.c_double), ("step1", C.c_double), ("step2", C.c_double)]
 
 
 class gbs_knn_stats(C.Structure):
@@ -72,6 +73,8 @@ class gbs_knn_stats(C.Structure):
 
 
 GBS_SHARD_ITERATE, GBS_SHARD_DONE, GBS_SHARD_COMPACT, GBS_SHARD_NAN = range(4)
+GBS_DRIVER_KELLEY, GBS_DRIVER_BISECT, GBS_DRIVER_BRENT, GBS_DRIVER_LOG = range(4)
+DRIVERS = {"kelley": GBS_DRIVER_KELLEY, "bisect": GBS_DRIVER_BISECT, "brent": GBS_DRIVER_BRENT, "log": GBS_DRIVER_LOG}
 
 _P = C.c_void_p
 _I64 = C.c_int64
@@ -128,6 +131,9 @@ _SIGS = {
                                   _I64, C.c_int32]),
     "gbs_shard_next": (C.c_int, [C.POINTER(gbs_shard_state)]),
     "gbs_shard_update": (C.c_int, [C.POINTER(gbs_shard_state), C.POINTER(gbs_cost_eval)]),
+    "gbs_shard_set_driver": (C.c_int, [C.POINTER(gbs_shard_state), C.c_int32]),
+    "gbs_cost_pass_log_f32": (C.c_int, [_P, _P, _I64, _I64, C.c_double, C.c_double, C.c_double, _P, _P]),
+    "gbs_cost_pass_log_f64": (C.c_int, [_P, _P, _I64, _I64, C.c_double, C.c_double, C.c_double, _P, _P]),
     "gbs_compact_f32": (C.c_int, [_P, _P, _I64, C.c_double, C.c_double, _P, _I64, C.POINTER(_I64), _P]),
     "gbs_compact_f64": (C.c_int, [_P, _P, _I64, C.c_double, C.c_double, _P, _I64, C.POINTER(_I64), _P]),
     "gbs_status_string": (C.c_char_p, [C.c_int]),
@@ -291,6 +297,18 @@ class Context:
         fn = globals()["gbs_cost_pass_" + _suffix(x)]
         _check(fn(self._h, C.c_void_p(x.data_ptr()), x.numel(), int(k), float(a), float(t),
                   C.c_void_p(buf.data_ptr()), _stream_ptr(stream)), "gbs_cost_pass")
+        rec = gbs_cost_eval.from_buffer_copy(bytes(buf.cpu().numpy()))
+        return {f: getattr(rec, f) for f, _ in gbs_cost_eval._fields_ if f != "pad"}
+
+    def cost_pass_log(self, x, k, a, t, xmin, stream=None):
+        """The pass of gbs_cost_pass_log_*: counts at a and t, and the cost sum in the
+        coordinates u = log1p(x - xmin)."""
+        import torch
+        x = self._in(x, "x")
+        buf = torch.empty(C.sizeof(gbs_cost_eval), dtype=torch.uint8, device=x.device)
+        fn = globals()["gbs_cost_pass_log_" + _suffix(x)]
+        _check(fn(self._h, C.c_void_p(x.data_ptr()), x.numel(), int(k), float(a), float(t), float(xmin),
+                  C.c_void_p(buf.data_ptr()), _stream_ptr(stream)), "gbs_cost_pass_log")
         rec = gbs_cost_eval.from_buffer_copy(bytes(buf.cpu().numpy()))
         return {f: getattr(rec, f) for f, _ in gbs_cost_eval._fields_ if f != "pad"}
 

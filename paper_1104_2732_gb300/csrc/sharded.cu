@@ -16,7 +16,7 @@
 #include "common.cuh"
 #include "elem.cuh"
 
-static_assert(sizeof(gbs_shard_state) == 136, "gbs_shard_state layout is part of the C-ABI");
+static_assert(sizeof(gbs_shard_state) == 184, "gbs_shard_state layout is part of the C-ABI");
 static_assert(sizeof(gbs_array_stats) == 88 && sizeof(gbs_cost_eval) == 48, "C-ABI struct layout");
 
 namespace gbs {
@@ -77,6 +77,32 @@ void done(gbs_shard_state* s, double v, int32_t how, int64_t clt) {
   if (clt >= 0) finish_zero(s, clt);
 }
 
+// Brent's root-finder on g(y) = #(x < y) - k + 1/2 over the bracket (a, b), where
+// g(a) = #(x <= a) - k + 1/2 < 0 and g(b) = #(x < b) - k + 1/2 > 0: inverse quadratic
+// interpolation through (a, b, the last point evaluated) when their g are distinct, else
+// the secant through the ends; the interpolant is taken when it lies strictly inside and
+// moves less than half the step before last, else the midpoint (Brent's safeguard).
+double brent_point(gbs_shard_state* s, double mid) {
+  const double a = s->a, b = s->b;
+  if (s->cle_a < 0) return mid;
+  const double ga = (double)(s->cle_a - s->k) + 0.5, gb = (double)(s->clt_b - s->k) + 0.5;
+  double t;
+  const double c = s->px, gc = s->pg;
+  const bool iqi = s->it > 0 && c != a && c != b && gc != ga && gc != gb && ga != gb;
+  if (iqi) {
+    t = a * gb * gc / ((ga - gb) * (ga - gc)) + b * ga * gc / ((gb - ga) * (gb - gc)) +
+        c * ga * gb / ((gc - ga) * (gc - gb));
+  } else {
+    t = a - ga * (b - a) / (gb - ga);
+  }
+  const double last = s->it > 0 ? s->px : (std::fabs(ga) < std::fabs(gb) ? a : b);
+  const bool ok = std::isfinite(t) && t > a && t < b && (s->it < 2 || std::fabs(t - last) < 0.5 * std::fabs(s->step2));
+  const double chosen = ok ? t : mid;
+  s->step2 = s->step1;
+  s->step1 = chosen - last;
+  return chosen;
+}
+
 // ---------------------------------------------------------------------------------
 // Compaction of (a, b] (the finish of Sec. 3): warp ballots, one atomic per warp.
 // ---------------------------------------------------------------------------------
@@ -130,6 +156,78 @@ gbs_status compact(gbs_ctx* c, const T* x, int64_t n, double a, double b, T* z, 
   return (int64_t)h > zcap ? GBS_ENOMEM : GBS_OK;
 }
 
+// One pass of the log driver: the counts at a and t and S = sum over a < x < t of
+// (u(t) - u(x)), u = log1p(x - xmin) in float32; per-CTA records, summed in a fixed order
+// by log_pass_total_kernel.
+struct LogPart {
+  unsigned long long lt, le, lea;
+  double S;
+};
+template <typename T>
+__global__ void __launch_bounds__(256) log_pass_kernel(const T* __restrict__ x, long long n, T a, T t, double xmin,
+                                                       float ut, LogPart* part) {
+  __shared__ LogPart s_p[8];
+  using C = typename Ops<T>::C;
+  const C ca = CmpOf<T>::le(a), ct_lt = CmpOf<T>::lt(t), ct_le = CmpOf<T>::le(t);
+  unsigned int lt = 0, le = 0, lea = 0;
+  float S = 0.f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const T v = x[i];
+    const C cv = CmpOf<T>::of(v);
+    lt += cv < ct_lt;
+    le += cv <= ct_le;
+    lea += cv <= ca;
+    if ((cv > ca) & (cv < ct_lt)) S += ut - log1pf((float)((double)v - xmin));
+  }
+  LogPart p;
+  p.lt = __reduce_add_sync(0xffffffffu, lt);
+  p.le = __reduce_add_sync(0xffffffffu, le);
+  p.lea = __reduce_add_sync(0xffffffffu, lea);
+  double Sd = (double)S;
+  for (int o = 16; o > 0; o >>= 1) Sd += __shfl_xor_sync(0xffffffffu, Sd, o);
+  p.S = Sd;
+  if ((threadIdx.x & 31) == 0) s_p[threadIdx.x >> 5] = p;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    LogPart q = s_p[0];
+    for (int w = 1; w < 8; ++w) { q.lt += s_p[w].lt; q.le += s_p[w].le; q.lea += s_p[w].lea; q.S += s_p[w].S; }
+    part[blockIdx.x] = q;
+  }
+}
+
+__global__ void log_pass_total_kernel(const LogPart* part, int nparts, long long k, double ua, double ut,
+                                      gbs_cost_eval* out) {
+  if (threadIdx.x != 0) return;
+  LogPart q{0ull, 0ull, 0ull, 0.0};
+  for (int i = 0; i < nparts; ++i) { q.lt += part[i].lt; q.le += part[i].le; q.lea += part[i].lea; q.S += part[i].S; }
+  gbs_cost_eval e;
+  e.c_lt_t = (long long)q.lt; e.c_le_t = (long long)q.le; e.c_le_a = (long long)q.lea; e.pad = 0;
+  e.S = q.S;
+  e.dphi = ((double)e.c_le_a - (double)k + 0.5) * (ut - ua) + e.S;
+  *out = e;
+}
+
+template <typename T>
+gbs_status cost_pass_log(gbs_ctx* c, const T* x, int64_t n, int64_t k, double a, double t, double xmin,
+                         gbs_cost_eval* out, void* stream) {
+  if (!c || !x || !out || n < 1 || k < 1 || k > n) return GBS_EINVAL;
+  if (!std::isfinite(a) || !std::isfinite(t) || !std::isfinite(xmin) || !((T)a < (T)t) || !(a > xmin - 1.0))
+    return GBS_EINVAL;
+  DeviceGuard g(c->device);
+  if (!g.ok) return GBS_ECUDA;
+  gbs_status st = gbs_internal_ensure(c, 0);
+  if (st != GBS_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int blocks = (int)std::min<long long>((n + 255) / 256, (long long)c->num_sms * 8);
+  auto* part = reinterpret_cast<LogPart*>(static_cast<unsigned char*>(c->aux) + 4096);   // within the 1 MiB area
+  const double ua = std::log1p((double)(T)a - xmin), ut = std::log1p((double)(T)t - xmin);
+  log_pass_kernel<T><<<blocks, 256, 0, s>>>(x, n, (T)a, (T)t, xmin, (float)ut, part);
+  log_pass_total_kernel<<<1, 32, 0, s>>>(part, blocks, k, ua, ut, out);
+  if (cudaGetLastError() != cudaSuccess) return GBS_ECUDA;
+  c->last_stream = s;
+  return GBS_OK;
+}
+
 }  // namespace
 }  // namespace gbs
 
@@ -153,6 +251,8 @@ gbs_status gbs_shard_begin(gbs_shard_state* s, int32_t elem_bytes, int64_t n, in
   s->n_neginf = total->n_neginf;
   s->dfv = 1;
   s->cle_a = -1;
+  s->driver = GBS_DRIVER_KELLEY;
+  s->xmin = total->n_finite > 0 ? round_to(total->min, elem_bytes) : 0.0;
   const int64_t nneg = total->n_neginf, npos = total->n_posinf;
   if (total->n_nan > 0) {
     s->phase = GBS_SHARD_NAN;
@@ -207,16 +307,34 @@ gbs_status gbs_shard_next(gbs_shard_state* s) {
       return GBS_OK;
     }
   }
+  const double mid = s->a + 0.5 * (s->b - s->a);   // the bracket's midpoint in value
   double t;
-  if (s->use_bisect || !s->dfv || s->cle_a < 0) {
+  if (s->driver == GBS_DRIVER_BISECT) {
+    t = inside(mid, s->a, s->b, eb);
+  } else if (s->driver == GBS_DRIVER_BRENT) {
+    t = inside(brent_point(s, mid), s->a, s->b, eb);
+  } else if (s->use_bisect || !s->dfv || s->cle_a < 0) {
     const uint64_t ka = host_ukey(s->a, eb), kb = host_ukey(s->b, eb);
     t = inside(host_ukey_value(ka + (kb - ka) / 2, eb), s->a, s->b, eb);
   } else {
     const double gL = (double)(s->cle_a - s->k) + 0.5, gR = (double)(s->clt_b - s->k) + 0.5;
-    const double w = s->b - s->a;
-    t = inside(s->a + (gR * w - s->dF) / (gR - gL), s->a, s->b, eb);
+    if (s->driver == GBS_DRIVER_LOG) {   // the tangent intersection in u = log1p(x - xmin)
+      const double ua = std::log1p(s->a - s->xmin), ub = std::log1p(s->b - s->xmin);
+      const double ut = ua + (gR * (ub - ua) - s->dF) / (gR - gL);
+      t = inside(s->xmin + std::expm1(ut), s->a, s->b, eb);
+    } else {
+      const double w = s->b - s->a;
+      t = inside(s->a + (gR * w - s->dF) / (gR - gL), s->a, s->b, eb);
+    }
   }
   s->t = t;
+  return GBS_OK;
+}
+
+gbs_status gbs_shard_set_driver(gbs_shard_state* s, int32_t driver) {
+  if (!s || driver < GBS_DRIVER_KELLEY || driver > GBS_DRIVER_LOG || s->it != 0) return GBS_EINVAL;
+  s->driver = driver;
+  if (driver == GBS_DRIVER_LOG && s->phase == GBS_SHARD_ITERATE) s->dfv = 0;   // its dF is in u: not known yet
   return GBS_OK;
 }
 
@@ -242,8 +360,13 @@ gbs_status gbs_shard_update(gbs_shard_state* s, const gbs_cost_eval* total) {
     return GBS_OK;
   }
   const double gL = (double)(s->cle_a - k) + 0.5;
-  const double dphi = gL * (s->t - s->a) + total->S;
+  const double width = s->driver == GBS_DRIVER_LOG ? std::log1p(s->t - s->xmin) - std::log1p(s->a - s->xmin)
+                                                   : s->t - s->a;
+  const double dphi = gL * width + total->S;
   const int64_t pop = s->cle_b - s->cle_a;
+  // the root-finder's memory: the point just evaluated with its g on the side it moves
+  s->px = s->t;
+  s->pg = cle < k ? (double)(cle - k) + 0.5 : (double)(clt - k) + 0.5;
   if (cle < k) {               // step 1.4: the subgradient at t is negative
     s->a = s->t;
     s->cle_a = cle;
@@ -256,10 +379,21 @@ gbs_status gbs_shard_update(gbs_shard_state* s, const gbs_cost_eval* total) {
     s->dfv = 1;
   }
   const int64_t npop = s->cle_b - s->cle_a;
-  const int prev = s->use_bisect;
-  s->use_bisect = (!prev) && ((double)npop > 0.75 * (double)pop);
-  s->stalled = ((double)npop > 0.875 * (double)pop) ? s->stalled + 1 : 0;
+  if (s->driver == GBS_DRIVER_KELLEY || s->driver == GBS_DRIVER_LOG) {   // the safeguards of the cutting plane
+    const int prev = s->use_bisect;
+    s->use_bisect = (!prev) && ((double)npop > 0.75 * (double)pop);
+    s->stalled = ((double)npop > 0.875 * (double)pop) ? s->stalled + 1 : 0;
+  }
   return GBS_OK;
+}
+
+gbs_status gbs_cost_pass_log_f32(gbs_ctx* ctx, const float* x, int64_t n, int64_t k, double a, double t,
+                                 double xmin, gbs_cost_eval* out, void* stream) {
+  return cost_pass_log<float>(ctx, x, n, k, a, t, xmin, out, stream);
+}
+gbs_status gbs_cost_pass_log_f64(gbs_ctx* ctx, const double* x, int64_t n, int64_t k, double a, double t,
+                                 double xmin, gbs_cost_eval* out, void* stream) {
+  return cost_pass_log<double>(ctx, x, n, k, a, t, xmin, out, stream);
 }
 
 gbs_status gbs_compact_f32(gbs_ctx* ctx, const float* x, int64_t n, double a, double b, float* z, int64_t z_cap,

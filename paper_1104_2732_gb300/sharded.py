@@ -7,7 +7,9 @@ The scalar steps are the library's host functions ``gbs_shard_begin`` /
 runs on a shard through a *backend*, and the per-pass totals are formed by a *comm*:
 
 * backend (per-shard work): ``stats(x) -> dict`` (the gbs_array_stats fields),
-  ``cost_pass(x, a, t) -> dict`` (c_lt_t, c_le_t, c_le_a, S), ``compact(x, a, b) ->
+  ``cost_pass(x, a, t) -> dict`` (c_lt_t, c_le_t, c_le_a, S), ``cost_pass_log(x, a, t,
+  xmin)`` (the same with S in the coordinates u = log1p(x - xmin), for the log driver),
+  ``compact(x, a, b) ->
   shard's elements of (a, b]``, ``select(z, r) -> z_(r)``, ``concat(list)`` and
   ``empty(elem_bytes)`` (a set of no elements, for a process that holds none).
   :class:`GpuBackend` runs them with a :class:`~paper_1104_2732_gb300.Context`.
@@ -24,9 +26,9 @@ from __future__ import annotations
 import ctypes as C
 import math
 
-from . import (GBS_OK, GBS_SHARD_COMPACT, GBS_SHARD_DONE, GBS_SHARD_ITERATE, GBS_SHARD_NAN, GBS_ENAN,
-               GbsError, gbs_array_stats, gbs_cost_eval, gbs_shard_begin, gbs_shard_next,
-               gbs_shard_state, gbs_shard_update)
+from . import (DRIVERS, GBS_DRIVER_LOG, GBS_OK, GBS_SHARD_COMPACT, GBS_SHARD_DONE, GBS_SHARD_ITERATE,
+               GBS_SHARD_NAN, GBS_ENAN, GbsError, gbs_array_stats, gbs_cost_eval, gbs_shard_begin, gbs_shard_next,
+               gbs_shard_set_driver, gbs_shard_state, gbs_shard_update)
 
 _STAT_SUMS = ("n", "n_nan", "n_neginf", "n_posinf", "n_negzero", "n_finite")
 _EVAL_SUMS = ("c_lt_t", "c_le_t", "c_le_a")
@@ -119,6 +121,9 @@ class GpuBackend:
     def cost_pass(self, x, a, t):
         return self.ctx.cost_pass(x, 1, a, t)
 
+    def cost_pass_log(self, x, a, t, xmin):
+        return self.ctx.cost_pass_log(x, 1, a, t, xmin)
+
     def compact(self, x, a, b):
         return self.ctx.compact(x, a, b)
 
@@ -135,13 +140,16 @@ class GpuBackend:
         return float(self.ctx.select_kth(z, r).item())
 
 
-def select_kth_sharded(shards, k, backend, comm=None, elem_bytes=4, cap=0, maxit=0, trace=None):
+def select_kth_sharded(shards, k, backend, comm=None, elem_bytes=4, cap=0, maxit=0, trace=None, driver="kelley"):
     """x_(k) of the concatenation of the shards of every process (1-based k).
 
     ``shards``: this process's shards (any number, empty ones allowed: a process with no
     element still takes part in every collective, with zero counts and an empty set at
-    the gather); ``k`` is the rank in the whole vector.  Returns a Python float holding
-    the element (``-0.0`` kept)."""
+    the gather); ``k`` is the rank in the whole vector.  ``driver`` picks the next point:
+    "kelley" (the cutting plane, Algorithm 1), "bisect", "brent" (root-finding on the
+    subgradient) or "log" (Kelley on u = log1p(x - xmin)), the paper's comparisons; the
+    result does not depend on it.  Returns a Python float holding the element (``-0.0``
+    kept)."""
     comm = comm or LocalComm()
     shards = [s for s in shards if s is not None and len(s) > 0]
     # pass 0 on every shard (Sec. 3, step 0), totals over the shards and processes
@@ -160,13 +168,15 @@ def select_kth_sharded(shards, k, backend, comm=None, elem_bytes=4, cap=0, maxit
     state = gbs_shard_state()
     _check(gbs_shard_begin(C.byref(state), int(elem_bytes), n, int(k), C.byref(total), int(cap), int(maxit)),
            "gbs_shard_begin")
+    _check(gbs_shard_set_driver(C.byref(state), DRIVERS[driver]), "gbs_shard_set_driver")
+    log = state.driver == GBS_DRIVER_LOG
     # cutting-plane passes (Algorithm 1, steps 1.1-1.4)
     while state.phase == GBS_SHARD_ITERATE:
         _check(gbs_shard_next(C.byref(state)), "gbs_shard_next")
         if state.phase != GBS_SHARD_ITERATE:
             break
         a, t = state.a, state.t
-        ev = [backend.cost_pass(s, a, t) for s in shards]
+        ev = [backend.cost_pass_log(s, a, t, state.xmin) if log else backend.cost_pass(s, a, t) for s in shards]
         tot = gbs_cost_eval()
         for f, v in zip(_EVAL_SUMS, comm.sum_i64([sum(int(r[f]) for r in ev) for f in _EVAL_SUMS])):
             setattr(tot, f, v)

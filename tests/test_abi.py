@@ -66,7 +66,7 @@ def test_struct_sizes_match_header(libpath):
     assert ctypes.sizeof(gbs.gbs_config) == 8 + 4 * 10
     assert ctypes.sizeof(gbs.gbs_cost_eval) == 48
     assert ctypes.sizeof(gbs.gbs_array_stats) == 88
-    assert ctypes.sizeof(gbs.gbs_shard_state) == 3 * 8 + 8 * 4 + 5 * 8 + 5 * 8
+    assert ctypes.sizeof(gbs.gbs_shard_state) == 3 * 8 + 8 * 4 + 5 * 8 + 5 * 8 + 2 * 4 + 5 * 8
     assert ctypes.sizeof(gbs.gbs_run_stats) == 4 * 8 + 3 * 8 + 64 * 8 * 2 + 72 * 8 + 64 * 8 + 8
 
 
