@@ -11,7 +11,7 @@ value       whole-job Gelem/s = (selections x n) / time, device-timed with CUDA 
 e2e         the same through the public API with the array in pinned HOST memory:
             host-to-device copy + selections + device-to-host read of the results
 roofline    the persistent select kernel: algorithmic bytes (passes x n x 4 + the finish's
-            bytes: the compacted bracket written once and read once per radix round) /
+            bytes: the compacted bracket written once and read once) /
             its CUDA-event duration, against the measured HBM copy bandwidth
 cpu_baseline  the CPU oracle (numpy introselect on totalOrder keys, one thread) on the
             same array and ranks
@@ -652,7 +652,7 @@ def bench_f64(gbs, ctx, torch, np, args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
-    alg = sum((r["passes"] * n + r["finish_pop"] * (1 + r["finish_rounds"])) * 8 for r in recs)
+    alg = sum((r["passes"] * n + 2 * r["finish_pop"]) * 8 for r in recs)
     peaks, kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     for _ in range(2):
@@ -853,8 +853,9 @@ def main():
     # ---------------- roofline of the select kernel ----------------
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    # passes x n x 4 + the finish's bytes (compacted bracket written once, read once a round)
-    bytes_per_call = [(r["passes"] * n + r["finish_pop"] * (1 + r["finish_rounds"])) * 4 for r in records]
+    # passes x n x 4 + the finish's bytes (the compacted bracket written once and read once;
+    # the radix rounds after the first two read only the second-level copy)
+    bytes_per_call = [(r["passes"] * n + 2 * r["finish_pop"]) * 4 for r in records]
     alg_bytes = args.steps * sum(bytes_per_call)
     achieved = alg_bytes / (sum(launch_ms) * 1e-3) / 1e9
     traffic, traffic_src = select_traffic()

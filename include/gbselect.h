@@ -90,7 +90,7 @@ typedef struct {
     int32_t passes;        /* full passes over x, the min/max/count pass included */
     int32_t kelley_steps;  /* iterates from the tangent intersection (Algorithm 1, step 1.1) */
     int32_t bisect_steps;  /* safeguard iterates (bracket midpoint in totalOrder keys) */
-    int32_t finish_rounds; /* 8-bit radix rounds of the finish */
+    int32_t finish_rounds; /* 12-bit radix rounds of the finish */
     int32_t grid;          /* CTAs of the persistent launch */
     int32_t learned;       /* 1 if a proposed bracket was used, 2 if it failed its count check */
     int64_t n, k;

@@ -11,9 +11,10 @@ namespace gbs {
 
 constexpr int kThreads = 512;          // threads per CTA of the persistent kernels
 constexpr int kWarps = kThreads / 32;
-constexpr int kDigitBits = 8;          // radix digit of the exact finish
+constexpr int kDigitBits = 12;         // radix digit of the exact finish
 constexpr int kBins = 1 << kDigitBits;
-constexpr int kMaxRounds = 8;          // 64-bit keys / 8-bit digits
+constexpr int kMaxRounds = (64 + kDigitBits - 1) / kDigitBits;   // 64-bit keys
+static_assert(kBins % kThreads == 0, "the finish's digit search gives each thread whole bins");
 constexpr int kMaxGrid = 2048;         // upper bound on CTAs of a persistent launch
 constexpr int kMaxIt = 64;             // length of the per-call iterate record
 

@@ -107,6 +107,8 @@ extern "C" gbs_status gbs_select_kth_f32_noalloc(const float* x, int64_t n, int6
   A.rs = reinterpret_cast<gbs_run_stats*>(s.base + kOffRs);
   A.z = reinterpret_cast<float*>(s.base + kOffZ);
   A.z_elems = zel;
+  A.z2 = nullptr;   // no second-level buffer: every round of the finish reads the regions
+  A.z2_cap = 0;
   A.stats_out = nullptr;
   A.eval_out = nullptr;
   A.proposal = nullptr;

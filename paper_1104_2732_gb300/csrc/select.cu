@@ -326,7 +326,8 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
   __shared__ double s_f64[kWarps];
   __shared__ BracketState<T> s_br;
   __shared__ unsigned int s_zcnt;
-  __shared__ unsigned int s_hist[kBins];
+  __shared__ unsigned int s_z2n;   // elements this CTA copied to its segment of z2
+  __shared__ int s_found;
   __shared__ unsigned long long s_tns[72];
   __shared__ int s_ntns;
   __shared__ long long s_pops[kMaxIt];
@@ -339,10 +340,13 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
   __shared__ StatsPartial s_st;
   __shared__ Sum6 s_sum6[kWarps + 1];
 
-  // region offsets of the finish, and before it the warps' compaction staging buffers
-  __shared__ __align__(16) unsigned char s_big[kChunkBytes > 8 * (kMaxGrid + 1) ? kChunkBytes
-                                                                                 : 8 * (kMaxGrid + 1)];
+  // the finish's region offsets and digit histogram, and before them the warps'
+  // compaction staging buffers
+  constexpr int kOffBytes = 8 * (kMaxGrid + 1);
+  constexpr int kFinBytes = kOffBytes + 4 * kBins;
+  __shared__ __align__(16) unsigned char s_big[kChunkBytes > kFinBytes ? kChunkBytes : kFinBytes];
   unsigned long long* s_off = reinterpret_cast<unsigned long long*>(s_big);
+  unsigned int* const s_hist = reinterpret_cast<unsigned int*>(s_big + kOffBytes);
   T* const s_wb = reinterpret_cast<T*>(s_big) + (tid >> 5) * (kChunkBytes / sizeof(T) / kWarps);
 
   const Geometry<T> geo(A.x, n);
@@ -821,12 +825,36 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     // ---------------- exact finish: radix select inside (a, b] ----------------
     const int slot = (pass - 1) & 1;
     // region offsets (exclusive prefix of the per-CTA compaction counts)
-    for (unsigned int i = tid; i < G; i += kThreads)
-      s_off[i + 1] = pass == 0 ? __ldcg(&A.spart[i].c_reg) : __ldcg(&A.part[slot * G + i].c_reg);
-    if (tid == 0) s_off[0] = 0;
+    {   // a thread sums kOffPer consecutive counts, then a scan over the CTA
+      constexpr int kOffPer = (kMaxGrid + kThreads - 1) / kThreads;
+      unsigned long long v[kOffPer];
+      unsigned long long loc = 0;
+#pragma unroll
+      for (int j = 0; j < kOffPer; ++j) {
+        const unsigned int i = tid * kOffPer + j;
+        v[j] = i >= G ? 0ull : (pass == 0 ? __ldcg(&A.spart[i].c_reg) : __ldcg(&A.part[slot * G + i].c_reg));
+        loc += v[j];
+      }
+      unsigned long long incl = loc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((tid & 31) >= o) incl += y;
+      }
+      if ((tid & 31) == 31) s_u64[tid >> 5] = incl;
+      __syncthreads();
+      unsigned long long run = incl - loc;
+      for (int w = 0; w < (tid >> 5); ++w) run += s_u64[w];
+#pragma unroll
+      for (int j = 0; j < kOffPer; ++j) {
+        const unsigned int i = tid * kOffPer + j;
+        run += v[j];
+        if (i < G) s_off[i + 1] = run;
+      }
+      if (tid == 0) s_off[0] = 0;
+    }
     __syncthreads();
     if (tid == 0) {
-      for (unsigned int i = 1; i <= G; ++i) s_off[i] += s_off[i - 1];
       s_rank = (unsigned long long)(k - fin.cle_a);
       const U lo = ukey(fin.a) + 1, hi = ukey(fin.b);
       const U diff = lo ^ hi;
@@ -845,94 +873,154 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     // zero end takes the key of +0 (no NaN reaches the compacted regions)
     const U k_lo = ukey(fa == T(0) ? T(0) : fa), k_hi = ukey(fb == T(0) ? T(0) : fb);
     const int warp = tid >> 5;
+    // the second sweep also copies the elements of the digit the first one chose into
+    // this CTA's segment of z2, and later sweeps read only those.  Segment g starts at
+    // round_down(lo_i) + g kVec, which keeps segments apart and 16-byte aligned, so z2
+    // needs P + G kVec elements.
+    constexpr unsigned long long kZV = Ops<T>::kVec;
+    const bool use_z2 = A.z2 != nullptr && (long long)(P + (unsigned long long)G * kZV) <= A.z2_cap &&
+                        P / G < (1ull << 31);
+    T* const z2seg = use_z2 ? A.z2 + (lo_i / kZV * kZV + (unsigned long long)bid * kZV) : nullptr;
+    if (tid == 0) s_z2n = 0;
     while (s_known < W) {
       const int known = s_known;
       const U prefix = s_prefix;
       const int nbits = (W - known) < kDigitBits ? (W - known) : kDigitBits;
       const int sh = W - known - nbits;
       const unsigned int dmask = (1u << nbits) - 1u;
+      const bool copy = use_z2 && rounds == 1 && known + nbits < W;   // a later round will read z2
+      const bool from_z2 = use_z2 && rounds >= 2;
       for (int i = tid; i < kBins; i += kThreads) s_hist[i] = 0;
       __syncthreads();
-      unsigned int r = 0;
-      {
-        unsigned int lo_r = 0, hi_r = G;   // largest r with s_off[r] <= lo_i
-        while (hi_r - lo_r > 1) {
-          const unsigned int mid = (lo_r + hi_r) / 2;
-          if (s_off[mid] <= lo_i) lo_r = mid; else hi_r = mid;
-        }
-        r = lo_r;
-      }
-      for (; r < G && s_off[r] < hi_i; ++r) {
-        const unsigned long long s0 = s_off[r] > lo_i ? s_off[r] : lo_i;
-        const unsigned long long s1 = s_off[r + 1] < hi_i ? s_off[r + 1] : hi_i;
-        const T* zr = A.z + region_start(r, nch, G, Ops<T>::kVec);
-        const unsigned long long rbase = s_off[r];
-        // warp-uniform sweep, kFinU elements per lane loaded before any is used; warps
-        // with no element in the bracket skip the histogram, and a warp whose active
-        // lanes share one digit (a run of equal values) adds once
-        constexpr int kFinU = 8;
-        for (unsigned long long i0 = s0 + (unsigned long long)warp * 32; i0 < s1;
-             i0 += (unsigned long long)kThreads * kFinU) {
-          T v[kFinU];
-#pragma unroll
-          for (int j = 0; j < kFinU; ++j) {
-            const unsigned long long i = i0 + (unsigned long long)j * kThreads + lane;
-            v[j] = i < s1 ? __ldcg(zr + (i - rbase)) : fa;   // fa is outside (a, b]
+      // One element a lane, called by every lane of the warp together: the digit of an
+      // element of (a, b] under the known prefix goes to the histogram.  A lane counts
+      // one "hot" digit in a register (the digit it met twice in a row most recently, so a
+      // run of tied values does not serialise on one shared-memory address); the copying
+      // sweep appends the elements to this CTA's segment of z2, a warp at a time.
+      unsigned int hot = 0xffffffffu, last = 0xffffffffu, hcnt = 0;
+      auto take = [&](T v, bool valid) {
+        const U key = ukey(v);
+        const bool ok = valid && (key > k_lo) && (key <= k_hi) && (known == 0 || (U)(key >> (W - known)) == prefix);
+        const unsigned int d = (unsigned int)(key >> sh) & dmask;
+        if (ok) {
+          if (d == hot) {
+            ++hcnt;
+          } else {
+            atomicAdd(&s_hist[d], 1u);
+            if (d == last) {
+              if (hcnt) atomicAdd(&s_hist[hot], hcnt);
+              hot = d;
+              hcnt = 0;
+            }
+            last = d;
           }
+        }
+        if (copy) {
+          const unsigned int act = __ballot_sync(0xffffffffu, ok);
+          if (act) {
+            const int l0 = __ffs(act) - 1;
+            unsigned int base = 0;
+            if (lane == l0) base = atomicAdd(&s_z2n, (unsigned int)__popc(act));
+            base = __shfl_sync(0xffffffffu, base, l0);
+            if (ok) z2seg[base + __popc(act & ((1u << lane) - 1u))] = v;
+          }
+        }
+      };
+      // a contiguous range [j0, j1) of src (16-byte aligned): 16-byte vectors, kFinU in
+      // flight per lane, warp-uniform trips; the scalar head and tail by warp 0
+      auto sweep = [&](const T* __restrict__ src, unsigned int j0, unsigned int j1) {
+        using V = typename Ops<T>::V;
+        constexpr int kVec = Ops<T>::kVec;
+        constexpr int kFinU = 2;
+        const unsigned int jv0 = (j0 + kVec - 1) / kVec, jv1 = j1 / kVec;
+        const V* sv = reinterpret_cast<const V*>(src);
+        if (jv0 < jv1) {
+          for (unsigned int b = jv0 + (unsigned int)warp * 32; b < jv1; b += (unsigned int)kThreads * kFinU) {
+            V r[kFinU];
 #pragma unroll
-          for (int j = 0; j < kFinU; ++j) {
-            const U key = ukey(v[j]);
-            const bool inb = (key > k_lo) && (key <= k_hi);
-            const bool match = known == 0 || (U)(key >> (W - known)) == prefix;
-            const unsigned int d = (inb && match) ? (unsigned int)(key >> sh) & dmask : kBins;
-            const unsigned int act = __ballot_sync(0xffffffffu, d < kBins);
-            if (act) {
-              const int l0 = __ffs(act) - 1;
-              const unsigned int d0 = __shfl_sync(0xffffffffu, d, l0);
-              if (__all_sync(0xffffffffu, d == kBins || d == d0)) {
-                if (lane == l0) atomicAdd(&s_hist[d0], (unsigned int)__popc(act));
-              } else if (d < kBins) {
-                atomicAdd(&s_hist[d], 1u);
-              }
+            for (int u = 0; u < kFinU; ++u) {
+              const unsigned int iv = b + (unsigned int)u * kThreads + lane;
+              if (iv < jv1) r[u] = __ldcg(sv + iv);
+            }
+#pragma unroll
+            for (int u = 0; u < kFinU; ++u) {
+              const bool ok = b + (unsigned int)u * kThreads + lane < jv1;
+#pragma unroll
+              for (int e = 0; e < kVec; ++e) take(ok ? Ops<T>::get(r[u], e) : fa, ok);
             }
           }
         }
+        if (warp == 0) {   // the elements outside whole vectors (fewer than 2 kVec)
+          const unsigned int h1 = jv0 < jv1 ? jv0 * kVec : j1;
+          const unsigned int t0 = jv0 < jv1 ? jv1 * kVec : j1;
+          const unsigned int nh = h1 - j0, nt = j1 - t0;
+          const bool ok = (unsigned int)lane < nh + nt;
+          const unsigned int j = (unsigned int)lane < nh ? j0 + lane : t0 + (lane - nh);
+          take(ok ? __ldcg(src + j) : fa, ok);
+        }
+      };
+      if (from_z2) {
+        sweep(z2seg, 0u, s_z2n);   // this CTA's own copies (written by its own threads)
+      } else {
+        unsigned int r = 0;
+        {
+          unsigned int lo_r = 0, hi_r = G;   // largest r with s_off[r] <= lo_i
+          while (hi_r - lo_r > 1) {
+            const unsigned int mid = (lo_r + hi_r) / 2;
+            if (s_off[mid] <= lo_i) lo_r = mid; else hi_r = mid;
+          }
+          r = lo_r;
+        }
+        for (; r < G && s_off[r] < hi_i; ++r) {
+          const unsigned long long s0 = s_off[r] > lo_i ? s_off[r] : lo_i;
+          const unsigned long long s1 = s_off[r + 1] < hi_i ? s_off[r + 1] : hi_i;
+          const T* zr = A.z + region_start(r, nch, G, Ops<T>::kVec);
+          sweep(zr, (unsigned int)(s0 - s_off[r]), (unsigned int)(s1 - s_off[r]));
+        }
       }
+      if (hcnt) atomicAdd(&s_hist[hot], hcnt);
       __syncthreads();
       for (int i = tid; i < kBins; i += kThreads)
         if (s_hist[i]) atomicAdd(&A.ghist[rounds * kBins + i], (unsigned long long)s_hist[i]);
       if (!grid_sync(A.ctrl, G)) return;
       stamp();
-      if (tid < 32) {   // warp 0: find the digit holding rank s_rank
-        unsigned long long h[kBins / 32];
+      {   // the CTA finds the digit holding rank s_rank: kBins / kThreads bins a thread
+        constexpr int kPer = kBins / kThreads;
+        unsigned long long h[kPer];
         unsigned long long local = 0;
 #pragma unroll
-        for (int j = 0; j < kBins / 32; ++j) {
-          h[j] = __ldcg(&A.ghist[rounds * kBins + tid * (kBins / 32) + j]);
+        for (int j = 0; j < kPer; ++j) {
+          h[j] = __ldcg(&A.ghist[rounds * kBins + tid * kPer + j]);
           local += h[j];
         }
         unsigned long long incl = local;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (tid >= o) incl += y;
+          if (lane >= o) incl += y;
         }
+        if (lane == 31) s_u64[warp] = incl;
+        if (tid == 0) s_found = 0;
+        __syncthreads();
+        unsigned long long wbase = 0;
+        for (int w = 0; w < warp; ++w) wbase += s_u64[w];
         const unsigned long long want = s_rank;
-        const unsigned long long excl = incl - local;
-        const bool mine = excl < want && want <= incl;
-        const unsigned int who = __ballot_sync(0xffffffffu, mine);
-        if (mine) {
+        const unsigned long long excl = wbase + incl - local;
+        __syncthreads();   // every thread has read s_rank
+        if (excl < want && want <= excl + local) {
           unsigned long long c = excl;
           int d = 0;
-          for (int j = 0; j < kBins / 32; ++j) {
-            if (c + h[j] >= want) { d = tid * (kBins / 32) + j; break; }
+          for (int j = 0; j < kPer; ++j) {
+            if (c + h[j] >= want) { d = tid * kPer + j; break; }
             c += h[j];
           }
           s_rank = want - c;
           s_prefix = (U)((prefix << nbits) | (U)d);
           s_known = known + nbits;
+          s_found = 1;
         }
-        if (who == 0 && tid == 0) {   // no bin holds the rank: inconsistent counts
+        __syncthreads();
+        if (tid == 0 && !s_found) {   // no bin holds the rank: inconsistent counts
           atomicCAS(&A.ctrl->status, 0, (int)GBS_EINTERNAL);
           s_known = W;
           s_prefix = 0;                 // ukey_value(0) is a NaN: the result is flagged
@@ -1005,6 +1093,14 @@ long long z_elems_for(long long n, int grid) {
   const int vec = vec_of<T>();
   return region_start(grid, chunk_count(n / vec + 1), grid, vec);
 }
+// Elements of the finish's second-level buffer: the brackets compacted once they hold at
+// most cap elements (a compaction forced by the iteration limit may exceed it and then
+// reads the regions in every round).
+template <typename T>
+long long z2_elems_for(long long n, long long cap, int grid) {
+  const long long m = std::min<long long>(n, std::max<long long>(cap, std::max<long long>(n / 8, 4096)));
+  return (m + 3) / 4 * 4 + (long long)grid * vec_of<T>();
+}
 
 template <typename T>
 float stats_sigma(long long n, int grid) {
@@ -1030,18 +1126,22 @@ gbs_status launch_select(gbs_ctx* c, const T* x, long long n, long long k, T* ou
   if (!g.ok) return GBS_ECUDA;
   const int grid = grid_for<T>(c, n);
   const long long zel = z_elems_for<T>(n, grid);
-  const size_t zb = mode == kModeSelect ? (size_t)zel * sizeof(T) : 0;
+  const long long cap = c->cfg.cap > 0 ? c->cfg.cap : std::max<long long>(n / 8, 4096);
+  const size_t zb = mode == kModeSelect ? (size_t)(zel + z2_elems_for<T>(n, cap, grid)) * sizeof(T) : 0;
   gbs_status s = gbs_internal_ensure(c, zb);
   if (s != GBS_OK) return s;
   SelArgs<T> A;
   A.x = x; A.n = n; A.k = k; A.out = out; A.mode = mode;
   A.maxit = c->cfg.maxit > 0 ? c->cfg.maxit : 64;
   if (A.maxit > kMaxIt) A.maxit = kMaxIt;
-  A.cap = c->cfg.cap > 0 ? c->cfg.cap : std::max<long long>(n / 8, 4096);
+  A.cap = cap;
   A.a_eval = a; A.t_eval = t;
   A.sigma_stats = stats_sigma<T>(n, grid);
   A.ctrl = c->ctrl; A.part = c->part; A.spart = c->spart; A.ghist = c->ghist;
   A.z = reinterpret_cast<T*>(c->z); A.z_elems = zel;
+  // the finish's second-level buffer after the compaction regions (16-byte aligned)
+  A.z2 = mode == kModeSelect ? A.z + zel : nullptr;
+  A.z2_cap = mode == kModeSelect ? z2_elems_for<T>(n, cap, grid) : 0;
   A.rs = c->rs; A.stats_out = sout; A.eval_out = eout;
   A.proposal = nullptr;
   if (cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), stream) != cudaSuccess) return GBS_ECUDA;
@@ -1094,12 +1194,13 @@ cudaError_t select_launch_f32(const SelArgs<float>& A, int grid, cudaStream_t st
 gbs_status reserve_select(gbs_ctx* c, long long n, int elem_bytes) {
   DeviceGuard g(c->device);
   if (!g.ok) return GBS_ECUDA;
+  const long long cap = c->cfg.cap > 0 ? c->cfg.cap : std::max<long long>(n / 8, 4096);
   if (elem_bytes == 4) {
     const int grid = grid_for<float>(c, n);
-    return gbs_internal_ensure(c, (size_t)z_elems_for<float>(n, grid) * 4);
+    return gbs_internal_ensure(c, (size_t)(z_elems_for<float>(n, grid) + z2_elems_for<float>(n, cap, grid)) * 4);
   }
   const int grid = grid_for<double>(c, n);
-  return gbs_internal_ensure(c, (size_t)z_elems_for<double>(n, grid) * 8);
+  return gbs_internal_ensure(c, (size_t)(z_elems_for<double>(n, grid) + z2_elems_for<double>(n, cap, grid)) * 8);
 }
 
 }  // namespace gbs

@@ -49,6 +49,8 @@ struct SelArgs {
   unsigned long long* ghist;       // [kMaxRounds][kBins]
   T* z;                            // compaction area, regions at region_start(g)
   long long z_elems;               // its size in elements
+  T* z2;                           // the finish's second-level buffer (16-byte aligned), or nullptr
+  long long z2_cap;                // its size in elements
   gbs_run_stats* rs;               // device record of this call
   const double* proposal;          // learned bracket {a, b, valid} for pass 0, or nullptr
   gbs_array_stats* stats_out;      // kModeStats
