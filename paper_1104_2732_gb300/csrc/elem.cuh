@@ -137,6 +137,80 @@ __device__ __forceinline__ void core(float x, float a, float t_lt, float, float 
   core(x, a, t_lt, nsig, tsig, lt, le, S);
 }
 
+// Shared-memory store at a 32-bit shared-space address.
+__device__ __forceinline__ unsigned int smem_u32(const void* p) { return (unsigned int)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void st_shared(unsigned int addr, float v) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_shared(unsigned int addr, double v) {
+  asm volatile("st.shared.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ void ld_shared(unsigned int addr, float& v) {
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+}
+__device__ __forceinline__ void ld_shared(unsigned int addr, double& v) {
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+}
+
+// One element of a compacting cutting-plane pass: core() at (a, t), and an element of
+// (a, b] is stored at the shared-memory address `off`, which then moves on by one slot of
+// the lane's column (32 elements).  float32: one predicate x > a serves both the cost
+// term and the bracket test.
+__device__ __forceinline__ void core_keep(float x, float a, float t, float, float b, float nsig, float tsig,
+                                          unsigned& lt, unsigned& le, float& S, unsigned& off) {
+  asm volatile(
+      "{\n\t"
+      ".reg .pred p, q, g, r, w;\n\t"
+      ".reg .f32 d;\n\t"
+      "setp.lt.f32 p, %4, %6;\n\t"
+      "setp.le.f32 q, %4, %6;\n\t"
+      "setp.gt.f32 g, %4, %5;\n\t"
+      "and.pred r, g, p;\n\t"
+      "setp.le.and.f32 w, %4, %7, g;\n\t"
+      "fma.rn.f32 d, %4, %8, %9;\n\t"
+      "@p add.u32 %0, %0, 1;\n\t"
+      "@q add.u32 %1, %1, 1;\n\t"
+      "@r add.f32 %2, %2, d;\n\t"
+      "@w st.shared.f32 [%3], %4;\n\t"
+      "@w add.u32 %3, %3, 128;\n\t"
+      "}"
+      : "+r"(lt), "+r"(le), "+f"(S), "+r"(off)
+      : "f"(x), "f"(a), "f"(t), "f"(b), "f"(nsig), "f"(tsig)
+      : "memory");
+}
+// float64: the key comparisons of core(), the bracket test on the same key.
+__device__ __forceinline__ void core_keep(double xv, unsigned long long ka, unsigned long long kt_lt,
+                                          unsigned long long kt_le, unsigned long long kb_le, float nsig, float tsig,
+                                          unsigned& lt, unsigned& le, float& S, unsigned& off) {
+  core(xv, ka, kt_lt, kt_le, nsig, tsig, lt, le, S);
+  const unsigned long long kx = ukey_bits((uint64_t)__double_as_longlong(xv));
+  const bool w = (kx > ka) & (kx <= kb_le);
+  if (w) st_shared(off, xv);
+  off += w ? 256u : 0u;
+}
+
+// One element of a compaction pass without a cut: an element of (a, b] is stored at the
+// shared-memory address `off`, which then moves on by one slot of the lane's column.
+__device__ __forceinline__ void keep_only(float x, float a, float b, unsigned& off) {
+  asm volatile(
+      "{\n\t"
+      ".reg .pred g, w;\n\t"
+      "setp.gt.f32 g, %1, %2;\n\t"
+      "setp.le.and.f32 w, %1, %3, g;\n\t"
+      "@w st.shared.f32 [%0], %1;\n\t"
+      "@w add.u32 %0, %0, 128;\n\t"
+      "}"
+      : "+r"(off)
+      : "f"(x), "f"(a), "f"(b)
+      : "memory");
+}
+__device__ __forceinline__ void keep_only(double xv, unsigned long long ka, unsigned long long kb_le, unsigned& off) {
+  const unsigned long long kx = ukey_bits((uint64_t)__double_as_longlong(xv));
+  const bool w = (kx > ka) & (kx <= kb_le);
+  if (w) st_shared(off, xv);
+  off += w ? 256u : 0u;
+}
+
 template <typename T> __device__ __forceinline__ typename Ops<T>::C cmp_pos_inf();
 template <> __device__ __forceinline__ float cmp_pos_inf<float>() { return INFINITY; }
 template <> __device__ __forceinline__ unsigned long long cmp_pos_inf<double>() { return 0xFFF0000000000000ull; }

@@ -68,45 +68,48 @@ __device__ __forceinline__ void stream_chunks(const T* __restrict__ x, const Geo
   for (unsigned int j = 0; j < my; ++j) stream_chunk<T>(xv, bid + (rev ? my - 1 - j : j) * G, nch - 1, g.nv, f);
 }
 
-// As stream_chunks, and every element with keep(element) is appended to `zr` (counter
-// *cnt in shared memory).  A lane writes its kept elements of a chunk to its own slots of
-// the warp's shared-memory buffer `wb` as soon as they are tested (slot j of lane L at
-// wb[L + 32 j]: no bank conflicts), so the loaded vectors are dead before the warp's
-// prefix sum; the warp then copies them to `zr` with consecutive stores, each output
-// index finding its lane by a binary search over the lanes' inclusive counts.
-template <typename T, typename Fn, typename Keep>
+// As stream_chunks, and the elements the pass keeps are appended to `zr` (counter *cnt
+// in shared memory).  fk(v, off) counts v and, when it keeps v, stores it at the shared
+// address off and advances off by one slot: slot j of lane L is wb[L + 32 j] (no bank
+// conflicts), so the loaded vectors are dead before the warp's prefix sum; each lane then
+// copies its kept elements of the chunk to their places after those of the lower lanes.
+template <typename T, typename FK>
 __device__ __forceinline__ void stream_chunks_compact(const T* __restrict__ x, const Geometry<T>& g, bool rev,
-                                                      Fn& f, Keep& keep, T* __restrict__ zr,
-                                                      unsigned int* cnt, T* wb) {
+                                                      FK& fk, T* __restrict__ zr, unsigned int* cnt, T* wb) {
   using V = typename Ops<T>::V;
   constexpr int kVec = Ops<T>::kVec;
+  constexpr unsigned int kSlot = 32u * sizeof(T);
   const int lane = threadIdx.x & 31;
+  const unsigned int off0 = smem_u32(wb + lane);
   const V* xv = reinterpret_cast<const V*>(x + g.head);
   const unsigned int G = gridDim.x, bid = blockIdx.x;
   const unsigned int nch = (unsigned int)chunk_count(g.nv);
   const unsigned int my = bid < nch ? (nch - 1 - bid) / G + 1 : 0;
-  for (unsigned int j = 0; j < my; ++j) {
+  // the loads of chunk j + 1 are issued before chunk j's prefix sum and copy-out, so that
+  // they are in flight during that serial part
+  V r[kVPT];
+  auto load = [&](unsigned int j) {
     const unsigned int c = bid + (rev ? my - 1 - j : j) * G;
     const V* p = xv + (long long)c * kChunkVecs + threadIdx.x;
     const long long lim = g.nv - (long long)c * kChunkVecs - threadIdx.x;
-    V r[kVPT];
 #pragma unroll
     for (int u = 0; u < kVPT; ++u)
       if ((long long)u * kThreads < lim) r[u] = load_stream(p + u * kThreads);
-    unsigned int k = 0;
+  };
+  if (my) load(0);
+  for (unsigned int j = 0; j < my; ++j) {
+    const unsigned int c = bid + (rev ? my - 1 - j : j) * G;
+    const long long lim = g.nv - (long long)c * kChunkVecs - threadIdx.x;
+    unsigned int off = off0;
 #pragma unroll
     for (int u = 0; u < kVPT; ++u) {
       if ((long long)u * kThreads < lim) {
-        Ops<T>::each(r[u], f);
 #pragma unroll
-        for (int e = 0; e < kVec; ++e) {
-          const T v = Ops<T>::get(r[u], e);
-          const bool kk = keep(v);
-          if (kk) wb[lane + 32 * k] = v;
-          k += kk;
-        }
+        for (int e = 0; e < kVec; ++e) fk(Ops<T>::get(r[u], e), off);
       }
     }
+    if (j + 1 < my) load(j + 1);
+    const unsigned int k = (off - off0) / kSlot;
     unsigned int incl = k;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -118,19 +121,17 @@ __device__ __forceinline__ void stream_chunks_compact(const T* __restrict__ x, c
       unsigned int b0 = 0;
       if (lane == 31) b0 = atomicAdd(cnt, total);
       b0 = __shfl_sync(0xffffffffu, b0, 31);
-      __syncwarp();
-      for (unsigned int i0 = 0; i0 < total; i0 += 32) {
-        const unsigned int i = i0 + lane;
-        int L = 0;                       // lanes whose inclusive count is <= i
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const unsigned int v = __shfl_sync(0xffffffffu, incl, L + step - 1);
-          if (v <= i) L += step;
+      // each lane copies its own slots (so no lane reads another's): its q-th kept element
+      // goes to b0 + (kept by lower lanes) + q
+      T* dst = zr + b0 + (incl - k);
+      const unsigned int maxk = __reduce_max_sync(0xffffffffu, k);
+      for (unsigned int q = 0; q < maxk; ++q) {
+        if (q < k) {
+          T v;
+          ld_shared(off0 + q * kSlot, v);
+          dst[q] = v;
         }
-        const unsigned int exL = __shfl_sync(0xffffffffu, incl, L) - __shfl_sync(0xffffffffu, k, L);
-        if (i < total) zr[b0 + i] = wb[L + 32 * (i - exL)];
       }
-      __syncwarp();
     }
   }
 }
@@ -201,7 +202,10 @@ __device__ __forceinline__ Thr<T> thresholds(T a, T t, T b) {
 }
 
 // One streaming pass over x at the iterate t (Algorithm 1, step 1.2).  FIRST also counts
-// #(x <= a) and #(x < b); COMPACT also appends the elements of (a, b] to region `zr`.
+// #(x <= a) and #(x < b); COMPACT also appends the elements of (a, b] to region `zr`, and
+// a compacting pass after the first only does that (no cut at t: the finish ranks the
+// compacted elements of (a, b] exactly, so a last cut would only have shrunk the range
+// whose elements it has to read anyway).
 // Kept out of line so that its registers are allocated apart from the kernel's control.
 template <typename T, bool FIRST, bool COMPACT>
 __device__ __noinline__ bool cut_pass(const T* __restrict__ x, const Geometry<T>& geo, bool rev, Thr<T> h,
@@ -220,15 +224,26 @@ __device__ __noinline__ bool cut_pass(const T* __restrict__ x, const Geometry<T>
     }
   };
   if (COMPACT) {
-    auto keep = [&](T v) { const C cv = CmpOf<T>::of(v); return (cv > h.a_le) & (cv <= h.b_le); };
+    auto fk = [&](T v, unsigned int& off) {
+      if (FIRST) {
+        core_keep(v, h.a_le, h.t_lt, h.t_le, h.b_le, nsig, tsig, lt, le, S, off);
+        const C cv = CmpOf<T>::of(v);
+        xa += (cv <= h.a_le);
+        xb += (cv < h.b_lt);
+      } else {
+        keep_only(v, h.a_le, h.b_le, off);
+      }
+    };
     if ((long long)blockIdx.x * kThreads + threadIdx.x < geo.head + (geo.n - geo.tail0)) {
-      auto fk = [&](T v) {
-        f(v);
-        if (keep(v)) zr[atomicAdd(s_cnt, 1u)] = v;
+      const unsigned int o0 = smem_u32(wb + (threadIdx.x & 31));
+      auto fe = [&](T v) {   // the scalar head and tail: kept elements go straight to zr
+        unsigned int o = o0;
+        fk(v, o);
+        if (o != o0) zr[atomicAdd(s_cnt, 1u)] = v;
       };
-      stream_edges(x, geo, fk);
+      stream_edges(x, geo, fe);
     }
-    stream_chunks_compact(x, geo, rev, f, keep, zr, s_cnt, wb);
+    stream_chunks_compact(x, geo, rev, fk, zr, s_cnt, wb);
   } else {
     stream_edges(x, geo, f);
     stream_chunks(x, geo, rev, f);
@@ -297,13 +312,19 @@ __device__ __noinline__ bool stats_pass_learned(const T* __restrict__ x, const G
   };
   auto keep = [&](T v) { const C cv = CmpOf<T>::of(v); return !Ops<T>::is_nan(v) & (cv > ca) & (cv <= cb_le); };
   if ((long long)blockIdx.x * kThreads + threadIdx.x < geo.head + (geo.n - geo.tail0)) {
-    auto fk = [&](T v) {
+    auto fe = [&](T v) {
       f(v);
       if (keep(v)) zr[atomicAdd(s_cnt, 1u)] = v;
     };
-    stream_edges(x, geo, fk);
+    stream_edges(x, geo, fe);
   }
-  stream_chunks_compact(x, geo, false, f, keep, zr, s_cnt, wb);
+  auto fk = [&](T v, unsigned int& off) {
+    f(v);
+    const bool w = keep(v);
+    if (w) st_shared(off, v);
+    off += w ? 32u * (unsigned int)sizeof(T) : 0u;
+  };
+  stream_chunks_compact(x, geo, false, fk, zr, s_cnt, wb);
   out.mn = cmp_pos_inf<T>(); out.mx = cmp_neg_inf<T>();
   out.nnan = nnan; out.nneg = 0; out.npos = 0; out.seen = nnan; out.sum = 0.f;
   pa.la = la; pa.lblt = lblt;
@@ -784,7 +805,12 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
         }
         if (resolved && bid == 0 && br.it < kMaxIt) s_pops[br.it] = 0;
       }
-      if (!resolved) {
+      if (!resolved && br.compact && !br.first) {
+        // the compaction pass alone: the bracket stays, the finish ranks its elements
+        const long long pop = nb.cle_b - nb.cle_a;
+        if (bid == 0 && br.it < kMaxIt) { s_pops[br.it] = pop; s_iter[br.it] = (double)NAN; }
+        nb.phase = ((long long)tt.c_reg == pop) ? 2 : 4;
+      } else if (!resolved) {
         const long long pop = nb.cle_b - nb.cle_a;
         if (clt < k && k <= cle) {
           nb.phase = 1; nb.result = br.t; nb.how = GBS_HOW_HIT; nb.clt_res = clt;
