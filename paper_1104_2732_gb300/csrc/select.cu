@@ -73,9 +73,11 @@ __device__ __forceinline__ void stream_chunks(const T* __restrict__ x, const Geo
 // address off and advances off by one slot: slot j of lane L is wb[L + 32 j] (no bank
 // conflicts), so the loaded vectors are dead before the warp's prefix sum; each lane then
 // copies its kept elements of the chunk to their places after those of the lower lanes.
-template <typename T, typename FK>
+// on_kept(v, act) follows each copy in every lane of the warp (act: the lane copied v).
+template <typename T, typename FK, typename OnKept>
 __device__ __forceinline__ void stream_chunks_compact(const T* __restrict__ x, const Geometry<T>& g, bool rev,
-                                                      FK& fk, T* __restrict__ zr, unsigned int* cnt, T* wb) {
+                                                      FK& fk, T* __restrict__ zr, unsigned int* cnt, T* wb,
+                                                      OnKept& on_kept) {
   using V = typename Ops<T>::V;
   constexpr int kVec = Ops<T>::kVec;
   constexpr unsigned int kSlot = 32u * sizeof(T);
@@ -126,11 +128,13 @@ __device__ __forceinline__ void stream_chunks_compact(const T* __restrict__ x, c
       T* dst = zr + b0 + (incl - k);
       const unsigned int maxk = __reduce_max_sync(0xffffffffu, k);
       for (unsigned int q = 0; q < maxk; ++q) {
-        if (q < k) {
-          T v;
+        const bool act = q < k;
+        T v = T(0);
+        if (act) {
           ld_shared(off0 + q * kSlot, v);
           dst[q] = v;
         }
+        on_kept(v, act);
       }
     }
   }
@@ -201,16 +205,52 @@ __device__ __forceinline__ Thr<T> thresholds(T a, T t, T b) {
   return h;
 }
 
+// The first radix round of the finish over the elements of (a, b]: their keys lie above
+// k_lo and at most k_hi (a zero end takes the key of +0, which makes the key test the IEEE
+// one), the leading `known` bits where ukey(a) + 1 and ukey(b) agree form the prefix, and
+// the digit is the next kDigitBits (fewer at the end of the key).
+template <typename T>
+struct FinDigit {
+  using U = typename KeyOf<T>::U;
+  U k_lo, k_hi, prefix;
+  int known, sh;
+  unsigned int dmask;
+  bool exact;   // no zero end: every element of (a, b] passes the key and prefix tests
+};
+template <typename T>
+__device__ __forceinline__ FinDigit<T> fin_digit0(T a, T b) {
+  using U = typename KeyOf<T>::U;
+  constexpr int W = KeyOf<T>::kBitsW;
+  FinDigit<T> f;
+  const U lo = ukey(a) + 1, hi = ukey(b);
+  const U diff = lo ^ hi;
+  const int known = diff == 0 ? W : (W == 32 ? __clz((unsigned int)diff) : __clzll((unsigned long long)diff));
+  f.known = known;
+  f.prefix = known == 0 ? U(0) : (known == W ? hi : (U)(hi >> (W - known)));
+  f.k_lo = ukey(a == T(0) ? T(0) : a);
+  f.k_hi = ukey(b == T(0) ? T(0) : b);
+  const int nbits = (W - known) < kDigitBits ? (W - known) : kDigitBits;
+  f.sh = W - known - nbits;
+  f.dmask = (1u << nbits) - 1u;
+  f.exact = a != T(0) && b != T(0);
+  return f;
+}
+
 // One streaming pass over x at the iterate t (Algorithm 1, step 1.2).  FIRST also counts
 // #(x <= a) and #(x < b); COMPACT also appends the elements of (a, b] to region `zr`, and
 // a compacting pass after the first only does that (no cut at t: the finish ranks the
 // compacted elements of (a, b] exactly, so a last cut would only have shrunk the range
 // whose elements it has to read anyway).
 // Kept out of line so that its registers are allocated apart from the kernel's control.
+// A compacting pass after the first also forms the finish's first-round histogram of the
+// elements it keeps (digits by dg, counts in hist), so that the finish starts at its digit
+// search.
 template <typename T, bool FIRST, bool COMPACT>
 __device__ __noinline__ bool cut_pass(const T* __restrict__ x, const Geometry<T>& geo, bool rev, Thr<T> h,
                                       float nsig, float tsig, T* __restrict__ zr, unsigned int* s_cnt,
-                                      T* wb, PassAcc& acc) {
+                                      T* wb, unsigned int* hist, FinDigit<T> dg, PassAcc& acc) {
+  using U = typename KeyOf<T>::U;
+  constexpr int W = KeyOf<T>::kBitsW;
   using C = typename Ops<T>::C;
   using V = typename Ops<T>::V;
   unsigned int lt = 0, le = 0, xa = 0, xb = 0;
@@ -234,16 +274,37 @@ __device__ __noinline__ bool cut_pass(const T* __restrict__ x, const Geometry<T>
         keep_only(v, h.a_le, h.b_le, off);
       }
     };
+    // the histogram of the kept elements (act: the lane holds one).  Per-lane shared-memory
+    // adds: warp-wide aggregation (ballots over the lanes' digits) costs more here than
+    // the conflicts of tied values it would save.
+    auto on_kept = [&](T v, bool act) {
+      if (!FIRST && act) {
+        const U key = ukey(v);
+        if (dg.exact || (key > dg.k_lo && key <= dg.k_hi &&
+                         (dg.known == 0 || (U)(key >> (W - dg.known)) == dg.prefix)))
+          atomicAdd(&hist[(unsigned int)(key >> dg.sh) & dg.dmask], 1u);
+      }
+    };
+    auto hist_one = [&](T v) {   // one element outside the warp-wide copy-out
+      if (!FIRST) {
+        const U key = ukey(v);
+        if (key > dg.k_lo && key <= dg.k_hi && (dg.known == 0 || (U)(key >> (W - dg.known)) == dg.prefix))
+          atomicAdd(&hist[(unsigned int)(key >> dg.sh) & dg.dmask], 1u);
+      }
+    };
     if ((long long)blockIdx.x * kThreads + threadIdx.x < geo.head + (geo.n - geo.tail0)) {
       const unsigned int o0 = smem_u32(wb + (threadIdx.x & 31));
       auto fe = [&](T v) {   // the scalar head and tail: kept elements go straight to zr
         unsigned int o = o0;
         fk(v, o);
-        if (o != o0) zr[atomicAdd(s_cnt, 1u)] = v;
+        if (o != o0) {
+          zr[atomicAdd(s_cnt, 1u)] = v;
+          hist_one(v);
+        }
       };
       stream_edges(x, geo, fe);
     }
-    stream_chunks_compact(x, geo, rev, fk, zr, s_cnt, wb);
+    stream_chunks_compact(x, geo, rev, fk, zr, s_cnt, wb, on_kept);
   } else {
     stream_edges(x, geo, f);
     stream_chunks(x, geo, rev, f);
@@ -324,12 +385,18 @@ __device__ __noinline__ bool stats_pass_learned(const T* __restrict__ x, const G
     if (w) st_shared(off, v);
     off += w ? 32u * (unsigned int)sizeof(T) : 0u;
   };
-  stream_chunks_compact(x, geo, false, fk, zr, s_cnt, wb);
+  auto no_hist = [](T, bool) {};
+  stream_chunks_compact(x, geo, false, fk, zr, s_cnt, wb, no_hist);
   out.mn = cmp_pos_inf<T>(); out.mx = cmp_neg_inf<T>();
   out.nnan = nnan; out.nneg = 0; out.npos = 0; out.seen = nnan; out.sum = 0.f;
   pa.la = la; pa.lblt = lblt;
   return true;
 }
+
+// The finish's digit histogram: dynamic shared memory of kHistBytes (apart from the
+// compaction staging buffers, since the compacting pass fills it).
+constexpr int kHistBytes = 4 * kBins;
+extern __shared__ __align__(16) unsigned int g_hist_smem[];
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
@@ -364,10 +431,9 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
   // the finish's region offsets and digit histogram, and before them the warps'
   // compaction staging buffers
   constexpr int kOffBytes = 8 * (kMaxGrid + 1);
-  constexpr int kFinBytes = kOffBytes + 4 * kBins;
-  __shared__ __align__(16) unsigned char s_big[kChunkBytes > kFinBytes ? kChunkBytes : kFinBytes];
+  __shared__ __align__(16) unsigned char s_big[kChunkBytes > kOffBytes ? kChunkBytes : kOffBytes];
   unsigned long long* s_off = reinterpret_cast<unsigned long long*>(s_big);
-  unsigned int* const s_hist = reinterpret_cast<unsigned int*>(s_big + kOffBytes);
+  unsigned int* const s_hist = g_hist_smem;   // the finish's digit histogram (dynamic, kHistBytes)
   T* const s_wb = reinterpret_cast<T*>(s_big) + (tid >> 5) * (kChunkBytes / sizeof(T) / kWarps);
 
   const Geometry<T> geo(A.x, n);
@@ -460,6 +526,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
   // With a proposed bracket, pass 0 is first the lean check of the proposal; the plain
   // pass 0 follows only when an end fails its check (the same decision in every CTA).
   bool lean = prop_ok;
+  bool hist0 = false;   // the compacting pass formed the finish's first-round histogram
   __shared__ unsigned long long s_prop[4];   // #(x <= a), #(x < b), #(x <= b), #compacted
   for (;;) {
     {
@@ -728,23 +795,33 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     const float tsig = Ops<T>::img(s_br.t) * s_br.sigma;
     const int first = s_br.first, compact = s_br.compact;
     const bool rev = (pass & 1) == 0;   // pass 0 ran forward
+    // a compacting pass after the first also forms the finish's first-round histogram
+    const FinDigit<T> dg = fin_digit0(s_br.a, s_br.b);
+    const bool fill = compact && !first;
     if (tid == 0) s_zcnt = 0;
+    if (fill)
+      for (int i = tid; i < kBins; i += kThreads) s_hist[i] = 0;
     __syncthreads();
     PassAcc acc;
     T* zr = A.z + region_start(bid, nch, G, Ops<T>::kVec);
     bool ok;
     if (first) {
-      if (compact) ok = cut_pass<T, true, true>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, acc);
-      else ok = cut_pass<T, true, false>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, acc);
+      if (compact) ok = cut_pass<T, true, true>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, s_hist, dg, acc);
+      else ok = cut_pass<T, true, false>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, s_hist, dg, acc);
     } else {
-      if (compact) ok = cut_pass<T, false, true>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, acc);
-      else ok = cut_pass<T, false, false>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, acc);
+      if (compact) ok = cut_pass<T, false, true>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, s_hist, dg, acc);
+      else ok = cut_pass<T, false, false>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, s_hist, dg, acc);
     }
     if (!ok) return;
     if (bid == 0 && tid == 0 && pass < kMaxIt) s_tstream[pass] = globaltimer();
     const unsigned int lt = acc.lt, le = acc.le, xa = acc.xa, xb = acc.xb;
     const float S = acc.S;
     __syncthreads();   // every append to this CTA's region is done
+    if (fill && dg.known < W) {   // the histogram of round 0 (visible after the barrier)
+      for (int i = tid; i < kBins; i += kThreads)
+        if (s_hist[i]) atomicAdd(&A.ghist[i], (unsigned long long)s_hist[i]);
+      hist0 = true;
+    }
     Sum6 v6;
     v6.u[0] = lt; v6.u[1] = le; v6.u[2] = xa; v6.u[3] = xb;
     v6.u[4] = (compact && tid == 0) ? s_zcnt : 0u;   // the CTA's count, once
@@ -916,6 +993,8 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
       const unsigned int dmask = (1u << nbits) - 1u;
       const bool copy = use_z2 && rounds == 1 && known + nbits < W;   // a later round will read z2
       const bool from_z2 = use_z2 && rounds >= 2;
+      const bool pre = hist0 && rounds == 0;   // the compacting pass formed this round's histogram
+      if (!pre) {
       for (int i = tid; i < kBins; i += kThreads) s_hist[i] = 0;
       __syncthreads();
       // One element a lane, called by every lane of the warp together: the digit of an
@@ -928,19 +1007,16 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
         const U key = ukey(v);
         const bool ok = valid && (key > k_lo) && (key <= k_hi) && (known == 0 || (U)(key >> (W - known)) == prefix);
         const unsigned int d = (unsigned int)(key >> sh) & dmask;
-        if (ok) {
-          if (d == hot) {
-            ++hcnt;
-          } else {
-            atomicAdd(&s_hist[d], 1u);
-            if (d == last) {
-              if (hcnt) atomicAdd(&s_hist[hot], hcnt);
-              hot = d;
-              hcnt = 0;
-            }
-            last = d;
-          }
-        }
+        // branch-free (lanes of a warp that disagree would otherwise serialise both paths)
+        const bool h = ok && d == hot;
+        const bool at = ok && !h;
+        const bool sw = at && d == last;
+        hcnt += h ? 1u : 0u;
+        if (at) atomicAdd(&s_hist[d], 1u);
+        if (sw && hcnt) atomicAdd(&s_hist[hot], hcnt);
+        hot = sw ? d : hot;
+        hcnt = sw ? 0u : hcnt;
+        last = at ? d : last;
         if (copy) {
           const unsigned int act = __ballot_sync(0xffffffffu, ok);
           if (act) {
@@ -1010,6 +1086,7 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
         if (s_hist[i]) atomicAdd(&A.ghist[rounds * kBins + i], (unsigned long long)s_hist[i]);
       if (!grid_sync(A.ctrl, G)) return;
       stamp();
+      }
       {   // the CTA finds the digit holding rank s_rank: kBins / kThreads bins a thread
         constexpr int kPer = kBins / kThreads;
         unsigned long long h[kPer];
@@ -1101,7 +1178,9 @@ template <typename T> constexpr int vec_of() { return 16 / (int)sizeof(T); }
 template <typename T>
 int grid_for(gbs_ctx* c, long long n) {
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, select_kernel<T>, kThreads, 0) != cudaSuccess) {
+  if (cudaFuncSetAttribute(select_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHistBytes) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, select_kernel<T>, kThreads, kHistBytes) != cudaSuccess) {
     cudaGetLastError();
     occ = 1;
   }
@@ -1180,7 +1259,7 @@ gbs_status launch_select(gbs_ctx* c, const T* x, long long n, long long k, T* ou
   }
   void* args[] = {&A};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)select_kernel<T>, dim3(grid), dim3(kThreads), args,
-                                              0, stream);
+                                              kHistBytes, stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return GBS_ECUDA;
@@ -1204,7 +1283,10 @@ long long select_z_elems_f32(long long n, int grid) { return z_elems_for<float>(
 float select_stats_sigma_f32(long long n, int grid) { return stats_sigma<float>(n, grid); }
 int select_occupancy_f32() {
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, select_kernel<float>, kThreads, 0) != cudaSuccess) {
+  if (cudaFuncSetAttribute(select_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHistBytes) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, select_kernel<float>, kThreads, kHistBytes) !=
+          cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
@@ -1213,8 +1295,11 @@ int select_occupancy_f32() {
 cudaError_t select_launch_f32(const SelArgs<float>& A, int grid, cudaStream_t stream) {
   SelArgs<float> a = A;
   void* args[] = {&a};
+  const cudaError_t e =
+      cudaFuncSetAttribute(select_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHistBytes);
+  if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel((const void*)select_kernel<float>, dim3(grid), dim3(kThreads), args,
-                                     0, stream);
+                                     kHistBytes, stream);
 }
 
 gbs_status reserve_select(gbs_ctx* c, long long n, int elem_bytes) {
