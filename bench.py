@@ -13,8 +13,8 @@ e2e         the same through the public API with the array in pinned HOST memory
 roofline    the persistent select kernel: algorithmic bytes (passes x n x 4 + the finish's
             bytes: the compacted bracket written once and read once) /
             its CUDA-event duration, against the measured HBM copy bandwidth
-cpu_baseline  the CPU oracle (numpy introselect on totalOrder keys, one thread) on the
-            same array and ranks
+cpu_baseline  the CPU oracle (numpy introselect on totalOrder keys) on three steps of
+            the same workload, one selection a task on every host core
 
 ``--impl reference`` times that oracle as the reference arm.  Under torchrun (N > 1)
 every rank runs an independent replica of the workload (the single-array path has no
@@ -167,43 +167,51 @@ def select_traffic():
     return int(m1.group(1)), "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over the 5 ranks"
 
 
-def cpu_oracle_time(x, ks):
-    """The CPU oracle as it stands (oracle.select.select_kth, single-threaded numpy)."""
-    from oracle import select as osel
-    t0 = time.perf_counter()
-    for k in ks:
-        osel.select_kth(x, k)
-    return time.perf_counter() - t0
+def cpu_oracle_steps(x, ks, steps, warm_steps=0):
+    """The CPU oracle as it stands (oracle.select.select_kth, numpy) on `steps` steps of
+    the workload -- every rank of ks on the whole array x -- one selection a task on every
+    host core (x shared with the workers)."""
+    tasks = [int(k) for _ in range(steps) for k in ks]
+    warm = [int(k) for _ in range(max(1, warm_steps)) for k in ks]
+    with SharedArray(x) as sh:
+        wall, cores = oracle_pool_time(_oracle_rank_task, tasks, init=_shm_worker_init, initargs=sh.initargs,
+                                       warm=warm)
+    return {"value": len(tasks) * x.size / wall / 1e9, "unit": "Gelem/s", "cores": cores, "kind": "oracle",
+            "sample": f"{steps} steps of the workload (the {len(ks)} ranks on the whole array), "
+                      "one selection a task", "seconds": wall, "ms_per_step": 1e3 * wall / steps}
+
+
+HEADLINE_METRIC = "k-th select Gelem/s (n=2^27 float32)"
+
+
+def headline_config(n, ks, world):
+    """The `config` of the headline line (both arms)."""
+    return {"workload": f"single-array k-th select, n=2^27 float32 {FAMILY} "
+                        "(+5% duplicates, 10 +-inf), 5 ranks per step",
+            "n": n, "ranks": ks, "parallelism": f"replicas x{world}",
+            "l2": "input larger than L2 (no flush needed)"}
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the CPU oracle on the host cores, on a bounded sample of the workload.
-
-    Each step selects the median of one contiguous slice of the 2^27 array; the slice
-    length is chosen so that the K + W oracle calls take about a minute in total (the
-    full array on every step when K is small)."""
-    import numpy as np
+    """Reference arm: the CPU oracle as it stands on the host cores, on the headline
+    workload itself -- each step selects the five ranks on the whole 2^27 array, one
+    selection a task of a process pool over every host core (W steps untimed, then K
+    timed; the steps overlap on the cores, so ms_per_step is the wall time / K)."""
     import synth
     n = 1 << N_LOG2
+    ks = ranks_for(n)
     x = synth.heavy_mixture(FAMILY, n, seed=SEED)
-    budget_elems = 1.6e9          # ~1 min of the oracle at ~25-30 Melem/s
-    m = int(min(n, max(1 << 20, budget_elems / max(1, args.steps + args.warmup))))
-    slices = [x[(i * m) % (n - m + 1):(i * m) % (n - m + 1) + m] for i in range(args.steps + args.warmup)]
-    for i in range(args.warmup):
-        cpu_oracle_time(slices[i], [(m + 1) // 2])
-    times = [cpu_oracle_time(slices[args.warmup + i], [(m + 1) // 2]) for i in range(args.steps)]
-    t = sum(times)
-    value = args.steps * m / t / 1e9
+    cpu = cpu_oracle_steps(x, ks, steps=args.steps, warm_steps=args.warmup)
+    value = cpu["value"]
     line = {
-        "impl": "reference", "metric": "k-th select Gelem/s (n=2^27 float32)", "value": value,
+        "impl": "reference", "metric": HEADLINE_METRIC, "value": value,
         "unit": "Gelem/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": cpu["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"single-array k-th select, n=2^27 float32 {FAMILY} (+5% dups, 10 inf)",
-                   "ranks": "median rank of a slice per step", "slice_elements": m,
-                   "l2": "input larger than L2"},
-        "cpu_baseline": {"value": value, "unit": "Gelem/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} medians of contiguous {m}-element slices of the 2^27 array"},
+        "config": headline_config(n, ks, world),
+        "cpu_baseline": {"value": value, "unit": "Gelem/s", "cores": cpu["cores"], "kind": "oracle",
+                         "sample": f"{args.steps} steps of the workload itself: the 5 ranks on the whole "
+                                   "2^27 array, one selection a task"},
         "e2e": {"value": value, "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     if rank == 0:
@@ -283,18 +291,15 @@ def bench_segmented(gbs, ctx, torch, np, args):
                    "mean_passes_large_segments": float(lpasses[big].mean()) if big.any() else None,
                    "identical_to_plain_start": bool(torch.equal(out.view(torch.int32), outl.view(torch.int32))),
                    "speedup_vs_plain_start": ms / lms_}
-    # CPU oracle (as it stands, 1 thread) on every 32nd segment, scaled to the batch
-    from oracle import select as osel
-    sample = range(0, S, 32)
-    t0 = time.perf_counter()
-    elems = 0
-    for s_ in sample:
-        seg = x_host[int(off[s_]):int(off[s_ + 1])]
-        osel.select_kth(seg, (seg.size + 1) // 2)
-        elems += seg.size
-    cpu_s = time.perf_counter() - t0
-    cpu = {"value": len(sample) / cpu_s, "unit": "selections/s", "gelem_s": elems / cpu_s / 1e9, "cores": 1,
-           "kind": "oracle", "sample": f"medians of {len(sample)} of the {S} segments (every 32nd)"}
+    # CPU oracle (as it stands) on the whole batch, one segment a task on every host core
+    cpu = None
+    if not args.no_cpu:
+        tasks = [(int(off[i]), int(off[i + 1])) for i in range(S)]
+        with SharedArray(x_host) as sh:
+            cpu_s, cores = oracle_pool_time(_oracle_segment_task, tasks, init=_shm_worker_init,
+                                            initargs=sh.initargs, warm=tasks[:64])
+        cpu = {"value": S / cpu_s, "unit": "selections/s", "gelem_s": total / cpu_s / 1e9, "cores": cores,
+               "kind": "oracle", "sample": f"the whole batch: medians of all {S} segments, one a task"}
     return {
         "workload": f"{S} float32 normal arrays, sizes log-uniform [1e3, 1e6], total {total} elements, medians",
         "metric": "selections/s", "value": S / (ms * 1e-3), "gelem_s": total / (ms * 1e-3) / 1e9,
@@ -360,11 +365,19 @@ def bench_lms(gbs, ctx, torch, np, args):
     forms = {"fused": (lms_f, lts_f), "materialised": (lms_m, lts_m), "plain": (lms_p, lts_p)}
     forms = {kk: (a.cpu().numpy(), b.cpu().numpy()) for kk, (a, b) in forms.items()}
     rng = np.random.default_rng(8)
-    sample = rng.choice(C, 8, replace=False)
+    n_sample = 8 if args.no_cpu else 64
+    sample = rng.choice(C, n_sample, replace=False)
     err = {kk: [0.0, 0.0] for kk in forms}
-    t0 = time.perf_counter()
-    oracle_vals = [oreg.lms_lts(X, y, th[c:c + 1].T, k, h) for c in sample]
-    cpu_s = time.perf_counter() - t0
+    if args.no_cpu:
+        t0 = time.perf_counter()
+        oracle_vals = [_lms_oracle_candidate_on(X, y, th, c, k, h) for c in sample]
+        cpu_s, cores = time.perf_counter() - t0, 1
+    else:
+        # the float64 oracle on every host core, one candidate a task
+        cpu_s, cores = oracle_pool_time(_lms_oracle_task, [int(c) for c in sample], init=_lms_worker_init,
+                                        initargs=(n, p, C, k, h))
+        oracle_vals = [_lms_oracle_candidate_on(X, y, th, c, k, h) for c in sample[:8]]
+        sample = sample[:8]
     for c, (wl, wt) in zip(sample, oracle_vals):
         for name, (l, t) in forms.items():
             err[name][0] = max(err[name][0], abs(l[c] / wl[0] - 1))
@@ -384,8 +397,8 @@ def bench_lms(gbs, ctx, torch, np, args):
         "residual_kernel": {"ms": res_ms, "bytes_written": C * n * 4,
                             "gbs": C * n * 4 / (res_ms * 1e-3) / 1e9,
                             "hbm_frac": C * n * 4 / (res_ms * 1e-3) / 1e9 / hbm, "peak_kind": f"{kind} hbm_gbs"},
-        "cpu_baseline": {"value": len(sample) / cpu_s, "unit": "candidates/s", "cores": 1, "kind": "oracle",
-                         "sample": f"float64 LMS and LTS of {len(sample)} of the {C} candidates"},
+        "cpu_baseline": {"value": n_sample / cpu_s, "unit": "candidates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"float64 LMS and LTS of {n_sample} of the {C} candidates, one a task"},
         "search": {"ms": search_ms, "n_refine": 10, "max_steps": 20,
                    "lms_value": float(srch["lms_value"][0]), "lts_value": float(srch["lts_value"][0]),
                    "lts_start_index": int(srch["lts_index"][0]),
@@ -395,6 +408,30 @@ def bench_lms(gbs, ctx, torch, np, args):
             "lms": float(np.max(np.abs(forms["fused"][0] / forms["materialised"][0] - 1))),
             "lts": float(np.max(np.abs(forms["fused"][1] / forms["materialised"][1] - 1)))},
     }
+
+
+_LMS = None
+
+
+def _lms_oracle_candidate_on(X, y, th, c, k, h):
+    """The float64 oracle's (LMS, LTS) objectives of candidate c."""
+    from oracle import regression as oreg
+    return oreg.lms_lts(X, y, th[c:c + 1].T, k, h)
+
+
+def _lms_worker_init(n, p, C, k, h):
+    """Pool worker start-up: the regression problem and its candidates, regenerated."""
+    global _LMS
+    import numpy as np
+    import synth
+    X, y, _ = synth.regression(n, p, 6)
+    th = np.ascontiguousarray(synth.elemental_thetas(X, y, C, 7).T)
+    _LMS = (X, y, th, k, h)
+
+
+def _lms_oracle_task(c):
+    X, y, th, k, h = _LMS
+    return _lms_oracle_candidate_on(X, y, th, c, k, h)
 
 
 KNN_N, KNN_P, KNN_M, KNN_K, KNN_C, KNN_SEED = 1 << 20, 8, 4096, 256, 16, 350
@@ -422,18 +459,67 @@ def _knn_oracle_queries(idx):
     return len(idx)
 
 
-def oracle_pool_time(fn, tasks, init=None):
+def oracle_pool_time(fn, tasks, init=None, initargs=(), warm=None):
     """Wall time of fn over tasks on every host core (a spawn-started process pool, so no
     process forks after CUDA is initialised; `init` runs in each worker before the timed
-    region) and the cores used."""
+    region, and `warm` -- by default one task a worker -- runs there untimed) and the
+    cores used."""
     import multiprocessing as mp
     cores = min(len(tasks), os.cpu_count() or 1)
-    with mp.get_context("spawn").Pool(cores, initializer=init) as pool:
-        pool.map(fn, tasks[:cores], chunksize=1)   # start-up outside the timed region
+    with mp.get_context("spawn").Pool(cores, initializer=init, initargs=initargs) as pool:
+        pool.map(fn, tasks[:cores] if warm is None else warm, chunksize=1)   # start-up, untimed
         t0 = time.perf_counter()
         pool.map(fn, tasks, chunksize=1)
         wall = time.perf_counter() - t0
     return wall, cores
+
+
+_SHM = None
+
+
+def _shm_worker_init(name, shape, dtype):
+    """Pool worker start-up: attach the shared array (created by the parent, which alone
+    unlinks it)."""
+    global _SHM
+    import numpy as np
+    from multiprocessing import shared_memory
+    h = shared_memory.SharedMemory(name=name)
+    _SHM = (h, np.ndarray(shape, dtype=np.dtype(dtype), buffer=h.buf))
+
+
+def _oracle_rank_task(k):
+    """One oracle selection of rank k on the shared array (one task of the pool)."""
+    from oracle import select as osel
+    osel.select_kth(_SHM[1], k)
+    return int(_SHM[1].size)
+
+
+def _oracle_segment_task(bounds):
+    """The oracle's median of one segment [s, e) of the shared array."""
+    from oracle import select as osel
+    s, e = bounds
+    osel.select_kth(_SHM[1][s:e], (e - s + 1) // 2)
+    return e - s
+
+
+class SharedArray:
+    """A host array in shared memory for the spawn pool's workers (context manager)."""
+
+    def __init__(self, x):
+        import numpy as np
+        from multiprocessing import shared_memory
+        self.h = shared_memory.SharedMemory(create=True, size=max(1, x.nbytes))
+        self.a = np.ndarray(x.shape, dtype=x.dtype, buffer=self.h.buf)
+        self.a[...] = x
+        self.initargs = (self.h.name, x.shape, x.dtype.str)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        del self.a
+        self.h.close()
+        self.h.unlink()
 
 
 def bench_knn(gbs, ctx, torch, np, args):
@@ -920,16 +1006,12 @@ def main():
     # ---------------- CPU oracle baseline (rank 0 only) ----------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        sample = ks[1:4]
-        t = cpu_oracle_time(x_host, sample)
-        cpu = {"value": len(sample) * n / t / 1e9, "unit": "Gelem/s", "cores": 1, "kind": "oracle",
-               "sample": "ranks n/100, (n+1)/2, 99n/100 on the full 2^27 array, one pass each",
-               "seconds": t}
+        cpu = cpu_oracle_steps(x_host, ks, steps=3)
 
     if rank == 0:
         sel_ms = [sum(launch_ms[i::len(ks)]) / args.steps for i in range(len(ks))]
         line = {
-            "metric": "k-th select Gelem/s (n=2^27 float32)",
+            "metric": HEADLINE_METRIC,
             "value": value,
             "unit": "Gelem/s",
             "n_gpus": world,
@@ -941,10 +1023,7 @@ def main():
             "vs_baseline": None,
             "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"single-array k-th select, n=2^27 float32 {FAMILY} "
-                                   "(+5% duplicates, 10 +-inf), 5 ranks per step",
-                       "n": n, "ranks": ks, "parallelism": f"replicas x{world}",
-                       "l2": "input larger than L2 (no flush needed)"},
+            "config": headline_config(n, ks, world),
             "gpu_launches": args.steps * len(ks),
             "e2e": {"value": e2e_value, "unit": "Gelem/s", "h2d_bytes_per_step": n * 4,
                     "d2h_bytes_per_step": len(ks) * 4},
