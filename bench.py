@@ -828,9 +828,11 @@ def bench_drivers(gbs, ctx, torch, np, args):
 
 
 def bench_sharded(gbs, ctx, torch, np, args, x):
-    """The 2^27 array as four host-simulated shards on this device (per-shard passes with
-    the library's kernels, totals summed on the host between passes); median; wall time of
-    the host-driven loop, identical result to the single-array select required."""
+    """The 2^27 array as four shards on this device, median: the device-resident loop
+    (per-shard passes into one device accumulator, the state advanced on the device, the
+    phase read back every 4 passes) and the host-driven loop (totals summed on the host
+    between passes); wall time of each, identical result to the single-array select
+    required."""
     from paper_1104_2732_gb300.sharded import GpuBackend, select_kth_sharded
     n = x.numel()
     m = n // 4
@@ -846,9 +848,23 @@ def bench_sharded(gbs, ctx, torch, np, args, x):
         trace = []
         got = select_kth_sharded(shards, k, GpuBackend(ctx), elem_bytes=4, trace=trace)
     ms = (time.perf_counter() - t0) / reps * 1e3
+    # the device-resident loop on the same shards (no process group: one rank)
+    from paper_1104_2732_gb300.sharded import select_kth_sharded_device
+    info = {}
+    select_kth_sharded_device(shards, k, ctx, elem_bytes=4, info=info)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        info = {}
+        got_d = select_kth_sharded_device(shards, k, ctx, elem_bytes=4, info=info)
+    ms_d = (time.perf_counter() - t0) / reps * 1e3
+    same = lambda v: bool(np.float32(v).view(np.uint32) == np.float32(single).view(np.uint32))
     return {"workload": "median of the 2^27 float32 array split into 4 shards on one device",
-            "metric": "ms/selection (host wall clock)", "value": ms, "cutting_plane_passes": len(trace),
-            "identical_to_single_array": bool(np.float32(got).view(np.uint32) == np.float32(single).view(np.uint32))}
+            "metric": "ms/selection (host wall clock)", "value": ms_d, "form": "device-resident loop",
+            "cutting_plane_passes": info["passes"], "launched_passes": info["launched_passes"],
+            "identical_to_single_array": same(got_d),
+            "host_loop": {"ms": ms, "cutting_plane_passes": len(trace), "identical_to_single_array": same(got)},
+            "speedup_vs_host_loop": ms / ms_d}
 
 
 def main():

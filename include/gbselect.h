@@ -494,6 +494,30 @@ gbs_status gbs_shard_update(gbs_shard_state* s, const gbs_cost_eval* total);
  * gbs_cost_pass_log_*.  EINVAL for an unknown driver or a state that has iterated. */
 gbs_status gbs_shard_set_driver(gbs_shard_state* s, int32_t driver);
 
+/* Device-resident loop (step 2 above without a host round trip per pass).  The state
+ * (made on the host by gbs_shard_begin, gbs_shard_set_driver and one gbs_shard_next) is
+ * copied to device memory, d_state, 8-byte aligned; d_acc is a device array of 8 int64,
+ * zeroed before the first pass, both owned by the caller.  Per pass, stream-ordered:
+ *   a. every shard: gbs_shard_pass_dev_*: if the state is ITERATE and d_acc[4] == 0, adds
+ *      the shard's #(x < t), #(x <= t), #(x <= a) to d_acc[0..2] and its S (the cost of
+ *      gbs_cost_pass_*, or of gbs_cost_pass_log_* for the log driver, on the float32
+ *      images of the elements) to d_acc[3] in fixed point: each block's part times
+ *      2^fx rounded to an integer, fx = 61 - e where n (t - a) < 2^e, the same in
+ *      every process, so the totals do not depend on the order of the additions;
+ *   b. the caller sums d_acc[0..3] over its processes in place (an all-reduce);
+ *   c. gbs_shard_step_dev: steps 1.3-1.4 from those totals, then step 1.1 (the code of
+ *      gbs_shard_update and gbs_shard_next), and clears d_acc[0..3].  An update or next
+ *      that fails leaves the state as it was and stores its status in d_acc[4], which
+ *      stops the loop.
+ * Once the state leaves ITERATE both calls do nothing, so the host may enqueue several
+ * passes and read the phase (and d_acc[4]) back now and then.  Step 3 is as above.
+ * EINVAL for a null or misaligned pointer or n < 0 (n = 0: nothing to do). */
+gbs_status gbs_shard_pass_dev_f32(gbs_ctx* ctx, const float* x, int64_t n, const gbs_shard_state* d_state,
+                                  int64_t* d_acc, void* stream);
+gbs_status gbs_shard_pass_dev_f64(gbs_ctx* ctx, const double* x, int64_t n, const gbs_shard_state* d_state,
+                                  int64_t* d_acc, void* stream);
+gbs_status gbs_shard_step_dev(gbs_ctx* ctx, gbs_shard_state* d_state, int64_t* d_acc, void* stream);
+
 /* One pass at the points a < t for rank k in the coordinates u = log1p(x - xmin)
  * (Sec. 4 Discussion: order statistics commute with increasing maps, and the log map
  * keeps huge elements from swamping the cost sums): the counts #(x < t), #(x <= t),

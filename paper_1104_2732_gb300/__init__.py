@@ -136,6 +136,9 @@ _SIGS = {
     "gbs_cost_pass_log_f64": (C.c_int, [_P, _P, _I64, _I64, C.c_double, C.c_double, C.c_double, _P, _P]),
     "gbs_compact_f32": (C.c_int, [_P, _P, _I64, C.c_double, C.c_double, _P, _I64, C.POINTER(_I64), _P]),
     "gbs_compact_f64": (C.c_int, [_P, _P, _I64, C.c_double, C.c_double, _P, _I64, C.POINTER(_I64), _P]),
+    "gbs_shard_pass_dev_f32": (C.c_int, [_P, _P, _I64, _P, _P, _P]),
+    "gbs_shard_pass_dev_f64": (C.c_int, [_P, _P, _I64, _P, _P, _P]),
+    "gbs_shard_step_dev": (C.c_int, [_P, _P, _P, _P]),
     "gbs_status_string": (C.c_char_p, [C.c_int]),
     "gbs_check_wait_timeout": (C.c_int, [_P, _I64, C.POINTER(C.c_int32), _P]),
 }
@@ -216,6 +219,12 @@ class Context:
         h = _P()
         _check(gbs_create(C.byref(h), self.device), "gbs_create")
         self._h = h
+
+    @property
+    def torch_device(self):
+        """The torch device of this context's GPU."""
+        import torch
+        return torch.device("cuda", self.device)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -311,6 +320,26 @@ class Context:
                   C.c_void_p(buf.data_ptr()), _stream_ptr(stream)), "gbs_cost_pass_log")
         rec = gbs_cost_eval.from_buffer_copy(bytes(buf.cpu().numpy()))
         return {f: getattr(rec, f) for f, _ in gbs_cost_eval._fields_ if f != "pad"}
+
+    def shard_pass_dev(self, x, d_state, d_acc, stream=None):
+        """gbs_shard_pass_dev_*: the shard's pass at the device state's (a, t), added into
+        d_acc (device int64[8]); d_state is a device uint8 tensor holding one
+        gbs_shard_state."""
+        import torch
+        x = self._in(x, "x")
+        self._in(d_state, "d_state", dtype=torch.uint8, numel=C.sizeof(gbs_shard_state))
+        self._in(d_acc, "d_acc", dtype=torch.int64, numel=8)
+        fn = globals()["gbs_shard_pass_dev_" + _suffix(x)]
+        _check(fn(self._h, C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(d_state.data_ptr()),
+                  C.c_void_p(d_acc.data_ptr()), _stream_ptr(stream)), "gbs_shard_pass_dev")
+
+    def shard_step_dev(self, d_state, d_acc, stream=None):
+        """gbs_shard_step_dev: bracket update and next point on the device state."""
+        import torch
+        self._in(d_state, "d_state", dtype=torch.uint8, numel=C.sizeof(gbs_shard_state))
+        self._in(d_acc, "d_acc", dtype=torch.int64, numel=8)
+        _check(gbs_shard_step_dev(self._h, C.c_void_p(d_state.data_ptr()), C.c_void_p(d_acc.data_ptr()),
+                                  _stream_ptr(stream)), "gbs_shard_step_dev")
 
     def compact(self, x, a, b, z=None, stream=None):
         """The elements of x in (a, b] (any order), as a view of z (allocated with room

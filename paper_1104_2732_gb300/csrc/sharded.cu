@@ -1,10 +1,10 @@
 // Selection over a vector split into shards that are reduced separately (on several
 // devices, in several processes, or as sub-ranges of one array): Algorithm 1 (Sec. 3)
 // with the per-pass totals summed by the caller, as the paper's multi-GPU remark sums
-// the per-device reductions on the host.  This file holds the scalar part of the method
-// as host code -- the starting bracket from the pass-0 totals (Sec. 3, step 0), the
-// cutting-plane iterate (step 1.1) and the bracket update (steps 1.3-1.4) -- and the
-// compaction kernel of the finish.  The per-element passes are the library's own
+// the per-device reductions on the host.  This file holds the host API of the scalar part
+// of the method -- the starting bracket from the pass-0 totals (Sec. 3, step 0), and the
+// cutting-plane iterate (step 1.1) and bracket update (steps 1.3-1.4) of shard_sm.cuh --
+// and the compaction kernel of the finish.  The per-element passes are the library's own
 // gbs_array_stats_* and gbs_cost_pass_* on each shard.
 #include <algorithm>
 #include <cmath>
@@ -15,6 +15,7 @@
 #include "api_internal.h"
 #include "common.cuh"
 #include "elem.cuh"
+#include "shard_sm.cuh"
 
 static_assert(sizeof(gbs_shard_state) == 184, "gbs_shard_state layout is part of the C-ABI");
 static_assert(sizeof(gbs_array_stats) == 88 && sizeof(gbs_cost_eval) == 48, "C-ABI struct layout");
@@ -22,86 +23,9 @@ static_assert(sizeof(gbs_array_stats) == 88 && sizeof(gbs_cost_eval) == 48, "C-A
 namespace gbs {
 namespace {
 
-// ---------------------------------------------------------------------------------
-// Host arithmetic on the element grid (float32 or float64).
-// ---------------------------------------------------------------------------------
-uint64_t host_ukey(double v, int eb) {   // totalOrder key of v as an element of width eb
-  if (eb == 4) {
-    uint32_t u;
-    const float f = (float)v;
-    std::memcpy(&u, &f, 4);
-    return (u & 0x80000000u) ? (uint64_t)(~u) : (uint64_t)(u | 0x80000000u);
-  }
-  uint64_t u;
-  std::memcpy(&u, &v, 8);
-  return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
-}
-double host_ukey_value(uint64_t k, int eb) {
-  if (eb == 4) {
-    const uint32_t kk = (uint32_t)k;
-    const uint32_t u = (kk & 0x80000000u) ? (kk & 0x7FFFFFFFu) : ~kk;
-    float f;
-    std::memcpy(&f, &u, 4);
-    return (double)f;
-  }
-  const uint64_t u = (k & 0x8000000000000000ull) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
-  double d;
-  std::memcpy(&d, &u, 8);
-  return d;
-}
-double round_to(double v, int eb) { return eb == 4 ? (double)(float)v : v; }
-double next_up(double v, int eb) {
-  return eb == 4 ? (double)std::nextafter((float)v, std::numeric_limits<float>::infinity())
-                 : std::nextafter(v, std::numeric_limits<double>::infinity());
-}
-double next_down(double v, int eb) {
-  return eb == 4 ? (double)std::nextafter((float)v, -std::numeric_limits<float>::infinity())
-                 : std::nextafter(v, -std::numeric_limits<double>::infinity());
-}
-// a point of the grid strictly inside (a, b), as close to v as possible
-double inside(double v, double a, double b, int eb) {
-  double t = round_to(v, eb);
-  if (!(t > a)) t = next_up(a, eb);
-  if (!(t < b)) t = next_down(b, eb);
-  return t;
-}
-
-// x_(k) = 0: -0 sorts before +0, so it is -0 when k - #(x < 0) <= #(x = -0)
-void finish_zero(gbs_shard_state* s, int64_t clt) {
-  if (s->result == 0.0) s->result = (s->k - clt) <= s->n_negzero ? -0.0 : 0.0;
-}
-void done(gbs_shard_state* s, double v, int32_t how, int64_t clt) {
-  s->phase = GBS_SHARD_DONE;
-  s->result = v;
-  s->how = how;
-  if (clt >= 0) finish_zero(s, clt);
-}
-
-// Brent's root-finder on g(y) = #(x < y) - k + 1/2 over the bracket (a, b), where
-// g(a) = #(x <= a) - k + 1/2 < 0 and g(b) = #(x < b) - k + 1/2 > 0: inverse quadratic
-// interpolation through (a, b, the last point evaluated) when their g are distinct, else
-// the secant through the ends; the interpolant is taken when it lies strictly inside and
-// moves less than half the step before last, else the midpoint (Brent's safeguard).
-double brent_point(gbs_shard_state* s, double mid) {
-  const double a = s->a, b = s->b;
-  if (s->cle_a < 0) return mid;
-  const double ga = (double)(s->cle_a - s->k) + 0.5, gb = (double)(s->clt_b - s->k) + 0.5;
-  double t;
-  const double c = s->px, gc = s->pg;
-  const bool iqi = s->it > 0 && c != a && c != b && gc != ga && gc != gb && ga != gb;
-  if (iqi) {
-    t = a * gb * gc / ((ga - gb) * (ga - gc)) + b * ga * gc / ((gb - ga) * (gb - gc)) +
-        c * ga * gb / ((gc - ga) * (gc - gb));
-  } else {
-    t = a - ga * (b - a) / (gb - ga);
-  }
-  const double last = s->it > 0 ? s->px : (std::fabs(ga) < std::fabs(gb) ? a : b);
-  const bool ok = std::isfinite(t) && t > a && t < b && (s->it < 2 || std::fabs(t - last) < 0.5 * std::fabs(s->step2));
-  const double chosen = ok ? t : mid;
-  s->step2 = s->step1;
-  s->step1 = chosen - last;
-  return chosen;
-}
+using sm::done;
+using sm::next_down;
+using sm::round_to;
 
 // ---------------------------------------------------------------------------------
 // Compaction of (a, b] (the finish of Sec. 3): warp ballots, one atomic per warp.
@@ -298,37 +222,8 @@ gbs_status gbs_shard_begin(gbs_shard_state* s, int32_t elem_bytes, int64_t n, in
 }
 
 gbs_status gbs_shard_next(gbs_shard_state* s) {
-  if (!s || s->phase != GBS_SHARD_ITERATE) return GBS_EINVAL;
-  const int eb = s->elem_bytes;
-  if (s->cle_a >= 0) {
-    const int64_t pop = s->cle_b - s->cle_a;
-    if (pop <= s->cap || s->it >= s->maxit || s->stalled >= 2) {
-      s->phase = GBS_SHARD_COMPACT;
-      return GBS_OK;
-    }
-  }
-  const double mid = s->a + 0.5 * (s->b - s->a);   // the bracket's midpoint in value
-  double t;
-  if (s->driver == GBS_DRIVER_BISECT) {
-    t = inside(mid, s->a, s->b, eb);
-  } else if (s->driver == GBS_DRIVER_BRENT) {
-    t = inside(brent_point(s, mid), s->a, s->b, eb);
-  } else if (s->use_bisect || !s->dfv || s->cle_a < 0) {
-    const uint64_t ka = host_ukey(s->a, eb), kb = host_ukey(s->b, eb);
-    t = inside(host_ukey_value(ka + (kb - ka) / 2, eb), s->a, s->b, eb);
-  } else {
-    const double gL = (double)(s->cle_a - s->k) + 0.5, gR = (double)(s->clt_b - s->k) + 0.5;
-    if (s->driver == GBS_DRIVER_LOG) {   // the tangent intersection in u = log1p(x - xmin)
-      const double ua = std::log1p(s->a - s->xmin), ub = std::log1p(s->b - s->xmin);
-      const double ut = ua + (gR * (ub - ua) - s->dF) / (gR - gL);
-      t = inside(s->xmin + std::expm1(ut), s->a, s->b, eb);
-    } else {
-      const double w = s->b - s->a;
-      t = inside(s->a + (gR * w - s->dF) / (gR - gL), s->a, s->b, eb);
-    }
-  }
-  s->t = t;
-  return GBS_OK;
+  if (!s) return GBS_EINVAL;
+  return sm::next(s);
 }
 
 gbs_status gbs_shard_set_driver(gbs_shard_state* s, int32_t driver) {
@@ -339,52 +234,8 @@ gbs_status gbs_shard_set_driver(gbs_shard_state* s, int32_t driver) {
 }
 
 gbs_status gbs_shard_update(gbs_shard_state* s, const gbs_cost_eval* total) {
-  if (!s || !total || s->phase != GBS_SHARD_ITERATE) return GBS_EINVAL;
-  const int64_t k = s->k;
-  if (total->c_le_a < 0 || total->c_lt_t < total->c_le_a || total->c_le_t < total->c_lt_t ||
-      total->c_le_t > s->n)
-    return GBS_EINTERNAL;
-  if (s->cle_a < 0) {          // the first pass counted #(x <= m)
-    s->cle_a = total->c_le_a;
-    if (s->cle_a >= k) {       // x_(k) = m; #(x < m) = #(x = -inf)
-      done(s, s->a, GBS_HOW_MIN, s->n_neginf);
-      return GBS_OK;
-    }
-  } else if (total->c_le_a != s->cle_a) {
-    return GBS_EINTERNAL;      // the shards did not all see the same array
-  }
-  s->it++;
-  const int64_t clt = total->c_lt_t, cle = total->c_le_t;
-  if (clt < k && k <= cle) {   // step 1.3: 0 in dF(t)
-    done(s, s->t, GBS_HOW_HIT, clt);
-    return GBS_OK;
-  }
-  const double gL = (double)(s->cle_a - k) + 0.5;
-  const double width = s->driver == GBS_DRIVER_LOG ? std::log1p(s->t - s->xmin) - std::log1p(s->a - s->xmin)
-                                                   : s->t - s->a;
-  const double dphi = gL * width + total->S;
-  const int64_t pop = s->cle_b - s->cle_a;
-  // the root-finder's memory: the point just evaluated with its g on the side it moves
-  s->px = s->t;
-  s->pg = cle < k ? (double)(cle - k) + 0.5 : (double)(clt - k) + 0.5;
-  if (cle < k) {               // step 1.4: the subgradient at t is negative
-    s->a = s->t;
-    s->cle_a = cle;
-    s->dF = s->dF - dphi;
-  } else {
-    s->b = s->t;
-    s->clt_b = clt;
-    s->cle_b = cle;
-    s->dF = dphi;
-    s->dfv = 1;
-  }
-  const int64_t npop = s->cle_b - s->cle_a;
-  if (s->driver == GBS_DRIVER_KELLEY || s->driver == GBS_DRIVER_LOG) {   // the safeguards of the cutting plane
-    const int prev = s->use_bisect;
-    s->use_bisect = (!prev) && ((double)npop > 0.75 * (double)pop);
-    s->stalled = ((double)npop > 0.875 * (double)pop) ? s->stalled + 1 : 0;
-  }
-  return GBS_OK;
+  if (!s || !total) return GBS_EINVAL;
+  return sm::update(s, total);
 }
 
 gbs_status gbs_cost_pass_log_f32(gbs_ctx* ctx, const float* x, int64_t n, int64_t k, double a, double t,

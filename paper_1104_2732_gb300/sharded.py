@@ -19,6 +19,11 @@ runs on a shard through a *backend*, and the per-pass totals are formed by a *co
   ``torch.distributed`` (one or more shards per rank; the collectives are one small
   all-reduce per pass and one all-gather of at most cap elements at the end).
 
+:func:`select_kth_sharded_device` keeps the cutting-plane loop on the device instead:
+the state lives in device memory, each pass adds the shards' counts and fixed-point
+cost into one device accumulator that the ranks all-reduce in place, and a one-thread
+step advances the state with the host API's own code (no host round trip per pass).
+
 The result equals the single-array result bit for bit.
 """
 from __future__ import annotations
@@ -26,8 +31,8 @@ from __future__ import annotations
 import ctypes as C
 import math
 
-from . import (DRIVERS, GBS_DRIVER_LOG, GBS_OK, GBS_SHARD_COMPACT, GBS_SHARD_DONE, GBS_SHARD_ITERATE,
-               GBS_SHARD_NAN, GBS_ENAN, GbsError, gbs_array_stats, gbs_cost_eval, gbs_shard_begin, gbs_shard_next,
+from . import (DRIVERS, GBS_DRIVER_LOG, GBS_EINTERNAL, GBS_OK, GBS_SHARD_COMPACT, GBS_SHARD_DONE,
+               GBS_SHARD_ITERATE, GBS_SHARD_NAN, GBS_ENAN, GbsError, gbs_array_stats, gbs_cost_eval, gbs_shard_begin, gbs_shard_next,
                gbs_shard_set_driver, gbs_shard_state, gbs_shard_update)
 
 _STAT_SUMS = ("n", "n_nan", "n_neginf", "n_posinf", "n_negzero", "n_finite")
@@ -59,13 +64,18 @@ class LocalComm:
 
 
 class TorchComm:
-    """Totals over the ranks of a torch.distributed process group (NCCL on devices,
-    gloo on CPU tensors); ``device`` is where the small reduction tensors live."""
+    """Totals over the ranks of a torch.distributed process group; ``device`` is where
+    the small reduction tensors live: by default the current CUDA device when the group's
+    backend is NCCL (which reduces device tensors only), else the CPU (gloo)."""
 
-    def __init__(self, group=None, device="cpu"):
+    def __init__(self, group=None, device=None):
+        import torch
         import torch.distributed as dist
         self.dist = dist
         self.group = group
+        if device is None:
+            nccl = dist.get_backend(group) == "nccl"
+            device = torch.device("cuda", torch.cuda.current_device()) if nccl else torch.device("cpu")
         self.device = device
 
     def _reduce(self, v, dtype, op):
@@ -134,10 +144,97 @@ class GpuBackend:
     def empty(self, elem_bytes):
         import torch
         return torch.empty(0, dtype=torch.float32 if elem_bytes == 4 else torch.float64,
-                           device=f"cuda:{self.ctx.device}")
+                           device=self.ctx.torch_device)
 
     def select(self, z, r):
         return float(self.ctx.select_kth(z, r).item())
+
+
+def _begin(shards, k, backend, comm, elem_bytes, cap, maxit, driver):
+    """Pass 0 on every shard (Sec. 3, step 0), its totals over the shards and processes,
+    and the state of gbs_shard_begin with the chosen driver."""
+    st = [backend.stats(s) for s in shards]
+    sums = comm.sum_i64([sum(int(r[f]) for r in st) for f in _STAT_SUMS])
+    fin = [r for r in st if int(r["n_finite"]) > 0]
+    total = gbs_array_stats()
+    for f, v in zip(_STAT_SUMS, sums):
+        setattr(total, f, v)
+    total.sum = comm.sum_f64([math.fsum(float(r["sum"]) for r in fin)])[0]
+    total.min = comm.min_f64([min((float(r["min"]) for r in fin), default=math.inf)])[0]
+    total.max = comm.max_f64([max((float(r["max"]) for r in fin), default=-math.inf)])[0]
+    if total.n_finite == 0:
+        total.min = total.max = 0.0
+    state = gbs_shard_state()
+    _check(gbs_shard_begin(C.byref(state), int(elem_bytes), total.n, int(k), C.byref(total), int(cap), int(maxit)),
+           "gbs_shard_begin")
+    _check(gbs_shard_set_driver(C.byref(state), DRIVERS[driver]), "gbs_shard_set_driver")
+    return state
+
+
+def _finish(state, shards, k, backend, comm, elem_bytes):
+    """The end of a sharded selection: the result, or the finish over (a, b] (Sec. 3)."""
+    if state.phase == GBS_SHARD_NAN:
+        raise GbsError(GBS_ENAN, "select_kth_sharded")
+    if state.phase == GBS_SHARD_DONE:
+        return state.result
+    assert state.phase == GBS_SHARD_COMPACT
+    local = [backend.compact(s, state.a, state.b) for s in shards]
+    z = comm.gather(backend.concat(local) if local else backend.empty(elem_bytes), backend)
+    r = int(k - state.cle_a)
+    return backend.select(z, r)
+
+
+def select_kth_sharded_device(shards, k, ctx, group=None, elem_bytes=4, cap=0, maxit=0, driver="kelley",
+                              check_every=4, info=None):
+    """x_(k) of the concatenation of the shards of every rank, with the cutting-plane
+    loop resident on the device: per pass, each shard's gbs_shard_pass_dev adds its
+    counts and fixed-point cost into one device int64[8]; with a process group the ranks
+    sum it in place by one all_reduce (NCCL on the device, stream-ordered); then
+    gbs_shard_step_dev updates the device state.  Nothing returns to the host during a
+    pass: the phase is read back every ``check_every`` passes.  Pass 0 and the finish
+    (compaction, one all_gather, select) are as in :func:`select_kth_sharded`.
+
+    ``shards``: this rank's CUDA tensors on ``ctx``'s device (any number, empty allowed).
+    ``group``: a torch.distributed group, or None for the default group when one is
+    initialised (else this process alone).  ``info`` (a dict) receives the passes taken.
+    The result equals the single-array result bit for bit."""
+    import torch
+    import torch.distributed as dist
+    backend = GpuBackend(ctx)
+    distributed = group is not None or (dist.is_available() and dist.is_initialized())
+    comm = TorchComm(group) if distributed else LocalComm()
+    shards = [s for s in shards if s is not None and len(s) > 0]
+    state = _begin(shards, k, backend, comm, elem_bytes, cap, maxit, driver)
+    if state.phase == GBS_SHARD_ITERATE:
+        _check(gbs_shard_next(C.byref(state)), "gbs_shard_next")
+    passes = 0
+    if state.phase == GBS_SHARD_ITERATE:
+        dev = ctx.torch_device
+        nbytes = C.sizeof(gbs_shard_state)
+        d_state = torch.frombuffer(bytearray(bytes(state)), dtype=torch.uint8).to(dev)
+        d_acc = torch.zeros(8, dtype=torch.int64, device=dev)
+        limit = int(state.maxit) + 2 * check_every + 2   # passes before the state must have left ITERATE
+        while True:
+            for _ in range(check_every):
+                for s in shards:
+                    ctx.shard_pass_dev(s, d_state, d_acc)
+                if distributed:
+                    dist.all_reduce(d_acc[:4], group=group)
+                ctx.shard_step_dev(d_state, d_acc)
+                passes += 1
+            raw = d_state.cpu().numpy().tobytes()
+            status = int(d_acc[4].item())
+            if status != 0:
+                raise GbsError(status, "gbs_shard_step_dev")
+            state = gbs_shard_state.from_buffer_copy(raw[:nbytes])
+            if state.phase != GBS_SHARD_ITERATE:
+                break
+            if passes > limit:
+                raise GbsError(GBS_EINTERNAL, "select_kth_sharded_device")
+    if info is not None:
+        info["passes"] = int(state.it)
+        info["launched_passes"] = passes
+    return _finish(state, shards, k, backend, comm, elem_bytes)
 
 
 def select_kth_sharded(shards, k, backend, comm=None, elem_bytes=4, cap=0, maxit=0, trace=None, driver="kelley"):
@@ -152,23 +249,7 @@ def select_kth_sharded(shards, k, backend, comm=None, elem_bytes=4, cap=0, maxit
     kept)."""
     comm = comm or LocalComm()
     shards = [s for s in shards if s is not None and len(s) > 0]
-    # pass 0 on every shard (Sec. 3, step 0), totals over the shards and processes
-    st = [backend.stats(s) for s in shards]
-    sums = comm.sum_i64([sum(int(r[f]) for r in st) for f in _STAT_SUMS])
-    fin = [r for r in st if int(r["n_finite"]) > 0]
-    total = gbs_array_stats()
-    for f, v in zip(_STAT_SUMS, sums):
-        setattr(total, f, v)
-    total.sum = comm.sum_f64([math.fsum(float(r["sum"]) for r in fin)])[0]
-    total.min = comm.min_f64([min((float(r["min"]) for r in fin), default=math.inf)])[0]
-    total.max = comm.max_f64([max((float(r["max"]) for r in fin), default=-math.inf)])[0]
-    if total.n_finite == 0:
-        total.min = total.max = 0.0
-    n = total.n
-    state = gbs_shard_state()
-    _check(gbs_shard_begin(C.byref(state), int(elem_bytes), n, int(k), C.byref(total), int(cap), int(maxit)),
-           "gbs_shard_begin")
-    _check(gbs_shard_set_driver(C.byref(state), DRIVERS[driver]), "gbs_shard_set_driver")
+    state = _begin(shards, k, backend, comm, elem_bytes, cap, maxit, driver)
     log = state.driver == GBS_DRIVER_LOG
     # cutting-plane passes (Algorithm 1, steps 1.1-1.4)
     while state.phase == GBS_SHARD_ITERATE:
@@ -184,13 +265,4 @@ def select_kth_sharded(shards, k, backend, comm=None, elem_bytes=4, cap=0, maxit
         if trace is not None:
             trace.append(t)
         _check(gbs_shard_update(C.byref(state), C.byref(tot)), "gbs_shard_update")
-    if state.phase == GBS_SHARD_NAN:
-        raise GbsError(GBS_ENAN, "select_kth_sharded")
-    if state.phase == GBS_SHARD_DONE:
-        return state.result
-    # finish: compaction of (a, b] on every shard, selection inside the union (Sec. 3)
-    assert state.phase == GBS_SHARD_COMPACT
-    local = [backend.compact(s, state.a, state.b) for s in shards]
-    z = comm.gather(backend.concat(local) if local else backend.empty(elem_bytes), backend)
-    r = int(k - state.cle_a)
-    return backend.select(z, r)
+    return _finish(state, shards, k, backend, comm, elem_bytes)
