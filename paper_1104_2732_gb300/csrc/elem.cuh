@@ -131,6 +131,40 @@ __device__ __forceinline__ void core(double xv, unsigned long long ka, unsigned 
   const float d = fmaf(f64_to_f32_trunc(u), nsig, tsig);
   S += in ? d : 0.f;
 }
+// float64, the fast form: every decision on the high 32 bits of the keys, exact unless an
+// element's high word equals a threshold's, when the element takes the comparisons above
+// (rare: those elements lie within 2^32 ulps of a or t).  Valid when t is not a zero (one
+// key serves "<" and "<="; kt = CmpOf::lt(t) = CmpOf::le(t)) and |a|, |t| < 2^127, so that
+// no element of (a, t) lies above float32's range: its float32 image is then formed from
+// the high word alone (exponent rebiased, 20 mantissa bits; 0 below the normal range).
+__device__ __forceinline__ bool core64_fast_ok(unsigned long long ka, unsigned long long kt_lt,
+                                               unsigned long long kt_le) {
+  constexpr unsigned long long kLo = 0x381FFFFFFFFFFFFFull, kHi = 0xC7E0000000000000ull;   // keys of -+2^127
+  return kt_lt == kt_le && ka > kLo && ka < kHi && kt_lt > kLo && kt_lt < kHi;
+}
+__device__ __forceinline__ void core64_fast(double xv, unsigned long long ka, unsigned long long kt, uint32_t a_hi,
+                                            uint32_t t_hi, float nsig, float tsig, unsigned& lt, unsigned& le,
+                                            float& S) {
+  const uint64_t u = (uint64_t)__double_as_longlong(xv);
+  const uint32_t hi = (uint32_t)(u >> 32);
+  const uint32_t khi = hi ^ ((uint32_t)((int32_t)hi >> 31) | 0x80000000u);
+  const bool p = khi < t_hi;                 // x < t for certain
+  const bool r = p & (khi > a_hi);           // a < x < t for certain
+  lt += p;
+  le += p;
+  const uint32_t fb = (((hi << 3) + 0x40000000u) & 0x7FFFFFFFu) | (hi & 0x80000000u);
+  const float xi = (hi & 0x7FFFFFFFu) >= 0x38100000u ? __uint_as_float(fb) : 0.f;
+  const float d = fmaf(xi, nsig, tsig);
+  S += r ? d : 0.f;
+  if ((khi == t_hi) | (khi == a_hi)) {
+    const unsigned long long kx = ukey_bits(u);
+    if (khi == t_hi) {
+      lt += (kx < kt);
+      le += (kx <= kt);
+    }
+    if ((kx > ka) & (kx < kt)) S += fmaf(f64_to_f32_trunc(u), nsig, tsig);
+  }
+}
 // float32: the IEEE comparisons of the inline-PTX core (both thresholds are t itself).
 __device__ __forceinline__ void core(float x, float a, float t_lt, float, float nsig, float tsig, unsigned& lt,
                                      unsigned& le, float& S) {
@@ -210,6 +244,8 @@ __device__ __forceinline__ void keep_only(double xv, unsigned long long ka, unsi
   if (w) st_shared(off, xv);
   off += w ? 256u : 0u;
 }
+
+
 
 template <typename T> __device__ __forceinline__ typename Ops<T>::C cmp_pos_inf();
 template <> __device__ __forceinline__ float cmp_pos_inf<float>() { return INFINITY; }

@@ -248,7 +248,7 @@ __device__ __forceinline__ FinDigit<T> fin_digit0(T a, T b) {
 template <typename T, bool FIRST, bool COMPACT>
 __device__ __noinline__ bool cut_pass(const T* __restrict__ x, const Geometry<T>& geo, bool rev, Thr<T> h,
                                       float nsig, float tsig, T* __restrict__ zr, unsigned int* s_cnt,
-                                      T* wb, unsigned int* hist, FinDigit<T> dg, PassAcc& acc) {
+                                      T* wb, unsigned int* hist, const FinDigit<T>* dgp, PassAcc& acc) {
   using U = typename KeyOf<T>::U;
   constexpr int W = KeyOf<T>::kBitsW;
   using C = typename Ops<T>::C;
@@ -280,6 +280,7 @@ __device__ __noinline__ bool cut_pass(const T* __restrict__ x, const Geometry<T>
     auto on_kept = [&](T v, bool act) {
       if (!FIRST && act) {
         const U key = ukey(v);
+        const FinDigit<T>& dg = *dgp;   // shared memory: read per kept element, not held
         if (dg.exact || (key > dg.k_lo && key <= dg.k_hi &&
                          (dg.known == 0 || (U)(key >> (W - dg.known)) == dg.prefix)))
           atomicAdd(&hist[(unsigned int)(key >> dg.sh) & dg.dmask], 1u);
@@ -288,6 +289,7 @@ __device__ __noinline__ bool cut_pass(const T* __restrict__ x, const Geometry<T>
     auto hist_one = [&](T v) {   // one element outside the warp-wide copy-out
       if (!FIRST) {
         const U key = ukey(v);
+        const FinDigit<T>& dg = *dgp;
         if (key > dg.k_lo && key <= dg.k_hi && (dg.known == 0 || (U)(key >> (W - dg.known)) == dg.prefix))
           atomicAdd(&hist[(unsigned int)(key >> dg.sh) & dg.dmask], 1u);
       }
@@ -305,6 +307,14 @@ __device__ __noinline__ bool cut_pass(const T* __restrict__ x, const Geometry<T>
       stream_edges(x, geo, fe);
     }
     stream_chunks_compact(x, geo, rev, fk, zr, s_cnt, wb, on_kept);
+  } else if (Ops<T>::kVec == 2 && !FIRST && core64_fast_ok((unsigned long long)h.a_le, (unsigned long long)h.t_lt,
+                                                               (unsigned long long)h.t_le)) {
+    // float64: decisions on the keys' high words (elem.cuh)
+    const unsigned long long ka = (unsigned long long)h.a_le, kt = (unsigned long long)h.t_lt;
+    const uint32_t a_hi = (uint32_t)(ka >> 32), t_hi = (uint32_t)(kt >> 32);
+    auto f64 = [&](T v) { core64_fast((double)v, ka, kt, a_hi, t_hi, nsig, tsig, lt, le, S); };
+    stream_edges(x, geo, f64);
+    stream_chunks(x, geo, rev, f64);
   } else {
     stream_edges(x, geo, f);
     stream_chunks(x, geo, rev, f);
@@ -796,6 +806,8 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     const int first = s_br.first, compact = s_br.compact;
     const bool rev = (pass & 1) == 0;   // pass 0 ran forward
     // a compacting pass after the first also forms the finish's first-round histogram
+    __shared__ FinDigit<T> s_dg;
+    if (tid == 0) s_dg = fin_digit0(s_br.a, s_br.b);
     const FinDigit<T> dg = fin_digit0(s_br.a, s_br.b);
     const bool fill = compact && !first;
     if (tid == 0) s_zcnt = 0;
@@ -806,11 +818,11 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
     T* zr = A.z + region_start(bid, nch, G, Ops<T>::kVec);
     bool ok;
     if (first) {
-      if (compact) ok = cut_pass<T, true, true>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, s_hist, dg, acc);
-      else ok = cut_pass<T, true, false>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, s_hist, dg, acc);
+      if (compact) ok = cut_pass<T, true, true>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, s_hist, &s_dg, acc);
+      else ok = cut_pass<T, true, false>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, s_hist, &s_dg, acc);
     } else {
-      if (compact) ok = cut_pass<T, false, true>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, s_hist, dg, acc);
-      else ok = cut_pass<T, false, false>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, s_hist, dg, acc);
+      if (compact) ok = cut_pass<T, false, true>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, s_hist, &s_dg, acc);
+      else ok = cut_pass<T, false, false>(A.x, geo, rev, thr, nsig, tsig, zr, &s_zcnt, s_wb, s_hist, &s_dg, acc);
     }
     if (!ok) return;
     if (bid == 0 && tid == 0 && pass < kMaxIt) s_tstream[pass] = globaltimer();
