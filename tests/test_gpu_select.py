@@ -220,6 +220,27 @@ def test_select_huge_outliers_do_not_add_passes(ctx, dtype):
         assert st["passes"] <= base["passes"] + 3
 
 
+@pytest.mark.parametrize("cap", [0, 64])
+def test_select_f64_clustered_within_one_high_word(ctx, cap):
+    """float64 passes decide on the keys' high 32 bits and take exact comparisons for the
+    elements that share a threshold's high word: here most elements lie within 2^32 ulps
+    of 1.0 and of -3.0 (so every iterate inside a cluster shares its high word with them),
+    with ties, zeros and a few spread values; results bit-exact for every rank."""
+    rng = np.random.default_rng(47)
+    n = 400_003
+    ulps = rng.integers(0, 1 << 31, n)
+    x = np.where(rng.random(n) < 0.5, 1.0 + ulps * 2.0 ** -52, -3.0 - ulps * 2.0 ** -51)
+    x[::97] = 1.0 + 12345 * 2.0 ** -52            # ties inside the cluster
+    x[::1009] = 0.0
+    x[::1013] = -0.0
+    x[:50] = rng.standard_normal(50) * 1e3        # a few values outside the clusters
+    ctx.set_config(cap=cap)
+    try:
+        check(ctx, x, (1, 77, n // 3, n // 2, (n + 1) // 2, 2 * n // 3, n - 5, n))
+    finally:
+        ctx.set_config(cap=0)
+
+
 def test_select_nan_reports_enan(ctx, lib):
     x = torch.from_numpy(synth.uniform(1000, seed=40)).cuda()
     x[17] = float("nan")
