@@ -343,6 +343,22 @@ def bench_lms(gbs, ctx, torch, np, args):
 
     reps = max(3, min(20, args.steps // 5))
     fused_ms, (lms_f, lts_f, fused_passes) = timed(lambda: ctx.lms_lts_fused(Xt, yt, tt, k=k, h=h), reps)
+    # the dominant kernel of the fused form: its compaction pass, timed by the library's
+    # CUDA events on the call's stream (mean over a few calls)
+    wms = []
+    for _ in range(5):
+        ctx.lms_lts_fused(Xt, yt, tt, k=k, h=h)
+        wms.append(ctx.lms_last_stats()["write_ms"])
+    write_ms = statistics.mean(wms)
+    clk_mhz = measured_peaks()[0].get("sm_max_mhz", 2070.0)
+    lane_peak = 152 * 128 * float(clk_mhz) * 1e6
+    ops = 9 * n * C
+    roofline = {"bound": "alu", "kernel": "fused_pass_kernel<1, compaction>", "algorithmic_ops_per_launch": ops,
+                "ops_per_candidate_row": 9, "achieved": ops / (write_ms * 1e-3), "peak": lane_peak,
+                "unit": "lane-ops/s", "frac": ops / (write_ms * 1e-3) / lane_peak, "pass_ms": write_ms,
+                "peak_derivation": "152 SMs x 128 FP32/INT32 lanes x the maximum SM clock",
+                "ops": "residual subtract, square, s <= a, s > b, a < s <= b, sum and count below, "
+                       "count above, count kept (the product runs on the tensor cores)"}
     # the same fused form started from the extremes (Algorithm 1, step 0) instead of the
     # sampled brackets
     ctx.set_config(lms_start=1)
@@ -387,7 +403,7 @@ def bench_lms(gbs, ctx, torch, np, args):
     return {
         "workload": "LMS/LTS, n=1e6, p=8, 30% contaminated rows, 2048 elemental candidates, k=(n+1)/2, h=(n+p+1)/2",
         "metric": "candidates/s", "value": C / (chosen_ms * 1e-3), "ms": chosen_ms, "chosen_form": chosen,
-        "fused_ms": fused_ms, "fused_passes": fused_passes,
+        "fused_ms": fused_ms, "fused_passes": fused_passes, "roofline": roofline,
         "fused_extremes_start": {"ms": fx_ms, "passes": fx_passes, "lms_identical": fx_same},
         "materialised_ms": mat_ms,
         "plain_value": C / (plain_ms * 1e-3), "plain_ms": plain_ms, "speedup_vs_plain": plain_ms / chosen_ms,

@@ -310,6 +310,18 @@ gbs_status gbs_lms_lts_fused_f32(gbs_ctx* ctx, const float* X, const float* y, i
                                  const float* theta, int32_t C, int64_t k_lms, int64_t h_lts,
                                  float* lms_out, double* lts_out, int32_t* passes, void* stream);
 
+/* Host record of the last gbs_lms_lts_fused_f32 call on ctx (synchronises its stream):
+ * passes over the rows, launches of the fused pass kernels, their device time (CUDA
+ * events recorded on the call's stream around each launch), and of that the time of the
+ * compaction pass (the one pass of the sampled start). */
+typedef struct {
+    int32_t passes;
+    int32_t pass_launches;
+    double pass_ms;
+    double write_ms;
+} gbs_lms_stats;
+gbs_status gbs_lms_last_stats(gbs_ctx* ctx, gbs_lms_stats* out);
+
 /* ---- The LMS / LTS estimator search (Sec. 5: computing the estimator takes many
  * evaluations of F(theta)).  Candidates theta_c (C x p row-major float32, device; elemental
  * fits, for instance) are given.

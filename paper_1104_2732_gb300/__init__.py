@@ -72,6 +72,11 @@ class gbs_knn_stats(C.Structure):
                 ("pass_launches", C.c_int32), ("pass_ms", C.c_double)]
 
 
+class gbs_lms_stats(C.Structure):
+    _fields_ = [("passes", C.c_int32), ("pass_launches", C.c_int32), ("pass_ms", C.c_double),
+                ("write_ms", C.c_double)]
+
+
 GBS_SHARD_ITERATE, GBS_SHARD_DONE, GBS_SHARD_COMPACT, GBS_SHARD_NAN = range(4)
 GBS_DRIVER_KELLEY, GBS_DRIVER_BISECT, GBS_DRIVER_BRENT, GBS_DRIVER_LOG = range(4)
 DRIVERS = {"kelley": GBS_DRIVER_KELLEY, "bisect": GBS_DRIVER_BISECT, "brent": GBS_DRIVER_BRENT, "log": GBS_DRIVER_LOG}
@@ -114,6 +119,7 @@ _SIGS = {
     "gbs_knn_classify_f32": (C.c_int, [_P, _P, _I64, C.c_int32, _P, C.c_int32, _P, C.c_int32, _I64, _P, _P, _P,
                                        _P]),
     "gbs_knn_last_stats": (C.c_int, [_P, C.POINTER(gbs_knn_stats)]),
+    "gbs_lms_last_stats": (C.c_int, [_P, C.POINTER(gbs_lms_stats)]),
     "gbs_bracket_model_set": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int32]),
     "gbs_bracket_model_get": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int32]),
     "gbs_bracket_model_save": (C.c_int, [_P, C.c_char_p]),
@@ -453,6 +459,12 @@ class Context:
                                      C.c_void_p(lts.data_ptr()), C.byref(npass), _stream_ptr(stream)),
                "gbs_lms_lts_fused")
         return lms, lts, npass.value
+
+    def lms_last_stats(self):
+        """Record of the last gbs_lms_lts_fused_f32 call (synchronises its stream)."""
+        rec = gbs_lms_stats()
+        _check(gbs_lms_last_stats(self._h, C.byref(rec)), "gbs_lms_last_stats")
+        return {f: getattr(rec, f) for f, _ in gbs_lms_stats._fields_}
 
     def lts_csteps(self, X, y, theta, h=None, max_steps=20, stream=None):
         """(theta_out (C, p) float32, objective (C,) float64, refits (C,) int32): C-steps of

@@ -46,6 +46,8 @@ struct gbs_ctx {
   size_t knn_bytes = 0;
   cudaEvent_t knn_ev[2] = {nullptr, nullptr};   // around the fused pass launches
   gbs_knn_stats knn_last{};
+  cudaEvent_t lms_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // around the fused LMS passes
+  gbs_lms_stats lms_last{};
   // LMS / LTS search: squares of a batch of candidates, C-step state; search arrays
   void* search_buf = nullptr;
   size_t search_bytes = 0;

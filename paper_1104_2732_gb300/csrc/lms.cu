@@ -235,6 +235,12 @@ size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 }  // namespace gbs
 
 void gbs_internal_release_lms(gbs_ctx* c) {
+  for (int e = 0; e < 4; ++e) {
+    if (c->lms_ev[e]) {
+      cudaEventDestroy(c->lms_ev[e]);
+      c->lms_ev[e] = nullptr;
+    }
+  }
   if (c->lms_buf) {
     cudaDeviceSynchronize();
     cudaFree(c->lms_buf);

@@ -124,6 +124,13 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// Stores v at addr when p holds, without a branch around the store.
+__device__ __forceinline__ void st_global_if(bool p, float* addr, float v) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.global.f32 [%1], %2;\n\t}" ::"r"((unsigned int)p),
+               "l"(addr), "f"(v)
+               : "memory");
+}
+
 // One element of a cost pass: le += [s <= t], S += [a < s <= t] * sigma * (t - s).
 __device__ __forceinline__ void core_le(float s, float a, float t, float nsig, float tsig, unsigned& le, float& S) {
   asm("{\n\t"
@@ -300,12 +307,14 @@ __device__ __forceinline__ void fused_item(const FusedArgs& A, long long item, f
           } else {
             // below the bracket: the stage's partial sum; inside: the lane's next slot; above:
             // counted (a NaN square, or a row past the end, fails all three tests)
-            nf[j] += (s > pb[j]) ? 1u : 0u;
+            const bool above = s > pb[j];
             const bool below = s <= pa[j];
-            const bool keep = (s > pa[j]) & (s <= pb[j]);
+            const bool keep = (s > pa[j]) & !above;
+            nf[j] += above ? 1u : 0u;
             stage_sum[j] += below ? s : 0.f;
             lea[j] += below ? 1u : 0u;
-            if (keep && kept[j] < room[j]) zp[j][kept[j]] = s;   // room is 0 for inactive lanes
+            // a predicated store, no branch (room is 0 for inactive lanes)
+            st_global_if(keep & (kept[j] < room[j]), zp[j] + kept[j], s);
             kept[j] += keep ? 1u : 0u;
           }
         }
@@ -392,7 +401,7 @@ __device__ __forceinline__ void fused_item(const FusedArgs& A, long long item, f
 
 // One pass: a persistent grid walks the work items (candidate block x row chunk).
 template <int KS, int MODE>
-__global__ void __launch_bounds__(kFT, 2) fused_pass_kernel(FusedArgs A) {
+__global__ void __launch_bounds__(kFT, (MODE == kFWrite && KS == 1) ? 3 : 2) fused_pass_kernel(FusedArgs A) {
   __shared__ __align__(16) float xs[2][kFRows * 16 * KS];
   __shared__ __align__(16) float ys[2][kFRows];
   const long long items = (long long)A.ncb * A.nrc;
@@ -969,8 +978,27 @@ extern "C" gbs_status gbs_lms_lts_fused_f32(gbs_ctx* c, const float* X, const fl
       theta, Cpad, p, P8, const_cast<float*>(A.th), const_cast<float*>(A.tl), C);
   fused_init_kernel<<<sgrid, 256, 0, strm>>>(A.tot, C, P.counters);
   if ((st = check()) != GBS_OK) return st;
+  // the passes' device time: events 0/1 around a statistics or cost pass (read after the
+  // synchronisation that follows it), 2/3 around the compaction pass (read at the end)
+  for (int e = 0; e < 4; ++e)
+    if (!c->lms_ev[e] && cudaEventCreate(&c->lms_ev[e]) != cudaSuccess) return GBS_ECUDA;
+  c->lms_last = gbs_lms_stats{};
+  bool timed_open = false;
+  auto read_timed = [&]() {
+    float ms = 0.f;
+    if (timed_open && cudaEventElapsedTime(&ms, c->lms_ev[0], c->lms_ev[1]) == cudaSuccess) c->lms_last.pass_ms += ms;
+    timed_open = false;
+  };
   auto pass = [&](int mode) {
-    return KS == 1 ? launch_pass<1>(mode, A, c->num_sms, strm) : launch_pass<2>(mode, A, c->num_sms, strm);
+    const int w = mode == kFWrite ? 2 : 0;
+    if (cudaEventRecord(c->lms_ev[w], strm) != cudaSuccess) return GBS_ECUDA;
+    const gbs_status r =
+        KS == 1 ? launch_pass<1>(mode, A, c->num_sms, strm) : launch_pass<2>(mode, A, c->num_sms, strm);
+    if (r != GBS_OK) return r;
+    if (cudaEventRecord(c->lms_ev[w + 1], strm) != cudaSuccess) return GBS_ECUDA;
+    if (mode != kFWrite) timed_open = true;
+    c->lms_last.pass_launches += 1;
+    return GBS_OK;
   };
   int npass = 0;
   unsigned int h_cnt[2] = {0u, 0u};
@@ -1022,6 +1050,7 @@ extern "C" gbs_status gbs_lms_lts_fused_f32(gbs_ctx* c, const float* X, const fl
       if (cudaMemcpyAsync(h_cnt, P.counters, sizeof(h_cnt), cudaMemcpyDeviceToHost, strm) != cudaSuccess ||
           cudaStreamSynchronize(strm) != cudaSuccess)
         return GBS_ECUDA;
+      read_timed();
       if (h_cnt[0] == 0) break;
       if (cudaMemsetAsync(P.counters, 0, sizeof(unsigned int), strm) != cudaSuccess) return GBS_ECUDA;
       A.ring_slot = it % kRing;
@@ -1055,6 +1084,15 @@ extern "C" gbs_status gbs_lms_lts_fused_f32(gbs_ctx* c, const float* X, const fl
       cudaStreamSynchronize(strm) != cudaSuccess)
     return GBS_ECUDA;
   if (passes) *passes = npass;
+  c->lms_last.passes = npass;
+  read_timed();
+  {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->lms_ev[2], c->lms_ev[3]) == cudaSuccess) {
+      c->lms_last.write_ms = ms;
+      c->lms_last.pass_ms += ms;
+    }
+  }
   const int m = (int)h_cnt[1];
   if (m > 0) {
     unsigned int* cnt2 = P.counters + 2;
@@ -1072,5 +1110,11 @@ extern "C" gbs_status gbs_lms_lts_fused_f32(gbs_ctx* c, const float* X, const fl
     if ((st = check()) != GBS_OK) return st;
   }
   c->last_segments = C;
+  return GBS_OK;
+}
+
+extern "C" gbs_status gbs_lms_last_stats(gbs_ctx* c, gbs_lms_stats* out) {
+  if (!c || !out) return GBS_EINVAL;
+  *out = c->lms_last;
   return GBS_OK;
 }

@@ -76,7 +76,7 @@ def test_struct_layouts_and_constants_match_the_c_compiler(libpath, tmp_path):
     include/gbselect.h (a field or constant missing from the header fails to compile)."""
     import paper_1104_2732_gb300 as gbs
     structs = [gbs.gbs_config, gbs.gbs_run_stats, gbs.gbs_array_stats, gbs.gbs_cost_eval, gbs.gbs_shard_state,
-               gbs.gbs_knn_stats]
+               gbs.gbs_knn_stats, gbs.gbs_lms_stats]
     consts = sorted(n for n in dir(gbs) if re.fullmatch(r"GBS_[A-Z0-9_]+", n) and isinstance(getattr(gbs, n), int))
     assert consts
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gbselect.h"', "int main(void) {"]
