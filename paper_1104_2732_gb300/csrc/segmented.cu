@@ -122,8 +122,9 @@ __device__ __forceinline__ void cta_stream(const float* __restrict__ xs, const G
 // As cta_stream, and appends every element with keep(element) to zb (shared memory or
 // this CTA's device-memory region, counter *cnt; appends past zcap are counted, not
 // written, so the caller's count check catches them).  Per warp iteration (16 elements a
-// lane) one atomic reserves the warp's kept elements; then, slot by slot, a ballot gives
-// every keeping lane its position, so each store covers consecutive addresses.
+// lane) one atomic reserves the warp's kept elements and a prefix sum over the lanes'
+// counts gives each lane its place: a lane writes its own kept elements one after
+// another (no dependent chain of ballots over the element slots).
 template <int B, typename Fn, typename Keep>
 __device__ __forceinline__ void cta_stream_compact(const float* __restrict__ xs, const Geometry<float>& g, Fn& f,
                                                    Keep& keep, float* zb, unsigned int zcap, unsigned int* cnt) {
@@ -144,7 +145,6 @@ __device__ __forceinline__ void cta_stream_compact(const float* __restrict__ xs,
       if (q < zcap) zb[q] = e;
     }
   }
-  const unsigned int lt_mask = (1u << lane) - 1u;
   const float4* xv = reinterpret_cast<const float4*>(xs + g.head);
   for (long long w0 = tid - lane; w0 < g.nv; w0 += 4 * B) {
     float4 r[4];
@@ -163,20 +163,26 @@ __device__ __forceinline__ void cta_stream_compact(const float* __restrict__ xs,
         for (int e = 0; e < 4; ++e) kmask |= (keep(Ops<float>::get(r[u], e)) ? 1u : 0u) << (u * 4 + e);
       }
     }
-    const unsigned int total = __reduce_add_sync(0xffffffffu, (unsigned int)__popc(kmask));
+    // each lane writes its kept elements at its place after those of the lower lanes
+    const unsigned int kc = (unsigned int)__popc(kmask);
+    unsigned int incl = kc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
     if (total) {
       unsigned int pos = 0;
-      if (lane == 0) pos = atomicAdd(cnt, total);
-      pos = __shfl_sync(0xffffffffu, pos, 0);
+      if (lane == 31) pos = atomicAdd(cnt, total);
+      pos = __shfl_sync(0xffffffffu, pos, 31) + (incl - kc);
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const bool kk = (kmask >> (u * 4 + e)) & 1u;
-          const unsigned int bal = __ballot_sync(0xffffffffu, kk);
-          const unsigned int q = pos + __popc(bal & lt_mask);
-          if (kk && q < zcap) zb[q] = Ops<float>::get(r[u], e);
-          pos += __popc(bal);
+          if (kk && pos < zcap) zb[pos] = Ops<float>::get(r[u], e);
+          pos += kk ? 1u : 0u;
         }
     }
   }
