@@ -241,6 +241,34 @@ def test_select_f64_clustered_within_one_high_word(ctx, cap):
         ctx.set_config(cap=0)
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("cap", [64, 20000, 150000])
+def test_compaction_and_finish_paths(ctx, dtype, cap):
+    """The compacting pass after the first (keep only, the finish's first-round histogram
+    formed as it keeps) and the finish's rounds: caps from 64 (a late compaction of a
+    narrow bracket) to n/2 (a wide one whose finish takes a third round and reads the
+    second-level copy), on data with heavy ties, runs of -0 and +0 (bracket ends at a
+    zero take the exact key tests), infinities and a dense cluster; every rank exact."""
+    rng = np.random.default_rng(48)
+    n = 300_007
+    x = rng.standard_normal(n)
+    x[rng.choice(n, n // 10, replace=False)] = 0.0
+    x[rng.choice(n, n // 10, replace=False)] = -0.0
+    x[rng.choice(n, n // 20, replace=False)] = 0.75
+    x[:9] = np.inf
+    x[9:17] = -np.inf
+    x[17:5017] = 1.0 + rng.integers(0, 4096, 5000) * 2.0 ** -20
+    x = x.astype(dtype)
+    ctx.set_config(cap=cap)
+    try:
+        ks = sorted({18, 1000, n // 3, int(np.count_nonzero(x < 0)) + 1, int(np.count_nonzero(x <= 0)),
+                     (n + 1) // 2, int(np.count_nonzero(x < 0.75)) + 1, int(np.count_nonzero(x <= 0.75)),
+                     2 * n // 3, n - 5000, n - 9})
+        check(ctx, x, ks)
+    finally:
+        ctx.set_config(cap=0)
+
+
 def test_select_nan_reports_enan(ctx, lib):
     x = torch.from_numpy(synth.uniform(1000, seed=40)).cuda()
     x[17] = float("nan")
