@@ -215,21 +215,6 @@ __device__ __forceinline__ bool radix_takes(float v, uint32_t key, bool filter, 
   return (!filter || ((v > a) && (v <= b))) && (known == 0 || (key >> (32 - known)) == prefix);
 }
 
-// Adds digit d (256: none) of every lane of the warp to the histogram: once for the warp
-// when its active lanes share the digit (runs of equal values), else once per lane.
-__device__ __forceinline__ void radix_hist_add(unsigned int d, int lane, unsigned int* hist) {
-  const unsigned int act = __ballot_sync(0xffffffffu, d < 256u);
-  if (act) {
-    const int l0 = __ffs(act) - 1;
-    const unsigned int d0 = __shfl_sync(0xffffffffu, d, l0);
-    if (__all_sync(0xffffffffu, d == 256u || d == d0)) {
-      if (lane == l0) atomicAdd(&hist[d0], (unsigned int)__popc(act));
-    } else if (d < 256u) {
-      atomicAdd(&hist[d], 1u);
-    }
-  }
-}
-
 // Calls fn(valid, value) on every element of buf[0, m) (16-byte aligned) for this warp's
 // share, kRadixV 16-byte loads in flight per lane; the warp loop is uniform (fn may use
 // warp collectives), and the last m mod 4 elements go to warp 0.
@@ -262,16 +247,29 @@ __device__ __forceinline__ void radix_sweep(const float* buf, int m, Fn& fn) {
 
 // Histogram of the next digit (bits [sh, sh + 8) of the key) over the elements of buf that
 // take part.
+// A lane adds its elements' digits one by one to the shared histogram, except the digit
+// it met twice in a row most recently, which it counts in a register (runs of tied values
+// would serialise on one counter); no warp-wide votes, so no dependent chain of them.
 template <int B>
 __device__ __forceinline__ void radix_hist(const float* buf, int m, bool filter, float a, float b, int known,
                                            uint32_t prefix, int sh, unsigned int dmask, unsigned int* hist) {
-  const int lane = threadIdx.x & 31;
+  unsigned int hot = 0xffffffffu, last = 0xffffffffu, hcnt = 0;
   auto fn = [&](bool ok, float v) {
     const uint32_t key = ukey(v);
-    radix_hist_add(ok && radix_takes(v, key, filter, a, b, known, prefix) ? (key >> sh) & dmask : 256u, lane,
-                   hist);
+    const bool in = ok && radix_takes(v, key, filter, a, b, known, prefix);
+    const unsigned int d = (key >> sh) & dmask;
+    const bool hh = in && d == hot;
+    const bool at = in && !hh;
+    const bool sw = at && d == last;
+    hcnt += hh ? 1u : 0u;
+    if (at) atomicAdd(&hist[d], 1u);
+    if (sw && hcnt) atomicAdd(&hist[hot], hcnt);
+    hot = sw ? d : hot;
+    hcnt = sw ? 0u : hcnt;
+    last = at ? d : last;
   };
   radix_sweep<B>(buf, m, fn);
+  if (hcnt) atomicAdd(&hist[hot], hcnt);
 }
 
 // Appends the elements of buf that take part to zs (counter *cnt; any order; at most cap
@@ -797,11 +795,16 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
         sh.rx.known0 = known;
         sh.rx.prefix0 = known == 0 ? 0u : (known == 32 ? hi : (hi >> (32 - known)));
       }
+      // the free part of the buffer past the segment (16-byte aligned) takes the elements
+      // of the chosen digit once they fit, so that the later rounds sweep only those
+      const int zoff = (int)((n + 3) & ~3ll);
+      float* const zsp = zoff + 256 <= CAP ? zb + zoff : nullptr;
+      const int zscap = zsp != nullptr ? CAP - zoff : 0;
       // trimmed-sum mode: both ranks from shared rounds
-      if (LTS) radix_select2<B>(zb, (int)n, (unsigned long long)k, (unsigned long long)k2, false, 0.f, 0.f, nullptr, 0,
+      if (LTS) radix_select2<B>(zb, (int)n, (unsigned long long)k, (unsigned long long)k2, false, 0.f, 0.f, zsp, zscap,
                                 sh.rx, &sh.key1, &sh.key2);
       const uint32_t key =
-          LTS ? sh.key1 : radix_select<B>(zb, (int)n, (unsigned long long)k, false, 0.f, 0.f, nullptr, 0, sh.rx);
+          LTS ? sh.key1 : radix_select<B>(zb, (int)n, (unsigned long long)k, false, 0.f, 0.f, zsp, zscap, sh.rx);
       const float q = ukey_value(key, 0.f);
       if (tid == 0) {
         if (sh.rx.rank == 0) atomicCAS(&A.ctrl->status, 0, (int)GBS_EINTERNAL);
