@@ -529,6 +529,14 @@ gbs_status gbs_shard_pass_dev_f32(gbs_ctx* ctx, const float* x, int64_t n, const
 gbs_status gbs_shard_pass_dev_f64(gbs_ctx* ctx, const double* x, int64_t n, const gbs_shard_state* d_state,
                                   int64_t* d_acc, void* stream);
 gbs_status gbs_shard_step_dev(gbs_ctx* ctx, gbs_shard_state* d_state, int64_t* d_acc, void* stream);
+/* A pass over several shards in one call: gbs_shard_pass_dev_* on shards[i] (device
+ * pointers) of lens[i] elements for i < count (host arrays), then, when step != 0,
+ * gbs_shard_step_dev (for a process that sums nothing with others).  Stops at the first
+ * failing launch and returns its status. */
+gbs_status gbs_shard_passes_dev_f32(gbs_ctx* ctx, const float* const* shards, const int64_t* lens, int32_t count,
+                                   gbs_shard_state* d_state, int64_t* d_acc, int32_t step, void* stream);
+gbs_status gbs_shard_passes_dev_f64(gbs_ctx* ctx, const double* const* shards, const int64_t* lens, int32_t count,
+                                   gbs_shard_state* d_state, int64_t* d_acc, int32_t step, void* stream);
 
 /* One pass at the points a < t for rank k in the coordinates u = log1p(x - xmin)
  * (Sec. 4 Discussion: order statistics commute with increasing maps, and the log map

@@ -145,6 +145,8 @@ _SIGS = {
     "gbs_shard_pass_dev_f32": (C.c_int, [_P, _P, _I64, _P, _P, _P]),
     "gbs_shard_pass_dev_f64": (C.c_int, [_P, _P, _I64, _P, _P, _P]),
     "gbs_shard_step_dev": (C.c_int, [_P, _P, _P, _P]),
+    "gbs_shard_passes_dev_f32": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_I64), C.c_int32, _P, _P, C.c_int32, _P]),
+    "gbs_shard_passes_dev_f64": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_I64), C.c_int32, _P, _P, C.c_int32, _P]),
     "gbs_status_string": (C.c_char_p, [C.c_int]),
     "gbs_check_wait_timeout": (C.c_int, [_P, _I64, C.POINTER(C.c_int32), _P]),
 }
@@ -338,6 +340,30 @@ class Context:
         fn = globals()["gbs_shard_pass_dev_" + _suffix(x)]
         _check(fn(self._h, C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(d_state.data_ptr()),
                   C.c_void_p(d_acc.data_ptr()), _stream_ptr(stream)), "gbs_shard_pass_dev")
+
+    def shard_passes_dev(self, shards, d_state, d_acc, step=False):
+        """A callable that runs one pass over all the shards (gbs_shard_passes_dev_*), then,
+        with step, the device step: the tensors are checked and their pointers marshalled
+        once, so each call costs one ABI call.  The call runs on the current stream."""
+        import torch
+        if not shards:
+            raise ValueError("shards: at least one shard expected")
+        dt = shards[0].dtype
+        for i, x in enumerate(shards):
+            self._in(x, f"shards[{i}]", dtype=dt)
+        self._in(d_state, "d_state", dtype=torch.uint8, numel=C.sizeof(gbs_shard_state))
+        self._in(d_acc, "d_acc", dtype=torch.int64, numel=8)
+        m = len(shards)
+        ptrs = (_P * m)(*[C.c_void_p(x.data_ptr()) for x in shards])
+        lens = (_I64 * m)(*[x.numel() for x in shards])
+        fn = globals()["gbs_shard_passes_dev_" + _suffix(shards[0])]
+        h, sp, ap, st = self._h, C.c_void_p(d_state.data_ptr()), C.c_void_p(d_acc.data_ptr()), int(bool(step))
+        keep = (shards, d_state, d_acc)   # the tensors outlive the callable
+
+        def run():
+            _check(fn(h, ptrs, lens, m, sp, ap, st, _stream_ptr(None)), "gbs_shard_passes_dev")
+        run.keep = keep
+        return run
 
     def shard_step_dev(self, d_state, d_acc, stream=None):
         """gbs_shard_step_dev: bracket update and next point on the device state."""

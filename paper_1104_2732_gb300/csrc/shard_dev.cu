@@ -51,13 +51,33 @@ __global__ void __launch_bounds__(kDevPassThreads) shard_pass_kernel(const T* __
   const float ut = lg ? (float)log1p((double)t - xmin) : 0.f;
   unsigned int lt = 0, le = 0, lea = 0;
   float S = 0.f;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const T v = x[i];
+  auto f = [&](T v) {
     const C cv = CmpOf<T>::of(v);
     lt += cv < ct_lt;
     le += cv <= ct_le;
     lea += cv <= ca;
     if ((cv > ca) & (cv < ct_lt)) S += lg ? ut - log1pf((float)((double)v - xmin)) : ft - Ops<T>::img(v);
+  };
+  // the scalar head and tail (any alignment), then the 16-byte body with four loads in
+  // flight per thread
+  using V = typename Ops<T>::V;
+  const Geometry<T> geo(x, n);
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  if (gtid < geo.head) f(x[gtid]);
+  if (gtid < geo.n - geo.tail0) f(x[geo.tail0 + gtid]);
+  const V* xv = reinterpret_cast<const V*>(x + geo.head);
+  long long i = gtid;
+  for (; i + 3 * stride < geo.nv; i += 4 * stride) {
+    V r[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) r[u] = load_stream(xv + i + u * stride);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) Ops<T>::each(r[u], f);
+  }
+  for (; i < geo.nv; i += stride) {
+    const V r = load_stream(xv + i);
+    Ops<T>::each(r, f);
   }
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned int r0 = __reduce_add_sync(0xffffffffu, lt), r1 = __reduce_add_sync(0xffffffffu, le),
@@ -134,6 +154,24 @@ gbs_status gbs_shard_pass_dev_f32(gbs_ctx* ctx, const float* x, int64_t n, const
 gbs_status gbs_shard_pass_dev_f64(gbs_ctx* ctx, const double* x, int64_t n, const gbs_shard_state* d_state,
                                   int64_t* d_acc, void* stream) {
   return pass_dev<double>(ctx, x, n, d_state, d_acc, stream);
+}
+gbs_status gbs_shard_passes_dev_f32(gbs_ctx* ctx, const float* const* shards, const int64_t* lens, int32_t count,
+                                   gbs_shard_state* d_state, int64_t* d_acc, int32_t step, void* stream) {
+  if (!ctx || count < 0 || (count > 0 && (!shards || !lens))) return GBS_EINVAL;
+  for (int32_t i = 0; i < count; ++i) {
+    const gbs_status st = pass_dev<float>(ctx, shards[i], lens[i], d_state, d_acc, stream);
+    if (st != GBS_OK) return st;
+  }
+  return step ? gbs_shard_step_dev(ctx, d_state, d_acc, stream) : GBS_OK;
+}
+gbs_status gbs_shard_passes_dev_f64(gbs_ctx* ctx, const double* const* shards, const int64_t* lens, int32_t count,
+                                   gbs_shard_state* d_state, int64_t* d_acc, int32_t step, void* stream) {
+  if (!ctx || count < 0 || (count > 0 && (!shards || !lens))) return GBS_EINVAL;
+  for (int32_t i = 0; i < count; ++i) {
+    const gbs_status st = pass_dev<double>(ctx, shards[i], lens[i], d_state, d_acc, stream);
+    if (st != GBS_OK) return st;
+  }
+  return step ? gbs_shard_step_dev(ctx, d_state, d_acc, stream) : GBS_OK;
 }
 gbs_status gbs_shard_step_dev(gbs_ctx* ctx, gbs_shard_state* d_state, int64_t* d_acc, void* stream) {
   if (!ctx || !d_state || !d_acc) return GBS_EINVAL;

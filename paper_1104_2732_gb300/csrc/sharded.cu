@@ -28,33 +28,56 @@ using sm::next_down;
 using sm::round_to;
 
 // ---------------------------------------------------------------------------------
-// Compaction of (a, b] (the finish of Sec. 3): warp ballots, one atomic per warp.
+// Compaction of (a, b] (the finish of Sec. 3): tiles staged in shared memory, one global
+// atomic per tile.
 // ---------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) compact_kernel(const T* __restrict__ x, long long n, T a, T b,
                                                       T* __restrict__ z, long long zcap,
                                                       unsigned long long* __restrict__ cnt) {
+  // each tile of 4 x 256 elements: the kept ones gathered in shared memory (a warp's
+  // ballot and one shared atomic per element slot), then one global atomic reserves the
+  // tile's place and the block copies them out with consecutive stores
   using C = typename Ops<T>::C;
+  __shared__ T s_buf[4 * 256];
+  __shared__ unsigned int s_n;
+  __shared__ unsigned long long s_base;
   const C ca = CmpOf<T>::le(a), cb = CmpOf<T>::le(b);
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
-    const long long i = base + threadIdx.x;
-    T v = T(0);
-    bool keep = false;
-    if (i < n) {
-      v = x[i];
-      const C cv = CmpOf<T>::of(v);
-      keep = !Ops<T>::is_nan(v) && (cv > ca) && (cv <= cb);
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += 4 * stride) {
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    T v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long i = base + u * stride + threadIdx.x;
+      v[u] = i < n ? x[i] : T(0);
     }
-    const unsigned int m = __ballot_sync(0xffffffffu, keep);
-    if (m) {
-      unsigned long long b0 = 0;
-      if (lane == 0) b0 = atomicAdd(cnt, (unsigned long long)__popc(m));
-      b0 = __shfl_sync(0xffffffffu, b0, 0);
-      const unsigned long long pos = b0 + (unsigned long long)__popc(m & ((1u << lane) - 1u));
-      if (keep && pos < (unsigned long long)zcap) z[pos] = v;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long i = base + u * stride + threadIdx.x;
+      bool keep = false;
+      if (i < n) {
+        const C cv = CmpOf<T>::of(v[u]);
+        keep = !Ops<T>::is_nan(v[u]) && (cv > ca) && (cv <= cb);
+      }
+      const unsigned int m = __ballot_sync(0xffffffffu, keep);
+      if (m) {
+        unsigned int b0 = 0;
+        if (lane == 0) b0 = atomicAdd(&s_n, (unsigned int)__popc(m));
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+        if (keep) s_buf[b0 + __popc(m & ((1u << lane) - 1u))] = v[u];
+      }
     }
+    __syncthreads();
+    const unsigned int tn = s_n;
+    if (threadIdx.x == 0 && tn) s_base = atomicAdd(cnt, (unsigned long long)tn);
+    __syncthreads();
+    const unsigned long long b0 = s_base;
+    for (unsigned int j = threadIdx.x; j < tn; j += blockDim.x)
+      if (b0 + j < (unsigned long long)zcap) z[b0 + j] = s_buf[j];
+    __syncthreads();
   }
 }
 

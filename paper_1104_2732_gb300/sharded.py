@@ -214,13 +214,17 @@ def select_kth_sharded_device(shards, k, ctx, group=None, elem_bytes=4, cap=0, m
         d_state = torch.frombuffer(bytearray(bytes(state)), dtype=torch.uint8).to(dev)
         d_acc = torch.zeros(8, dtype=torch.int64, device=dev)
         limit = int(state.maxit) + 2 * check_every + 2   # passes before the state must have left ITERATE
+        # one ABI call a pass over this rank's shards (and the step with it when alone)
+        run = ctx.shard_passes_dev(shards, d_state, d_acc, step=not distributed) if shards else None
         while True:
             for _ in range(check_every):
-                for s in shards:
-                    ctx.shard_pass_dev(s, d_state, d_acc)
                 if distributed:
+                    if run is not None:
+                        run()
                     dist.all_reduce(d_acc[:4], group=group)
-                ctx.shard_step_dev(d_state, d_acc)
+                    ctx.shard_step_dev(d_state, d_acc)
+                else:
+                    run()
                 passes += 1
             raw = d_state.cpu().numpy().tobytes()
             status = int(d_acc[4].item())

@@ -81,6 +81,14 @@ class FakeDeviceCtx:
         d_acc[2] += int((v <= a).sum())
         d_acc[3] += int(round(math.ldexp(S, sfix_bits(st))))
 
+    def shard_passes_dev(self, shards, d_state, d_acc, step=False):
+        def run():
+            for x in shards:
+                self.shard_pass_dev(x, d_state, d_acc)
+            if step:
+                self.shard_step_dev(d_state, d_acc)
+        return run
+
     def shard_step_dev(self, d_state, d_acc):
         import torch
         g = self.g
