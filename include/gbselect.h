@@ -63,7 +63,8 @@ enum {
 typedef struct {
     int64_t cap;         /* the pass that sees a bracket of <= cap elements compacts it and
                             the cutting plane stops (Sec. 3 ends the iterations once one more
-                            would cost more than it saves the finish); 0 = max(n/8, 4096) */
+                            would cost more than it saves the finish); 0 = max(n/4, 4096) for
+                            float32, max(n/8, 4096) for float64 */
     int32_t maxit;       /* cutting-plane iterations before compaction is forced; 0 = 64 */
     int32_t blocks_per_sm; /* CTAs per SM of the persistent kernel; 0 = 1 below 32 MiB of
                               input, else 2 (at most what fits) */

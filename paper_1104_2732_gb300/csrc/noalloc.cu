@@ -97,7 +97,7 @@ extern "C" gbs_status gbs_select_kth_f32_noalloc(const float* x, int64_t n, int6
   SelArgs<float> A;
   A.x = x; A.n = n; A.k = k; A.out = out; A.mode = kModeSelect;
   A.maxit = 64;
-  A.cap = n / 8 > 4096 ? n / 8 : 4096;
+  A.cap = n / 4 > 4096 ? n / 4 : 4096;   // the float32 default of the context path
   A.a_eval = 0.0; A.t_eval = 0.0;
   A.sigma_stats = select_stats_sigma_f32(n, s.grid);
   A.ctrl = reinterpret_cast<Ctrl*>(s.base + kOffCtrl);

@@ -1213,9 +1213,17 @@ long long z_elems_for(long long n, int grid) {
 // Elements of the finish's second-level buffer: the brackets compacted once they hold at
 // most cap elements (a compaction forced by the iteration limit may exceed it and then
 // reads the regions in every round).
+// The default cap: a quarter of a float32 array (the finish reads the compacted elements
+// at about a tenth of a pass's cost per element, so one more pass saves less than
+// finishing a quarter of the array costs), an eighth of a float64 one (whose compaction
+// and 64-bit finish rounds cost more per element).
+template <typename T>
+long long default_cap(long long n) {
+  return std::max<long long>(sizeof(T) == 4 ? n / 4 : n / 8, 4096);
+}
 template <typename T>
 long long z2_elems_for(long long n, long long cap, int grid) {
-  const long long m = std::min<long long>(n, std::max<long long>(cap, std::max<long long>(n / 8, 4096)));
+  const long long m = std::min<long long>(n, std::max<long long>(cap, default_cap<T>(n)));
   return (m + 3) / 4 * 4 + (long long)grid * vec_of<T>();
 }
 
@@ -1243,7 +1251,7 @@ gbs_status launch_select(gbs_ctx* c, const T* x, long long n, long long k, T* ou
   if (!g.ok) return GBS_ECUDA;
   const int grid = grid_for<T>(c, n);
   const long long zel = z_elems_for<T>(n, grid);
-  const long long cap = c->cfg.cap > 0 ? c->cfg.cap : std::max<long long>(n / 8, 4096);
+  const long long cap = c->cfg.cap > 0 ? c->cfg.cap : default_cap<T>(n);
   const size_t zb = mode == kModeSelect ? (size_t)(zel + z2_elems_for<T>(n, cap, grid)) * sizeof(T) : 0;
   gbs_status s = gbs_internal_ensure(c, zb);
   if (s != GBS_OK) return s;
@@ -1317,11 +1325,12 @@ cudaError_t select_launch_f32(const SelArgs<float>& A, int grid, cudaStream_t st
 gbs_status reserve_select(gbs_ctx* c, long long n, int elem_bytes) {
   DeviceGuard g(c->device);
   if (!g.ok) return GBS_ECUDA;
-  const long long cap = c->cfg.cap > 0 ? c->cfg.cap : std::max<long long>(n / 8, 4096);
   if (elem_bytes == 4) {
+    const long long cap = c->cfg.cap > 0 ? c->cfg.cap : default_cap<float>(n);
     const int grid = grid_for<float>(c, n);
     return gbs_internal_ensure(c, (size_t)(z_elems_for<float>(n, grid) + z2_elems_for<float>(n, cap, grid)) * 4);
   }
+  const long long cap = c->cfg.cap > 0 ? c->cfg.cap : default_cap<double>(n);
   const int grid = grid_for<double>(c, n);
   return gbs_internal_ensure(c, (size_t)(z_elems_for<double>(n, grid) + z2_elems_for<double>(n, cap, grid)) * 8);
 }
