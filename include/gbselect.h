@@ -243,8 +243,8 @@ gbs_status gbs_select_kth_f32_noalloc(const float* x, int64_t n, int64_t k, floa
  * floor((n_s+1)/2); out: S floats, device.  Each CTA takes whole segments, largest
  * first; a segment that fits in shared memory is radix-selected there, a larger one runs
  * the cutting plane (Algorithm 1) with CTA-wide reductions and compacts its final
- * bracket into shared memory, or, once it holds at most n_s/4 elements, into the CTA's
- * share of a 256 MiB device-memory area of the workspace.  A segment with n_s = 0 or k
+ * bracket into shared memory, or, once it holds at most n_s/2 elements, into the CTA's
+ * share of a 1 GiB device-memory area of the workspace.  A segment with n_s = 0 or k
  * outside [1, n_s] gets a NaN and GBS_EINVAL in the device status (gbs_last_stats).  The
  * call launches two kernels and no host synchronisation, so it can be captured in a CUDA
  * graph once the workspace holds 8*S bytes plus that area (gbs_reserve or a first call). */

@@ -6,7 +6,7 @@
 // is loaded once and radix-selected there.  A larger one runs the cutting plane of
 // Algorithm 1 (Sec. 3) with CTA-wide reductions: pass 0 (extremes, sum), then one fused
 // cost + count pass per iterate; the pass that sees a bracket small enough for shared
-// memory compacts it there, or one of at most n/4 elements into the CTA's own
+// memory compacts it there, or one of at most n/2 elements into the CTA's own
 // device-memory region, and the answer is radix-selected inside it (the hybrid of
 // Sec. 3; from device memory the rounds move to shared memory once the chosen digit's
 // elements fit there).  No CTA waits on another, so the launch needs no grid-wide barrier and the
@@ -35,7 +35,7 @@ __device__ __forceinline__ int sched_bucket(long long n) {
   const unsigned int u = __float_as_uint((float)n);   // (float)n is monotone in n, so is the key
   return (int)((u >> 20) - (127u << 3));              // 8 * exponent + top 3 mantissa bits
 }
-constexpr long long kSegGlobalDiv = 4;   // device-memory compaction once pop <= n / 4
+constexpr long long kSegGlobalDiv = 2;   // device-memory compaction once pop <= n / 2
 // smallest segment whose median starts from a learned bracket: every segment too large for
 // shared memory (in a sweep of 2^13..2^16 on 4096 normal arrays, all gave identical results
 // and 2^13 the shortest batch)
@@ -184,6 +184,77 @@ __device__ __forceinline__ void cta_stream_compact(const float* __restrict__ xs,
           if (kk && pos < zcap) zb[pos] = Ops<float>::get(r[u], e);
           pos += kk ? 1u : 0u;
         }
+    }
+  }
+}
+
+// As cta_stream_compact for the elements of (a, b], staged through shared memory (`slots`,
+// 16 floats per thread): a lane stores its kept elements in its own column of its warp's
+// 512 slots (slot q of lane L at 32 q + L), the warp issues the loads of its next
+// iteration, and only then reserves room for its kept elements with one atomic and has
+// each lane copy its column out after those of the lower lanes, four slots at a time.
+// The next vectors are in flight during the reservation and the copy-out; a column is
+// written and read by its own lane only.
+template <int B, typename Fn>
+__device__ __forceinline__ void cta_stream_compact_staged(const float* __restrict__ xs, const Geometry<float>& g,
+                                                          Fn& f, float a, float b, float* slots, float* zb,
+                                                          unsigned int zcap, unsigned int* cnt) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  auto scalar = [&](float e) {
+    f(e);
+    if ((e > a) & (e <= b)) {
+      const unsigned int q = atomicAdd(cnt, 1u);
+      if (q < zcap) zb[q] = e;
+    }
+  };
+  if (tid < g.head) scalar(xs[tid]);
+  if (tid < g.n - g.tail0) scalar(xs[g.tail0 + tid]);
+  const float4* xv = reinterpret_cast<const float4*>(xs + g.head);
+  const unsigned int col = smem_u32(slots + (tid >> 5) * 512 + lane);
+  long long w0 = tid - lane;
+  float4 r[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const long long i = w0 + lane + (long long)u * B;
+    if (i < g.nv) r[u] = __ldcs(xv + i);
+  }
+  for (; w0 < g.nv; w0 += 4 * B) {
+    unsigned int off = col;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long i = w0 + lane + (long long)u * B;
+      if (i < g.nv) {
+        Ops<float>::each(r[u], f);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) keep_only(Ops<float>::get(r[u], e), a, b, off);
+      }
+    }
+    const unsigned int kc = (off - col) >> 7;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long i = w0 + 4 * B + lane + (long long)u * B;
+      if (i < g.nv) r[u] = __ldcs(xv + i);
+    }
+    unsigned int incl = kc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total) {
+      unsigned int pos = 0;
+      if (lane == 31) pos = atomicAdd(cnt, total);
+      pos = __shfl_sync(0xffffffffu, pos, 31) + (incl - kc);
+      const unsigned int maxk = __reduce_max_sync(0xffffffffu, kc);
+      for (unsigned int q = 0; q < maxk; q += 4) {
+        float v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ld_shared(col + min(q + j, 15u) * 128u, v[j]);   // the column's 16 slots
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (q + j < kc && pos + q + j < zcap) zb[pos + q + j] = v[j];
+      }
     }
   }
 }
@@ -567,12 +638,12 @@ struct SegPassAcc {
   float S, sle;
 };
 // One cutting-plane pass over a segment at t (Algorithm 1, step 1.2); FIRST also counts at
-// the extremes, COMPACT appends (a, b] to zb (capacity zcap), SUMLE sums the elements at
-// or below a.
-template <int B, bool FIRST, bool COMPACT, bool SUMLE>
+// the extremes, COMPACT appends (a, b] to zb (capacity zcap; with STAGE through the shared
+// memory `slots`, 16 floats a thread), SUMLE sums the elements at or below a.
+template <int B, bool FIRST, bool COMPACT, bool SUMLE, bool STAGE>
 __device__ __noinline__ void seg_cut_pass(const float* __restrict__ xs, const Geometry<float>& g, float ca, float ct,
                                           float cb, float nsig, float tsig, float* zb, unsigned int zcap,
-                                          unsigned int* cnt, SegPassAcc& acc) {
+                                          unsigned int* cnt, float* slots, SegPassAcc& acc) {
   unsigned int lt = 0, le = 0, xa = 0, xb = 0;
   float S = 0.f, sle = 0.f;
   auto f = [&](float v) {
@@ -585,7 +656,9 @@ __device__ __noinline__ void seg_cut_pass(const float* __restrict__ xs, const Ge
       if (v <= ca) sle += v;
     }
   };
-  if (COMPACT) {
+  if (COMPACT && STAGE) {
+    cta_stream_compact_staged<B>(xs, g, f, ca, cb, slots, zb, zcap, cnt);
+  } else if (COMPACT) {
     auto keep = [&](float v) { return (v > ca) & (v <= cb); };
     cta_stream_compact<B>(xs, g, f, keep, zb, zcap, cnt);
   } else {
@@ -682,27 +755,31 @@ __device__ __noinline__ bool seg_propose(const float* __restrict__ xs, long long
 }
 
 // The lean first pass of a learned start: NaN count, #(x <= a), and (a, b] compacted into
-// zb (capacity zcap, counter *cnt, which also gives #(a < x <= b)).
+// zb in device memory (capacity zcap, counter *cnt, which also gives #(a < x <= b)),
+// staged through the shared memory `slots`.
 struct SegLeanAcc {
   unsigned int nnan, le_a;
 };
 template <int B>
 __device__ __noinline__ void seg_lean_pass(const float* __restrict__ xs, const Geometry<float>& g, float a, float b,
-                                           float* zb, unsigned int zcap, unsigned int* cnt, SegLeanAcc& acc) {
+                                           float* zb, unsigned int zcap, unsigned int* cnt, float* slots,
+                                           SegLeanAcc& acc) {
   unsigned int nnan = 0, le_a = 0;
   auto f = [&](float v) {
     nnan += (v != v);
     le_a += (v <= a);
   };
-  auto keep = [&](float v) { return (v > a) & (v <= b); };
-  cta_stream_compact<B>(xs, g, f, keep, zb, zcap, cnt);
+  cta_stream_compact_staged<B>(xs, g, f, a, b, slots, zb, zcap, cnt);
   acc.nnan = nnan;
   acc.le_a = le_a;
 }
 
-template <int B, int CAP, bool LTS>
+// STAGE: the dynamic shared memory holds 16 B staging floats past the CAP of the buffer,
+// and every compacting pass goes through them (cta_stream_compact_staged).
+template <int B, int CAP, bool LTS, bool STAGE>
 __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
-  extern __shared__ __align__(16) float zb[];   // CAP floats
+  static_assert(CAP >= 16 * B, "the lean pass stages through 16 floats of the buffer a thread");
+  extern __shared__ __align__(16) float zb[];   // CAP floats (+ 16 B staging floats with STAGE)
   __shared__ SegShared sh;
   const int tid = threadIdx.x, lane = tid & 31;
   constexpr int NW = B / 32;
@@ -837,7 +914,7 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
         seg_propose<B>(xs, n, A.W, zb, &sh.pa, &sh.pb)) {
       SegLeanAcc la;
       seg_lean_pass<B>(xs, g, sh.pa, sh.pb, A.zg + (long long)blockIdx.x * A.zg_cap, (unsigned int)A.zg_cap,
-                       &sh.zcnt, la);
+                       &sh.zcnt, zb, la);
       Sum6 v6;
       v6.u[0] = la.nnan; v6.u[1] = la.le_a; v6.u[2] = v6.u[3] = v6.u[4] = 0; v6.d = 0.0;
       const Sum6 r6 = cta_sum6<B>(v6, sh.sum6);   // also orders the appends before the finish
@@ -912,7 +989,7 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
     while (sh.phase == 0) {
       if (tid == 0) {   // step 1.1 (with the key-midpoint safeguard)
         // compaction of (a, b] in this pass: into shared memory when it fits there, else into
-        // the CTA's device-memory region once the bracket holds at most n / 4 elements
+        // the CTA's device-memory region once the bracket holds at most n / 2 elements
         const long long pop = sh.cle_b - sh.cle_a;
         sh.compact = pop <= CAP ? 1
                      : (A.zg != nullptr && pop <= (long long)A.zg_cap && pop * kSegGlobalDiv <= n) ? 2 : 0;
@@ -943,21 +1020,23 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
       float* const zdst = compact == 2 ? A.zg + (long long)blockIdx.x * A.zg_cap : zb;
       const unsigned int zcap = compact == 2 ? (unsigned int)A.zg_cap : (unsigned int)CAP;
       SegPassAcc pacc;
+      float* const slots = zb + CAP;   // the staging slots past the buffer (STAGE variants)
+#define GBS_SEG_PASS(F, C, SL) \
+  seg_cut_pass<B, F, C, SL, STAGE>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, slots, pacc)
       if (first) {
         if (compact) {
-          if (LTS) seg_cut_pass<B, true, true, true>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
-          else seg_cut_pass<B, true, true, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
+          if (LTS) GBS_SEG_PASS(true, true, true); else GBS_SEG_PASS(true, true, false);
         } else {
-          seg_cut_pass<B, true, false, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
+          GBS_SEG_PASS(true, false, false);
         }
       } else {
         if (compact) {
-          if (LTS) seg_cut_pass<B, false, true, true>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
-          else seg_cut_pass<B, false, true, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
+          if (LTS) GBS_SEG_PASS(false, true, true); else GBS_SEG_PASS(false, true, false);
         } else {
-          seg_cut_pass<B, false, false, false>(xs, g, ca, ct, cb, nsig, tsig, zdst, zcap, &sh.zcnt, pacc);
+          GBS_SEG_PASS(false, false, false);
         }
       }
+#undef GBS_SEG_PASS
       const unsigned int lt = pacc.lt, le = pacc.le, xa = pacc.xa, xb = pacc.xb;
       const float S = pacc.S, sle = pacc.sle;
       Sum6 v6;
@@ -1084,16 +1163,17 @@ __global__ void __launch_bounds__(B, 1024 / B) seg_kernel(SegArgs A) {
 
 // The launch variants the autotuner chooses from: CTA size and shared-memory capacity
 // for the direct / finishing select.
+// `stage` staging floats follow the buffer where they fit at the variant's occupancy.
 struct Variant {
-  int threads, cap;
+  int threads, cap, stage;
   void (*kernel)(SegArgs);
   void (*kernel_lts)(SegArgs);
 };
 const Variant kVariants[] = {
-    {512, 12288, seg_kernel<512, 12288, false>, seg_kernel<512, 12288, true>},
-    {512, 24576, seg_kernel<512, 24576, false>, seg_kernel<512, 24576, true>},
-    {1024, 49152, seg_kernel<1024, 49152, false>, seg_kernel<1024, 49152, true>},
-    {256, 12288, seg_kernel<256, 12288, false>, seg_kernel<256, 12288, true>},
+    {512, 12288, 16 * 512, seg_kernel<512, 12288, false, true>, seg_kernel<512, 12288, true, true>},
+    {512, 24576, 0, seg_kernel<512, 24576, false, false>, seg_kernel<512, 24576, true, false>},
+    {1024, 49152, 0, seg_kernel<1024, 49152, false, false>, seg_kernel<1024, 49152, true, false>},
+    {256, 12288, 0, seg_kernel<256, 12288, false, false>, seg_kernel<256, 12288, true, false>},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -1106,7 +1186,7 @@ gbs_status seg_launch(gbs_ctx* c, const SegLaunch& L, int variant, cudaStream_t 
   const Variant& v = kVariants[variant];
   const bool lts = L.outsum != nullptr;
   void (*kern)(SegArgs) = lts ? v.kernel_lts : v.kernel;
-  const size_t smem = (size_t)v.cap * sizeof(float);
+  const size_t smem = (size_t)(v.cap + v.stage) * sizeof(float);
   static bool attr_done[2][kNumVariants] = {};
   if (!attr_done[lts][variant]) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
@@ -1151,9 +1231,10 @@ gbs_status seg_launch(gbs_ctx* c, const SegLaunch& L, int variant, cudaStream_t 
 
 int seg_variant_threads(int v) { return (v >= 0 && v < kNumVariants) ? kVariants[v].threads : 0; }
 
-// Device-memory compaction area of a segmented launch, shared out among its CTAs (256 MiB:
-// about 220,000 elements a CTA at two CTAs on each of 152 SMs).
-constexpr size_t kSegZgBytes = size_t(256) << 20;
+// Device-memory compaction area of a segmented launch, shared out among its CTAs (1 GiB:
+// about 880,000 elements a CTA at two CTAs on each of 152 SMs, so that a bracket of half
+// of a 10^6-element segment fits).
+constexpr size_t kSegZgBytes = size_t(1024) << 20;
 
 size_t seg_workspace_bytes(int S) {
   const size_t head = ((size_t)S * 2 * sizeof(int) + 255) / 256 * 256;
