@@ -1009,13 +1009,12 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
       if (!pre) {
       for (int i = tid; i < kBins; i += kThreads) s_hist[i] = 0;
       __syncthreads();
-      // One element a lane, called by every lane of the warp together: the digit of an
-      // element of (a, b] under the known prefix goes to the histogram.  A lane counts
-      // one "hot" digit in a register (the digit it met twice in a row most recently, so a
-      // run of tied values does not serialise on one shared-memory address); the copying
-      // sweep appends the elements to this CTA's segment of z2, a warp at a time.
+      // One element a lane: the digit of an element of (a, b] under the known prefix goes to
+      // the histogram; returns whether it did.  A lane counts one "hot" digit in a register
+      // (the digit it met twice in a row most recently, so a run of tied values does not
+      // serialise on one shared-memory address).
       unsigned int hot = 0xffffffffu, last = 0xffffffffu, hcnt = 0;
-      auto take = [&](T v, bool valid) {
+      auto take = [&](T v, bool valid) -> bool {
         const U key = ukey(v);
         const bool ok = valid && (key > k_lo) && (key <= k_hi) && (known == 0 || (U)(key >> (W - known)) == prefix);
         const unsigned int d = (unsigned int)(key >> sh) & dmask;
@@ -1029,15 +1028,28 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
         hot = sw ? d : hot;
         hcnt = sw ? 0u : hcnt;
         last = at ? d : last;
-        if (copy) {
-          const unsigned int act = __ballot_sync(0xffffffffu, ok);
-          if (act) {
-            const int l0 = __ffs(act) - 1;
-            unsigned int base = 0;
-            if (lane == l0) base = atomicAdd(&s_z2n, (unsigned int)__popc(act));
-            base = __shfl_sync(0xffffffffu, base, l0);
-            if (ok) z2seg[base + __popc(act & ((1u << lane) - 1u))] = v;
-          }
+        return ok;
+      };
+      // The copying sweep appends a warp's taken elements of one trip to this CTA's segment
+      // of z2: a prefix over the lanes' counts and one shared atomic a warp and trip (a
+      // reservation per element slot serialised the warps on the counter when most
+      // elements fall in the chosen digit, as a run of ties does), then each lane stores
+      // its own elements one after another.  vals(i) is the lane's i-th element of the trip,
+      // bit i of km says whether it was taken.
+      auto append = [&](unsigned int km, auto&& vals) {
+        const unsigned int kc = (unsigned int)__popc(km);
+        unsigned int incl = kc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total) {
+          unsigned int base = 0;
+          if (lane == 31) base = atomicAdd(&s_z2n, total);
+          T* dst = z2seg + __shfl_sync(0xffffffffu, base, 31) + (incl - kc);
+          vals(km, dst);
         }
       };
       // a contiguous range [j0, j1) of src (16-byte aligned): 16-byte vectors, kFinU in
@@ -1056,12 +1068,23 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
               const unsigned int iv = b + (unsigned int)u * kThreads + lane;
               if (iv < jv1) r[u] = __ldcg(sv + iv);
             }
+            unsigned int km = 0;
 #pragma unroll
             for (int u = 0; u < kFinU; ++u) {
               const bool ok = b + (unsigned int)u * kThreads + lane < jv1;
 #pragma unroll
-              for (int e = 0; e < kVec; ++e) take(ok ? Ops<T>::get(r[u], e) : fa, ok);
+              for (int e = 0; e < kVec; ++e)
+                km |= take(ok ? Ops<T>::get(r[u], e) : fa, ok) ? 1u << (u * kVec + e) : 0u;
             }
+            if (copy)
+              append(km, [&](unsigned int m, T* dst) {
+                unsigned int q = 0;
+#pragma unroll
+                for (int u = 0; u < kFinU; ++u)
+#pragma unroll
+                  for (int e = 0; e < kVec; ++e)
+                    if ((m >> (u * kVec + e)) & 1u) dst[q++] = Ops<T>::get(r[u], e);
+              });
           }
         }
         if (warp == 0) {   // the elements outside whole vectors (fewer than 2 kVec)
@@ -1070,7 +1093,9 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
           const unsigned int nh = h1 - j0, nt = j1 - t0;
           const bool ok = (unsigned int)lane < nh + nt;
           const unsigned int j = (unsigned int)lane < nh ? j0 + lane : t0 + (lane - nh);
-          take(ok ? __ldcg(src + j) : fa, ok);
+          const T v = ok ? __ldcg(src + j) : fa;
+          const bool tk = take(v, ok);
+          if (copy) append(tk ? 1u : 0u, [&](unsigned int m, T* dst) { if (m) dst[0] = v; });
         }
       };
       if (from_z2) {
