@@ -229,7 +229,7 @@ gbs_status gbs_cost_pass_f64(gbs_ctx* ctx, const double* x, int64_t n, int64_t k
  * array of about 4.1 MiB that every GPU loading the library holds until process exit.
  * Limits: 1 <= k <= n <= 1048576 (2^20), else GBS_EINVAL before any launch.
  * Runs on the current device.  The first call on a device resolves the array's address
- * there (cudaGetSymbolAddress); make that first call before any stream capture.
+ * there (cudaGetSymbolAddress).
  * All calls share the array: calls whose GPU work overlaps in time (different streams,
  * several threads) race and give wrong results; serialise them.  There is no per-call
  * record to read back: a NaN result means that x holds a NaN or that the device work
