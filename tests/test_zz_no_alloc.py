@@ -1,7 +1,7 @@
 """The allocation-free entry point gbs_select_kth_f32_noalloc.
 
-It exists for callers that cannot let a library allocate device memory (stream
-capture, arena-managed hosts, loops that cannot afford an allocation's implicit
+It exists for callers that cannot let a library allocate device memory (arena-managed
+hosts, fixed device budgets, loops that cannot afford an allocation's implicit
 synchronisation).  It must return exactly what the context-based gbs_select_kth_f32
 returns.  This file is collected last so that a failure here comes after every other
 test has run; it passes alone in a fresh process as well.
