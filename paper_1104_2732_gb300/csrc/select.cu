@@ -1034,8 +1034,8 @@ __global__ void __launch_bounds__(kThreads, 2) select_kernel(SelArgs<T> A) {
       // of z2: a prefix over the lanes' counts and one shared atomic a warp and trip (a
       // reservation per element slot serialised the warps on the counter when most
       // elements fall in the chosen digit, as a run of ties does), then each lane stores
-      // its own elements one after another.  vals(i) is the lane's i-th element of the trip,
-      // bit i of km says whether it was taken.
+      // its own elements one after another: vals(km, dst) stores, from dst on, the trip's
+      // elements whose bits are set in km (bit i: the lane's i-th element of the trip).
       auto append = [&](unsigned int km, auto&& vals) {
         const unsigned int kc = (unsigned int)__popc(km);
         unsigned int incl = kc;
